@@ -1,0 +1,194 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (Sec. 3.1) and the
+benchmark configurations.  Shared by the tests, the smoke check and the
+benchmark; it holds no sorting arithmetic.
+
+Random numbers come from one counter-based generator: output i of stream s is
+SplitMix64's mixing function applied to base(s) + (i + 1) * gamma, where gamma
+is SplitMix64's odd increment (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014).  The stream base is itself the
+mix of (seed XOR (dist_id << 32) XOR (stream << 48)).  Everything is integer
+arithmetic modulo 2^64 in numpy, so x86 and arm64 produce identical bytes.
+
+Uniform integers in [0, R) use Lemire's multiply-shift (2019, "Fast random
+integer generation in an interval") without the rejection step: a 32-bit draw
+u maps to (u * R) >> 32.  The bias is below R / 2^32 and does not matter for
+synthetic sort inputs.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+_CHUNK = 1 << 24
+
+# Distribution ids.  0-6 are the seven distributions of the 100M-key u32
+# workload; 7-9 reproduce the shapes of the paper's input cases 3, 6 and 5.
+DISTS = {
+    0: "uniform_u32",          # uniform over [0, 2^32) (control)
+    1: "uniform_small_1000",   # uniform over [0, 1000)
+    2: "uniform_large_u32",    # uniform over [0, 2^32), a second stream
+    3: "sorted",               # nondecreasing, spread over [0, 2^32)
+    4: "reverse_sorted",       # dist 3 reversed
+    5: "nearly_sorted",        # dist 3 with n // 100 random swaps
+    6: "gaussian",             # mean 2^31, sd 2^20, clipped to [0, 2^32 - 1]
+    7: "sorted_95",            # sorted over [0, 1e6), then 5% of slots overwritten
+    8: "third_one_value",      # n // 3 copies of 500000, rest uniform over [0, 1e6)
+    9: "uniform_1e8",          # uniform over [0, 1e8)
+}
+DIST_IDS = {v: k for k, v in DISTS.items()}
+# Declared [min, max] of each distribution (the paper's "between 0 and M").
+DECLARED_BOUNDS = {
+    0: (0, 2**32 - 1), 1: (0, 999), 2: (0, 2**32 - 1), 3: (0, 2**32 - 1), 4: (0, 2**32 - 1),
+    5: (0, 2**32 - 1), 6: (0, 2**32 - 1), 7: (0, 999_999), 8: (0, 999_999), 9: (0, 10**8 - 1),
+}
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def stream_base(seed: int, dist_id: int = 0, stream: int = 0) -> np.uint64:
+    s = np.array([(seed ^ (dist_id << 32) ^ (stream << 48)) & (2**64 - 1)], np.uint64)
+    return _mix(s)[0]
+
+
+def u64(n: int, seed: int, dist_id: int = 0, stream: int = 0, start: int = 0) -> np.ndarray:
+    """n raw 64-bit draws of one stream, counters start+1 .. start+n."""
+    base = stream_base(seed, dist_id, stream)
+    out = np.empty(n, np.uint64)
+    with np.errstate(over="ignore"):
+        for a in range(0, n, _CHUNK):
+            b = min(n, a + _CHUNK)
+            ctr = np.arange(start + a + 1, start + b + 1, dtype=np.uint64)
+            out[a:b] = _mix(base + ctr * GAMMA)
+    return out
+
+
+def u32(n: int, seed: int, dist_id: int = 0, stream: int = 0) -> np.ndarray:
+    """n 32-bit draws: the high halves of the 64-bit draws."""
+    return (u64(n, seed, dist_id, stream) >> np.uint64(32)).astype(np.uint32)
+
+
+def uniform_below(n: int, R: int, seed: int, dist_id: int, stream: int = 0) -> np.ndarray:
+    """n integers in [0, R), R <= 2^32, by multiply-shift of 32-bit draws."""
+    if R == 2**32:
+        return u32(n, seed, dist_id, stream)
+    d = u32(n, seed, dist_id, stream).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        return ((d * np.uint64(R)) >> np.uint64(32)).astype(np.uint32)
+
+
+def _sorted_spread(n: int, seed: int, dist_id: int, hi: int) -> np.ndarray:
+    """A nondecreasing sequence over [0, hi) built without sorting: slot i holds
+    floor(i * hi / n) plus a random offset below the slot width."""
+    if n == 0:
+        return np.empty(0, np.uint32)
+    i = np.arange(n, dtype=np.uint64)
+    width = max(1, hi // n)
+    with np.errstate(over="ignore"):
+        base = (i * np.uint64(hi)) // np.uint64(n)
+        off = (u32(n, seed, dist_id, 1).astype(np.uint64) * np.uint64(width)) >> np.uint64(32)
+    v = np.minimum(base + off, np.uint64(hi - 1))
+    return v.astype(np.uint32)
+
+
+def keys_u32(n: int, dist: int | str = 0, seed: int = 0) -> np.ndarray:
+    """n uint32 keys of one of the distributions in DISTS."""
+    dist_id = DIST_IDS[dist] if isinstance(dist, str) else int(dist)
+    if dist_id in (0, 2):
+        return u32(n, seed, dist_id)
+    if dist_id == 1:
+        return uniform_below(n, 1000, seed, dist_id)
+    if dist_id == 3:
+        return _sorted_spread(n, seed, 3, 2**32)
+    if dist_id == 4:
+        return _sorted_spread(n, seed, 3, 2**32)[::-1].copy()
+    if dist_id == 5:
+        a = _sorted_spread(n, seed, 3, 2**32)
+        m = n // 100
+        if m:
+            # swap pairs (x_j, y_j) one after another, j = 0 .. m-1
+            xs = uniform_below(m, n, seed, 5, 2).astype(np.int64)
+            ys = uniform_below(m, n, seed, 5, 3).astype(np.int64)
+            for x, y in zip(xs.tolist(), ys.tolist()):
+                a[x], a[y] = a[y], a[x]
+        return a
+    if dist_id == 6:
+        return gaussian_u32(n, seed)
+    if dist_id == 7:
+        a = _sorted_spread(n, seed, 7, 10**6)
+        m = n // 20
+        if m:
+            pos = uniform_below(m, n, seed, 7, 2).astype(np.int64)
+            a[pos] = uniform_below(m, 10**6, seed, 7, 3)
+        return a
+    if dist_id == 8:
+        a = uniform_below(n, 10**6, seed, 8)
+        m = n // 3
+        if m:
+            # put 500000 at the n // 3 distinct slots (step * j + start) mod n,
+            # j < n // 3, with step coprime to n
+            r = u64(2, seed, 8, 2)
+            step = int(r[0] % np.uint64(n)) | 1
+            while math.gcd(step, n) != 1:
+                step += 2
+            start = int(r[1] % np.uint64(n))
+            pos = (np.arange(m, dtype=np.int64) * step + start) % n
+            a[pos] = 500_000
+        return a
+    if dist_id == 9:
+        return uniform_below(n, 10**8, seed, 9)
+    raise ValueError(f"unknown distribution {dist}")
+
+
+def gaussian_u32(n: int, seed: int = 0) -> np.ndarray:
+    """Mean 2^31, sd 2^20: the Irwin-Hall sum S of twelve 32-bit uniforms has
+    mean 6 * 2^32 and sd 2^32 (up to the discreteness of the draws), so
+    2^31 + ((S - 6 * 2^32) >> 12) has sd 2^20.  Integer only, clipped."""
+    out = np.empty(n, np.uint32)
+    for a in range(0, n, _CHUNK):
+        b = min(n, a + _CHUNK)
+        m = b - a
+        s = np.zeros(m, np.int64)
+        for j in range(6):
+            d = u64(m, seed, 6, 10 + j, start=a)
+            s += (d >> np.uint64(32)).astype(np.int64)
+            s += (d & np.uint64(0xFFFFFFFF)).astype(np.int64)
+        v = (2**31) + ((s - 6 * 2**32) >> 12)
+        out[a:b] = np.clip(v, 0, 2**32 - 1).astype(np.uint32)
+    return out
+
+
+def keys_u64(n: int, key_bits: int = 64, seed: int = 0, dist_id: int = 20) -> np.ndarray:
+    """n uint64 keys uniform over [0, 2^key_bits)."""
+    d = u64(n, seed, dist_id)
+    if key_bits < 64:
+        d = d >> np.uint64(64 - key_bits)
+    return d
+
+
+def index_values(n: int) -> np.ndarray:
+    """Payload = original index, so stability is visible in the output."""
+    return np.arange(n, dtype=np.uint32)
+
+
+def log_uniform_sizes(count: int, lo: int, hi: int, seed: int = 0, dist_id: int = 30) -> np.ndarray:
+    """count sizes floor(exp(U(ln lo, ln hi))) (double precision; sizes only)."""
+    d = u64(count, seed, dist_id)
+    u = (d >> np.uint64(11)).astype(np.float64) * (1.0 / 2**53)
+    s = np.floor(np.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))).astype(np.int64)
+    return np.clip(s, lo, hi)
+
+
+def segment_offsets(sizes) -> np.ndarray:
+    sizes = np.asarray(sizes, dtype=np.int64)
+    off = np.zeros(sizes.size + 1, np.uint64)
+    off[1:] = np.cumsum(sizes).astype(np.uint64)
+    return off
