@@ -1,0 +1,211 @@
+/*
+ * rsort.h -- C ABI of a GB300 (sm_103a) integer-sort library implementing the
+ * two methods compared in Horsmalahti, "Comparison of Bucket Sort and RADIX
+ * Sort" (arXiv:1206.3511): LSD radix sort (Sec. 2.5, Algorithm 4, built from
+ * the counting sort of Sec. 2.4, Algorithm 3) and bucket sort (Sec. 2.3,
+ * Algorithm 2).
+ *
+ * The problem (Sec. 2): given a sequence of keys, produce a permutation of it
+ * in nondecreasing order.  Both methods here are stable (the property is
+ * defined in Sec. 2.1 and claimed for each method in Sec. 2.3 and 2.5): keys
+ * that compare equal keep their input order, and an optional 32-bit value travels
+ * with its key.  The output is therefore unique and every call is
+ * bit-reproducible.
+ *
+ * Conventions shared by every call below:
+ *   - All key, value, offset and workspace pointers are DEVICE pointers of the
+ *     current CUDA device.  The caller owns and allocates all of them; no sort
+ *     call allocates device memory.
+ *   - Calls are asynchronous: they validate their arguments on the host,
+ *     enqueue kernels on `stream` and return.  Argument errors are returned
+ *     synchronously and nothing is enqueued.  Errors found on the device (a
+ *     key above 2^key_bits, a bounded wait that gave up) are recorded in a
+ *     status word inside the workspace; read them with rs_get_status().
+ *   - `stream` is a cudaStream_t (0 = the legacy default stream).
+ *   - `ws` must be 256-byte aligned and at least rs_workspace_bytes(...)
+ *     large.  A workspace may be reused by any number of calls issued on one
+ *     stream; calls that use the same workspace concurrently on different
+ *     streams race.
+ *   - keys_in is read only.  keys_out == keys_in (in place) is allowed; any
+ *     other overlap of inputs, outputs and workspace is an argument error
+ *     where it can be detected and undefined otherwise.  The same holds for
+ *     vals_in / vals_out.  vals_in and vals_out are both NULL (keys only) or
+ *     both non-NULL.
+ *   - Keys need only their natural alignment (4 bytes for u32, 8 for u64).
+ *   - n = 0 is a no-op that returns RS_OK.
+ *   - A single sort handles n <= RS_MAX_KEYS keys.
+ */
+#ifndef RSORT_H
+#define RSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RS_API __attribute__((visibility("default")))
+#else
+#define RS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* rs_stream_t;
+
+typedef enum rs_status {
+    RS_OK = 0,
+    RS_ERR_INVALID_ARG = 1,    /* bad pointer, size, alignment, overlap or parameter */
+    RS_ERR_WORKSPACE = 2,      /* workspace NULL, misaligned or smaller than required */
+    RS_ERR_KEY_RANGE = 3,      /* device: a key was >= 2^key_bits (or outside [min,max]) */
+    RS_ERR_BUDGET = 4,         /* server: request can never fit the memory budget */
+    RS_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    RS_ERR_DEVICE_TIMEOUT = 6, /* device: a bounded inter-block wait gave up */
+    RS_ERR_NOT_READY = 7,      /* server: request still running */
+    RS_ERR_SHUTDOWN = 8,       /* server: request cancelled by shutdown */
+    RS_ERR_UNSUPPORTED = 9     /* configuration not compiled into this build */
+} rs_status;
+
+/* Largest n for one (unsegmented) sort: per-block digit counts travel in the
+ * 30-bit count field of the inter-block status words. */
+#define RS_MAX_KEYS ((size_t)1 << 30)
+
+/* Algorithms for rs_workspace_bytes(). */
+#define RS_ALGO_RADIX 0
+#define RS_ALGO_BUCKET 1
+
+/* Kernel shape of one radix sort.  digit_bits is the D of a D-bit digit
+ * (Sec. 2.5 leaves the digit base open); a sort makes ceil(key_bits / D)
+ * passes.  Every valid configuration gives bit-identical output. */
+typedef struct rs_config {
+    int digit_bits;       /* 4 .. 11 */
+    int block_threads;    /* threads per block of the scatter pass */
+    int items_per_thread; /* keys per thread of the scatter pass */
+} rs_config;
+
+/* Human-readable name of a status code (static string, never NULL). */
+RS_API const char* rs_status_string(rs_status s);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+RS_API int rs_version(void);
+
+/* Default kernel shape for keys of `key_bytes` (4 or 8) bytes, with or
+ * without values, for n keys.  Returns RS_ERR_INVALID_ARG on bad sizes. */
+RS_API rs_status rs_default_config(int key_bytes, int has_values, size_t n, rs_config* out);
+
+/* Number of configurations compiled for (key_bytes, has_values) and the i-th
+ * of them (i = 0 .. count-1); these are the candidates an autotuner may try. */
+RS_API int rs_config_count(int key_bytes, int has_values);
+RS_API rs_status rs_config_get(int key_bytes, int has_values, int i, rs_config* out);
+
+/* Workspace bytes for one call of the given algorithm, valid for every
+ * compiled configuration with digit_bits <= 8.  key_bytes: 4 or 8.  key_bits: 0 means the full key
+ * width.  num_buckets: bucket count for RS_ALGO_BUCKET (0 = max(1, n/16));
+ * ignored for radix.  in_place: nonzero if keys_out will equal keys_in.
+ * Returns 0 for invalid arguments. */
+RS_API size_t rs_workspace_bytes(int algo, int key_bytes, int has_values, size_t n, int key_bits,
+                          size_t num_buckets, int in_place);
+
+/* Workspace bytes of a radix sort run with one explicit kernel shape (needed
+ * for shapes with digit_bits > 8, which rs_workspace_bytes does not cover).
+ * Returns 0 for invalid arguments or a shape that is not compiled. */
+RS_API size_t rs_workspace_bytes_cfg(int key_bytes, int has_values, size_t n, int key_bits, const rs_config* cfg);
+
+/* ---------------------------------------------------------------------------
+ * LSD radix sort, Sec. 2.5 Algorithm 4: d = ceil(key_bits / D) stable passes,
+ * least significant digit first, each pass a counting sort (Sec. 2.4,
+ * Algorithm 3) on one D-bit digit.  Every key must be < 2^key_bits
+ * (key_bits 1..32 for u32, 1..64 for u64; 0 means the full width); a larger
+ * key is reported as RS_ERR_KEY_RANGE by rs_get_status() and leaves the output
+ * unspecified (but every write stays inside keys_out / vals_out).
+ * Result: keys_out[0..n) nondecreasing; vals_out[i] is the value that came
+ * with keys_out[i]; equal keys in input order.
+ */
+RS_API rs_status rs_sort_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
+                      uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
+                      rs_stream_t stream);
+RS_API rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
+                      uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
+                      rs_stream_t stream);
+
+/* Same as rs_sort_u32/u64 with an explicit kernel shape (NULL = default).
+ * RS_ERR_UNSUPPORTED if that shape is not compiled. */
+RS_API rs_status rs_sort_u32_ex(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
+                         uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
+                         rs_stream_t stream, const rs_config* cfg);
+RS_API rs_status rs_sort_u64_ex(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
+                         uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
+                         rs_stream_t stream, const rs_config* cfg);
+
+/* ---------------------------------------------------------------------------
+ * Building blocks: one step of the radix path each.
+ *
+ * rs_digit_counts_*: the counting loop of Algorithm 3 for every pass of
+ * Algorithm 4 in one read of the keys.  counts_out (device, uint32,
+ * ceil(key_bits/D) * 2^D entries, row p = pass p) receives
+ * counts_out[p * 2^D + d] = #{i : (keys[i] >> (p*D)) & (2^D-1) == d}.
+ * digit_bits 4..11.
+ */
+RS_API rs_status rs_digit_counts_u32(const uint32_t* keys, size_t n, int key_bits, int digit_bits,
+                              uint32_t* counts_out, void* ws, size_t ws_bytes, rs_stream_t stream);
+RS_API rs_status rs_digit_counts_u64(const uint64_t* keys, size_t n, int key_bits, int digit_bits,
+                              uint32_t* counts_out, void* ws, size_t ws_bytes, rs_stream_t stream);
+
+/* rs_counting_pass_*: one stable counting sort (Algorithm 3) of the whole
+ * array on the digit (key >> shift) & (2^digit_bits - 1), digit_bits 4..11,
+ * shift 0..(key width - 1).  keys_out must not overlap keys_in (likewise the
+ * values).  Workspace: rs_workspace_bytes(RS_ALGO_RADIX, ...) for the same n. */
+RS_API rs_status rs_counting_pass_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
+                               uint32_t* vals_out, size_t n, int shift, int digit_bits, void* ws,
+                               size_t ws_bytes, rs_stream_t stream);
+RS_API rs_status rs_counting_pass_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
+                               uint32_t* vals_out, size_t n, int shift, int digit_bits, void* ws,
+                               size_t ws_bytes, rs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Device status.
+ *
+ * rs_get_status: waits for `stream`, then reads and clears the status word
+ * kept in the workspace header.  Returns RS_OK if no call that used this
+ * workspace since the last rs_get_status recorded a device error, otherwise
+ * the first error recorded (RS_ERR_KEY_RANGE, RS_ERR_DEVICE_TIMEOUT), or
+ * RS_ERR_CUDA if the stream itself failed.  ws must be a workspace that has
+ * been passed to at least one sort call.
+ */
+RS_API rs_status rs_get_status(const void* ws, rs_stream_t stream);
+
+/* Test hooks for the bounded inter-block waits.  spin_limit: polls before a
+ * wait gives up (0 = library default, about a second of polling).
+ * stall_tile: if >= 0, the block that handles that tile of every scatter pass
+ * never publishes its counts, so later blocks wait until spin_limit runs out
+ * and report RS_ERR_DEVICE_TIMEOUT (the output is then unspecified, but all
+ * writes stay inside the output arrays).  Process-wide; not thread safe;
+ * reset with rs_set_debug(0, -1). */
+RS_API void rs_set_debug(uint32_t spin_limit, int stall_tile);
+
+/* ---------------------------------------------------------------------------
+ * Kernel timing and launch counting (instrumentation for benchmarks; the
+ * paper measured whole sorts with clock(), Sec. 3.1).
+ *
+ * rs_profile_enable(1): from now on the library records a CUDA event before
+ * and after every kernel it launches, on the stream of that launch.
+ * rs_profile_read: waits for the recorded events, adds their durations per
+ * kernel kind into out[0 .. cap), returns the number of kinds filled (or -1
+ * on a CUDA error) and forgets the records.  rs_launch_count: number of
+ * kernels this library has launched since it was loaded (always counted).
+ */
+typedef struct rs_kernel_stat {
+    char name[32];
+    uint64_t launches;
+    double total_ms;
+} rs_kernel_stat;
+RS_API void rs_profile_enable(int enable);
+RS_API int rs_profile_read(rs_kernel_stat* out, int cap);
+RS_API uint64_t rs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSORT_H */

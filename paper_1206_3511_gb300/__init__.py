@@ -1,0 +1,129 @@
+"""GB300 (sm_103a) integer sorts: LSD radix sort and bucket sort after
+Horsmalahti, "Comparison of Bucket Sort and RADIX Sort" (arXiv:1206.3511).
+
+Every step runs in hand-written CUDA kernels inside librsort.so, reached
+through its C ABI (include/rsort.h).  PyTorch provides device memory and
+streams only.  The low-level functions of ``_lib`` carry the C names
+(``rs_sort_u32`` ...); the helpers below allocate outputs and workspaces with
+torch and raise ``SortError`` on a non-zero status.
+
+Keys are unsigned integers.  torch tensors of dtype uint32/int32 are treated as
+32-bit keys and uint64/int64 as 64-bit keys, bit for bit (a signed tensor's
+bits are sorted as unsigned).  Values are 32-bit (uint32 or int32).
+"""
+from __future__ import annotations
+
+from . import _lib
+from ._lib import (RS_ALGO_BUCKET, RS_ALGO_RADIX, STATUS, RsConfig, load, rs_config_count, rs_config_get,
+                   rs_counting_pass_u32, rs_counting_pass_u64, rs_default_config, rs_digit_counts_u32,
+                   rs_digit_counts_u64, rs_get_status, rs_launch_count, rs_profile_enable, rs_profile_read,
+                   rs_set_debug, rs_sort_u32, rs_sort_u32_ex, rs_sort_u64,
+                   rs_sort_u64_ex, rs_status_string, rs_version, rs_workspace_bytes, rs_workspace_bytes_cfg)
+
+__all__ = [
+    "SortError", "load", "sort", "counting_pass", "digit_counts", "workspace", "get_status", "key_bytes_of",
+    "rs_sort_u32", "rs_sort_u64", "rs_sort_u32_ex", "rs_sort_u64_ex", "rs_digit_counts_u32",
+    "rs_digit_counts_u64", "rs_counting_pass_u32", "rs_counting_pass_u64", "rs_get_status", "rs_set_debug",
+    "rs_status_string", "rs_version", "rs_workspace_bytes", "rs_workspace_bytes_cfg", "rs_default_config",
+    "rs_config_count", "rs_config_get", "RsConfig", "RS_ALGO_RADIX", "RS_ALGO_BUCKET", "STATUS",
+    "rs_profile_enable", "rs_profile_read", "rs_launch_count",
+]
+
+
+class SortError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)}" if what else STATUS.get(code, str(code)))
+
+
+def check(code: int, what: str = "") -> None:
+    if code != 0:
+        raise SortError(code, what)
+
+
+def key_bytes_of(t) -> int:
+    import torch
+
+    if t.dtype in (torch.uint32, torch.int32):
+        return 4
+    if t.dtype in (torch.uint64, torch.int64):
+        return 8
+    raise TypeError(f"keys must be a 32- or 64-bit integer tensor, got {t.dtype}")
+
+
+def _check_tensor(t, what):
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+
+
+def workspace(nbytes: int, device=None):
+    """A uint8 device buffer of nbytes (torch's allocator aligns it to >= 256 B)."""
+    import torch
+
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def sort(keys, values=None, key_bits: int = 0, out=None, out_values=None, ws=None, stream=None, config=None):
+    """Stable LSD radix sort of a 1-D CUDA tensor (rs_sort_u32 / rs_sort_u64).
+    Returns (sorted_keys, sorted_values or None)."""
+    import torch
+
+    _check_tensor(keys, "keys")
+    kb = key_bytes_of(keys)
+    n = keys.numel()
+    if values is not None:
+        _check_tensor(values, "values")
+        if values.numel() != n or values.element_size() != 4:
+            raise ValueError("values must be 32-bit with one entry per key")
+    out = torch.empty_like(keys) if out is None else out
+    if values is not None and out_values is None:
+        out_values = torch.empty_like(values)
+    cfg = _lib._as_cfg(config)
+    if ws is None:
+        if cfg is not None:
+            nbytes = rs_workspace_bytes_cfg(kb, values is not None, n, key_bits, cfg)
+        else:
+            nbytes = rs_workspace_bytes(RS_ALGO_RADIX, kb, values is not None, n, key_bits, 0, out is keys)
+        ws = workspace(nbytes, keys.device)
+    fn = rs_sort_u32_ex if kb == 4 else rs_sort_u64_ex
+    check(fn(keys, out, values, out_values, n, key_bits, ws, ws.numel(), stream, cfg), "rs_sort")
+    return out, out_values
+
+
+def counting_pass(keys, values=None, shift: int = 0, digit_bits: int = 8, ws=None, stream=None):
+    """One stable counting-sort pass on digit (key >> shift) & (2^digit_bits - 1)."""
+    import torch
+
+    _check_tensor(keys, "keys")
+    kb = key_bytes_of(keys)
+    n = keys.numel()
+    out = torch.empty_like(keys)
+    out_values = torch.empty_like(values) if values is not None else None
+    if ws is None:
+        ws = workspace(rs_workspace_bytes(RS_ALGO_RADIX, kb, values is not None, n, 0, 0, 0), keys.device)
+    fn = rs_counting_pass_u32 if kb == 4 else rs_counting_pass_u64
+    check(fn(keys, out, values, out_values, n, shift, digit_bits, ws, ws.numel(), stream), "rs_counting_pass")
+    return out, out_values
+
+
+def digit_counts(keys, key_bits: int = 0, digit_bits: int = 8, ws=None, stream=None):
+    """Per-pass digit counts, shape (ceil(key_bits/D), 2^D), as an int64 tensor."""
+    import torch
+
+    _check_tensor(keys, "keys")
+    kb = key_bytes_of(keys)
+    kbits = key_bits or 8 * kb
+    P = (kbits + digit_bits - 1) // digit_bits
+    counts = torch.empty(P * (1 << digit_bits), dtype=torch.int32, device=keys.device)
+    if ws is None:
+        ws = workspace(256, keys.device)
+    fn = rs_digit_counts_u32 if kb == 4 else rs_digit_counts_u64
+    check(fn(keys, keys.numel(), key_bits, digit_bits, counts, ws, ws.numel(), stream), "rs_digit_counts")
+    return counts.view(P, 1 << digit_bits).to(torch.int64)
+
+
+def get_status(ws, stream=None) -> int:
+    """Read and clear the device status word of a workspace (syncs the stream)."""
+    return rs_get_status(ws, stream)

@@ -1,0 +1,227 @@
+"""ctypes binding of librsort.so: one Python function per C entry point of
+include/rsort.h, with the same name and argument order.  Arguments may be
+torch tensors (their data pointer is passed), plain integers (raw device
+addresses) or None (NULL).  A ``stream`` of None means torch's current stream
+on the current device.  Nothing here computes; every step runs in the CUDA
+library, and importing fails loudly if that library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librsort.so")
+
+_lock = threading.Lock()
+_lib = None
+
+_c = ctypes
+_P = _c.c_void_p
+_SZ = _c.c_size_t
+_I = _c.c_int
+_U32 = _c.c_uint32
+_U64 = _c.c_uint64
+
+
+class RsConfig(_c.Structure):
+    _fields_ = [("digit_bits", _c.c_int), ("block_threads", _c.c_int), ("items_per_thread", _c.c_int)]
+
+    def as_tuple(self):
+        return (self.digit_bits, self.block_threads, self.items_per_thread)
+
+
+class RsKernelStat(_c.Structure):
+    _fields_ = [("name", _c.c_char * 32), ("launches", _c.c_uint64), ("total_ms", _c.c_double)]
+
+
+# name -> (restype, argtypes)
+SIGNATURES: dict[str, tuple] = {
+    "rs_status_string": (_c.c_char_p, [_I]),
+    "rs_version": (_I, []),
+    "rs_default_config": (_I, [_I, _I, _SZ, _c.POINTER(RsConfig)]),
+    "rs_config_count": (_I, [_I, _I]),
+    "rs_config_get": (_I, [_I, _I, _I, _c.POINTER(RsConfig)]),
+    "rs_workspace_bytes": (_SZ, [_I, _I, _I, _SZ, _I, _SZ, _I]),
+    "rs_workspace_bytes_cfg": (_SZ, [_I, _I, _SZ, _I, _c.POINTER(RsConfig)]),
+    "rs_sort_u32": (_I, [_P, _P, _P, _P, _SZ, _I, _P, _SZ, _P]),
+    "rs_sort_u64": (_I, [_P, _P, _P, _P, _SZ, _I, _P, _SZ, _P]),
+    "rs_sort_u32_ex": (_I, [_P, _P, _P, _P, _SZ, _I, _P, _SZ, _P, _c.POINTER(RsConfig)]),
+    "rs_sort_u64_ex": (_I, [_P, _P, _P, _P, _SZ, _I, _P, _SZ, _P, _c.POINTER(RsConfig)]),
+    "rs_digit_counts_u32": (_I, [_P, _SZ, _I, _I, _P, _P, _SZ, _P]),
+    "rs_digit_counts_u64": (_I, [_P, _SZ, _I, _I, _P, _P, _SZ, _P]),
+    "rs_counting_pass_u32": (_I, [_P, _P, _P, _P, _SZ, _I, _I, _P, _SZ, _P]),
+    "rs_counting_pass_u64": (_I, [_P, _P, _P, _P, _SZ, _I, _I, _P, _SZ, _P]),
+    "rs_get_status": (_I, [_P, _P]),
+    "rs_set_debug": (None, [_U32, _I]),
+    "rs_profile_enable": (None, [_I]),
+    "rs_profile_read": (_I, [_c.POINTER(RsKernelStat), _I]),
+    "rs_launch_count": (_U64, []),
+}
+
+STATUS = {
+    0: "RS_OK", 1: "RS_ERR_INVALID_ARG", 2: "RS_ERR_WORKSPACE", 3: "RS_ERR_KEY_RANGE", 4: "RS_ERR_BUDGET",
+    5: "RS_ERR_CUDA", 6: "RS_ERR_DEVICE_TIMEOUT", 7: "RS_ERR_NOT_READY", 8: "RS_ERR_SHUTDOWN",
+    9: "RS_ERR_UNSUPPORTED",
+}
+RS_ALGO_RADIX = 0
+RS_ALGO_BUCKET = 1
+
+
+def load(path: str | None = None):
+    """Load librsort.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(
+                f"{p} is missing: the CUDA library has not been built "
+                "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        lib = _c.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def ptr(x) -> int | None:
+    """Device address of a tensor, an int address, or None for NULL."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _call(name, *args):
+    return getattr(load(), name)(*args)
+
+
+# ---- one thin function per C entry point (same names, same argument order)
+def rs_status_string(s: int) -> str:
+    return _call("rs_status_string", s).decode()
+
+
+def rs_version() -> int:
+    return _call("rs_version")
+
+
+def rs_default_config(key_bytes, has_values, n) -> RsConfig:
+    cfg = RsConfig()
+    rc = _call("rs_default_config", key_bytes, int(bool(has_values)), n, _c.byref(cfg))
+    if rc:
+        raise ValueError(STATUS.get(rc, rc))
+    return cfg
+
+
+def rs_config_count(key_bytes, has_values) -> int:
+    return _call("rs_config_count", key_bytes, int(bool(has_values)))
+
+
+def rs_config_get(key_bytes, has_values, i) -> RsConfig:
+    cfg = RsConfig()
+    rc = _call("rs_config_get", key_bytes, int(bool(has_values)), i, _c.byref(cfg))
+    if rc:
+        raise ValueError(STATUS.get(rc, rc))
+    return cfg
+
+
+def rs_workspace_bytes(algo, key_bytes, has_values, n, key_bits, num_buckets, in_place) -> int:
+    return _call("rs_workspace_bytes", algo, key_bytes, int(bool(has_values)), n, key_bits, num_buckets,
+                 int(bool(in_place)))
+
+
+def rs_workspace_bytes_cfg(key_bytes, has_values, n, key_bits, cfg) -> int:
+    return _call("rs_workspace_bytes_cfg", key_bytes, int(bool(has_values)), n, key_bits,
+                 _c.byref(_as_cfg(cfg)))
+
+
+def _as_cfg(cfg):
+    if cfg is None or isinstance(cfg, RsConfig):
+        return cfg
+    return RsConfig(*cfg)
+
+
+def rs_sort_u32(keys_in, keys_out, vals_in, vals_out, n, key_bits, ws, ws_bytes, stream=None) -> int:
+    return _call("rs_sort_u32", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, key_bits, ptr(ws),
+                 ws_bytes, stream_handle(stream))
+
+
+def rs_sort_u64(keys_in, keys_out, vals_in, vals_out, n, key_bits, ws, ws_bytes, stream=None) -> int:
+    return _call("rs_sort_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, key_bits, ptr(ws),
+                 ws_bytes, stream_handle(stream))
+
+
+def rs_sort_u32_ex(keys_in, keys_out, vals_in, vals_out, n, key_bits, ws, ws_bytes, stream=None, cfg=None) -> int:
+    c = _as_cfg(cfg)
+    return _call("rs_sort_u32_ex", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, key_bits, ptr(ws),
+                 ws_bytes, stream_handle(stream), _c.byref(c) if c is not None else None)
+
+
+def rs_sort_u64_ex(keys_in, keys_out, vals_in, vals_out, n, key_bits, ws, ws_bytes, stream=None, cfg=None) -> int:
+    c = _as_cfg(cfg)
+    return _call("rs_sort_u64_ex", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, key_bits, ptr(ws),
+                 ws_bytes, stream_handle(stream), _c.byref(c) if c is not None else None)
+
+
+def rs_digit_counts_u32(keys, n, key_bits, digit_bits, counts_out, ws, ws_bytes, stream=None) -> int:
+    return _call("rs_digit_counts_u32", ptr(keys), n, key_bits, digit_bits, ptr(counts_out), ptr(ws), ws_bytes,
+                 stream_handle(stream))
+
+
+def rs_digit_counts_u64(keys, n, key_bits, digit_bits, counts_out, ws, ws_bytes, stream=None) -> int:
+    return _call("rs_digit_counts_u64", ptr(keys), n, key_bits, digit_bits, ptr(counts_out), ptr(ws), ws_bytes,
+                 stream_handle(stream))
+
+
+def rs_counting_pass_u32(keys_in, keys_out, vals_in, vals_out, n, shift, digit_bits, ws, ws_bytes,
+                         stream=None) -> int:
+    return _call("rs_counting_pass_u32", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, shift,
+                 digit_bits, ptr(ws), ws_bytes, stream_handle(stream))
+
+
+def rs_counting_pass_u64(keys_in, keys_out, vals_in, vals_out, n, shift, digit_bits, ws, ws_bytes,
+                         stream=None) -> int:
+    return _call("rs_counting_pass_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, shift,
+                 digit_bits, ptr(ws), ws_bytes, stream_handle(stream))
+
+
+def rs_get_status(ws, stream=None) -> int:
+    return _call("rs_get_status", ptr(ws), stream_handle(stream))
+
+
+def rs_set_debug(spin_limit: int, stall_tile: int) -> None:
+    _call("rs_set_debug", spin_limit, stall_tile)
+
+
+def rs_profile_enable(enable: bool) -> None:
+    _call("rs_profile_enable", int(bool(enable)))
+
+
+def rs_profile_read(cap: int = 32) -> dict[str, tuple[int, float]]:
+    """{kernel name: (launches, total ms)} of the events recorded since the
+    last read (waits for them)."""
+    arr = (RsKernelStat * cap)()
+    k = _call("rs_profile_read", arr, cap)
+    if k < 0:
+        raise RuntimeError("rs_profile_read: CUDA error while reading events")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(k)}
+
+
+def rs_launch_count() -> int:
+    return int(_call("rs_launch_count"))

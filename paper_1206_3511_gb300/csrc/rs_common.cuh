@@ -1,0 +1,167 @@
+// rs_common.cuh -- helpers shared by the kernels and host code of the sort
+// library: the workspace header, the inter-block status-word encoding,
+// relaxed global loads/stores, block-wide scans and workspace carving.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "rsort.h"
+
+namespace rs {
+
+constexpr uint32_t kFullMask = 0xffffffffu;
+
+// Status words of the decoupled look-back (Merrill & Garland, "Single-pass
+// parallel prefix scan with decoupled look-back", NVIDIA TR 2016).  One 32-bit
+// word per (tile, digit): 2 flag bits and a 30-bit count, stored with a single
+// store so a reader never sees a flag without its count.
+constexpr uint32_t kFlagShift = 30;
+constexpr uint32_t kFlagInvalid = 0u;
+constexpr uint32_t kFlagAggregate = 1u << kFlagShift;  // count = this tile's digit count
+constexpr uint32_t kFlagPrefix = 2u << kFlagShift;     // count = inclusive prefix over tiles
+constexpr uint32_t kCountMask = (1u << kFlagShift) - 1u;
+
+constexpr int kMinDigitBits = 4;
+constexpr int kMaxDigitBits = 11;
+constexpr int kMaxPasses = 16;  // 64-bit keys at 4-bit digits
+
+// First 256 bytes of every workspace.
+struct WsHeader {
+    uint32_t status;        // first device error (RS_OK = none); sticky until rs_get_status
+    uint32_t error_detail;  // tile or key index of that error, for debugging
+    uint32_t reserved0[6];
+    // Everything below is zeroed at the start of every call.
+    uint32_t tile_ctr[kMaxPasses];  // dynamic tile counters, one per pass
+    uint32_t done_ctr[8];           // "last block" counters
+    uint32_t reserved1[64 - 8 - kMaxPasses - 8];
+};
+static_assert(sizeof(WsHeader) == 256, "workspace header must be 256 bytes");
+constexpr size_t kHeaderZeroOffset = 32;  // offsetof(WsHeader, tile_ctr)
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ void set_device_error(WsHeader* h, uint32_t code, uint32_t detail) {
+    if (atomicCAS(&h->status, 0u, code) == 0u) h->error_detail = detail;
+}
+
+template <typename KeyT>
+__device__ __forceinline__ uint32_t digit_of(KeyT k, int shift, uint32_t mask) {
+    return (uint32_t)(k >> shift) & mask;
+}
+
+// Exclusive prefix sum of one value per thread across the block.  s_warp needs
+// BLOCK/32 + 1 words; the block total lands in s_warp[BLOCK/32].  Contains
+// __syncthreads() and must be reached by every thread.
+template <int BLOCK>
+__device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t x, uint32_t* s_warp) {
+    constexpr int kWarps = BLOCK / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFullMask, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kWarps ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFullMask, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < kWarps) s_warp[lane] = wi - w;
+        if (lane == kWarps - 1) s_warp[kWarps] = wi;
+    }
+    __syncthreads();
+    uint32_t r = inc - x + s_warp[warp];
+    __syncthreads();
+    return r;
+}
+
+// In-place exclusive prefix sum of a[0..len) in shared memory; each thread
+// scans a contiguous run of ceil(len/BLOCK) entries.
+template <int BLOCK>
+__device__ __forceinline__ void block_exclusive_scan_smem(uint32_t* a, int len, uint32_t* s_warp) {
+    const int per = (len + BLOCK - 1) / BLOCK;
+    const int start = threadIdx.x * per;
+    uint32_t sum = 0;
+    for (int i = 0; i < per; ++i) {
+        int j = start + i;
+        if (j < len) sum += a[j];
+    }
+    uint32_t run = block_exclusive_sum<BLOCK>(sum, s_warp);
+    for (int i = 0; i < per; ++i) {
+        int j = start + i;
+        if (j < len) {
+            uint32_t v = a[j];
+            a[j] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- host side
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Hands out 256-byte aligned regions of a workspace in order.
+struct Carver {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        size_t o = off;
+        off += align_up(bytes, 256);
+        return o;
+    }
+};
+
+inline bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t bbytes) {
+    if (!a || !b || !abytes || !bbytes) return false;
+    uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bbytes && y < x + abytes;
+}
+
+// Library-wide debug knobs (rs_set_debug).
+uint32_t debug_spin_limit();
+int debug_stall_tile();
+int device_sm_count();
+
+// Wraps one kernel launch: counts it and, while rs_profile_enable(1) is in
+// force, records CUDA events around it on its stream.
+class KernelScope {
+  public:
+    KernelScope(const char* name, cudaStream_t stream);
+    ~KernelScope();
+    KernelScope(const KernelScope&) = delete;
+    KernelScope& operator=(const KernelScope&) = delete;
+
+  private:
+    long slot_;
+    cudaStream_t stream_;
+};
+
+#define RS_CUDA_TRY(expr)                           \
+    do {                                            \
+        cudaError_t _e = (expr);                    \
+        if (_e != cudaSuccess) return RS_ERR_CUDA;  \
+    } while (0)
+
+}  // namespace rs

@@ -1,0 +1,44 @@
+// rs_radix.h -- internal interface of the radix-sort host code, shared with
+// the bucket-sort, segmented-sort and API translation units.
+#pragma once
+
+#include "rs_onesweep.cuh"
+
+namespace rs {
+
+// One compiled shape of the scatter-pass kernel.
+struct Variant {
+    int key_bytes;
+    bool vals;
+    int block;
+    int items;
+    int tile_keys;
+    cudaError_t (*launch)(const PassParams<RadixDigit>&, cudaStream_t);
+};
+
+// Byte offsets of the regions of a radix-sort workspace.
+struct RadixLayout {
+    int digit_bits;
+    int passes;
+    uint32_t bins;
+    uint32_t tile_keys;
+    uint32_t tiles;
+    size_t off_counts, off_scan, off_status[2], off_tmp_keys, off_tmp_vals, total;
+};
+
+RadixLayout radix_layout(int key_bytes, bool vals, size_t n, int key_bits, int digit_bits, int tile_keys,
+                         bool tmp_buffers);
+size_t radix_workspace_bytes(int key_bytes, bool vals, size_t n, int key_bits);
+size_t radix_workspace_bytes_cfg(int key_bytes, bool vals, size_t n, int key_bits, const rs_config& cfg);
+const Variant* find_variant(int key_bytes, bool vals, int block, int items);
+const Variant* default_variant(int key_bytes, bool vals);
+
+rs_status radix_sort_impl(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                          uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
+                          cudaStream_t stream, const rs_config* cfg);
+
+rs_status enqueue_digit_counts(int key_bytes, const void* keys, size_t n, int shift0, int digit_bits, int passes,
+                               int key_bits, uint32_t* counts, uint32_t* scan, uint32_t* zero_ptr,
+                               size_t zero_words, WsHeader* hdr, cudaStream_t stream);
+
+}  // namespace rs

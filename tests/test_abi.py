@@ -1,0 +1,88 @@
+"""CPU-only checks of the C ABI boundary: the library builds for sm_103a,
+loads, and exports every function include/*.h declares; the Python binding
+covers the same names; host-side argument checks work without a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        names += re.findall(r"^RS_API\s+[\w\s\*]+?\b(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1206_3511_gb300 import _build, _lib
+
+    _build.build()
+    return ctypes.CDLL(_lib.LIB_PATH)
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    assert "rs_sort_u32" in names and "rs_sort_u64" in names and "rs_get_status" in names
+    assert len(names) >= 15
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_python_binding_names_match_header():
+    from paper_1206_3511_gb300 import _lib
+
+    assert set(_declared()) == set(_lib.SIGNATURES), set(_declared()) ^ set(_lib.SIGNATURES)
+    for n in _declared():
+        assert callable(getattr(_lib, n)), n
+
+
+def test_host_side_queries_need_no_gpu(lib):
+    from paper_1206_3511_gb300 import _lib
+
+    _lib.load()
+    assert _lib.rs_version() >= 100
+    assert "RS_ERR_WORKSPACE" in _lib.rs_status_string(2)
+    ws = _lib.rs_workspace_bytes(0, 4, 0, 10**8, 32, 0, 0)
+    # header + counts + two status arrays + one 400 MB ping-pong buffer
+    assert 400_000_000 < ws < 500_000_000
+    assert _lib.rs_workspace_bytes(0, 4, 0, 10**8, 33, 0, 0) == 0   # key_bits above the key width
+    assert _lib.rs_workspace_bytes(0, 3, 0, 10, 0, 0, 0) == 0
+    cfg = _lib.rs_default_config(4, 0, 10**8)
+    assert cfg.digit_bits == 8
+    assert _lib.rs_config_count(4, 0) >= 8
+    seen = {_lib.rs_config_get(4, 0, i).as_tuple() for i in range(_lib.rs_config_count(4, 0))}
+    assert len(seen) == _lib.rs_config_count(4, 0)
+
+
+def test_argument_errors_are_returned_before_any_launch(lib):
+    from paper_1206_3511_gb300 import _lib
+
+    _lib.load()
+    fake = 1 << 40  # never dereferenced: every call below fails validation first
+    # vals_in without vals_out
+    assert _lib.rs_sort_u32(fake, fake + 4096, fake, None, 16, 32, fake, 1 << 20, 0) == 1
+    # key_bits out of range
+    assert _lib.rs_sort_u32(fake, fake + 4096, None, None, 16, 33, fake, 1 << 20, 0) == 1
+    # misaligned / missing workspace
+    assert _lib.rs_sort_u32(fake, fake + 4096, None, None, 16, 32, fake + 8, 1 << 20, 0) == 2
+    assert _lib.rs_sort_u32(fake, fake + 4096, None, None, 16, 32, None, 1 << 20, 0) == 2
+    # workspace too small
+    assert _lib.rs_sort_u32(fake, fake + 4096, None, None, 1000, 32, fake + (1 << 30), 64, 0) == 2
+    # partial overlap of input and output
+    assert _lib.rs_sort_u32(fake, fake + 8, None, None, 16, 32, fake + (1 << 30), 1 << 20, 0) == 1
+    # n above the single-sort limit
+    assert _lib.rs_sort_u32(fake, fake + 4096, None, None, (1 << 30) + 1, 32, fake, 1 << 20, 0) == 1
+    # n == 0 is a no-op
+    assert _lib.rs_sort_u32(None, None, None, None, 0, 32, fake, 1 << 20, 0) == 0
+    # a configuration that is not compiled
+    assert _lib.rs_sort_u32_ex(fake, fake + 4096, None, None, 16, 32, fake, 1 << 20, 0, (8, 256, 3)) == 9
