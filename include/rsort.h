@@ -20,7 +20,8 @@
  *     enqueue kernels on `stream` and return.  Argument errors are returned
  *     synchronously and nothing is enqueued.  Errors found on the device (a
  *     key above 2^key_bits, a bounded wait that gave up) are recorded in a
- *     status word inside the workspace; read them with rs_get_status().
+ *     status word inside the workspace; read them with rs_get_status() before
+ *     the next call on that workspace.
  *   - `stream` is a cudaStream_t (0 = the legacy default stream).
  *   - `ws` must be 256-byte aligned and at least rs_workspace_bytes(...)
  *     large.  A workspace may be reused by any number of calls issued on one
@@ -167,11 +168,11 @@ RS_API rs_status rs_counting_pass_u64(const uint64_t* keys_in, uint64_t* keys_ou
  * Device status.
  *
  * rs_get_status: waits for `stream`, then reads and clears the status word
- * kept in the workspace header.  Returns RS_OK if no call that used this
- * workspace since the last rs_get_status recorded a device error, otherwise
- * the first error recorded (RS_ERR_KEY_RANGE, RS_ERR_DEVICE_TIMEOUT), or
- * RS_ERR_CUDA if the stream itself failed.  ws must be a workspace that has
- * been passed to at least one sort call.
+ * kept in the workspace header.  Every call that takes a workspace clears
+ * that word when it starts on the device, so the word describes the most
+ * recent such call: RS_OK, or the first device error it recorded
+ * (RS_ERR_KEY_RANGE, RS_ERR_DEVICE_TIMEOUT).  Returns RS_ERR_CUDA if the
+ * stream itself failed.  ws must have been passed to at least one call.
  */
 RS_API rs_status rs_get_status(const void* ws, rs_stream_t stream);
 

@@ -29,16 +29,15 @@ constexpr int kMaxPasses = 16;  // 64-bit keys at 4-bit digits
 
 // First 256 bytes of every workspace.
 struct WsHeader {
-    uint32_t status;        // first device error (RS_OK = none); sticky until rs_get_status
-    uint32_t error_detail;  // tile or key index of that error, for debugging
+    // The whole header is zeroed at the start of every call.
+    uint32_t status;        // first device error of the last call (RS_OK = none)
+    uint32_t error_detail;  // tile or block index of that error, for debugging
     uint32_t reserved0[6];
-    // Everything below is zeroed at the start of every call.
     uint32_t tile_ctr[kMaxPasses];  // dynamic tile counters, one per pass
     uint32_t done_ctr[8];           // "last block" counters
     uint32_t reserved1[64 - 8 - kMaxPasses - 8];
 };
 static_assert(sizeof(WsHeader) == 256, "workspace header must be 256 bytes");
-constexpr size_t kHeaderZeroOffset = 32;  // offsetof(WsHeader, tile_ctr)
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
     uint32_t v;
@@ -48,6 +47,38 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
 
 __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Shared-memory accesses through 32-bit shared-window addresses, with the
+// predicate inside the instruction (no branch around the access).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void red_or_shared_if(uint32_t addr, uint32_t v, bool pred) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.u32 p, %2, 0; @p red.shared.or.b32 [%0], %1; }" ::"r"(addr), "r"(v),
+        "r"((uint32_t)pred)
+        : "memory");
+}
+
+__device__ __forceinline__ uint2 ld_shared_v2(uint32_t addr) {
+    uint2 r;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(addr) : "memory");
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
+    uint32_t r;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r) : "r"(addr) : "memory");
+    return r;
+}
+
+__device__ __forceinline__ void st_shared_v2_if(uint32_t addr, uint32_t x, uint32_t y, bool pred) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.u32 p, %3, 0; @p st.shared.v2.u32 [%0], {%1, %2}; }" ::"r"(addr), "r"(x), "r"(y),
+        "r"((uint32_t)pred)
+        : "memory");
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

@@ -46,47 +46,62 @@ struct CountParams {
 };
 
 constexpr int kCountBlock = 512;
-constexpr int kCountItems = 16;
+constexpr int kCountVecIters = 8;  // 16-byte loads per thread per chunk
+
+template <typename KeyT>
+__device__ __forceinline__ void count_key(uint32_t* s_cnt, KeyT k, int shift0, int D, int P, uint32_t bins,
+                                          KeyT& seen) {
+    seen |= k;
+    const uint32_t mask = bins - 1u;
+    for (int q = 0; q < P; ++q) atomicAdd(&s_cnt[q * bins + ((uint32_t)(k >> (shift0 + q * D)) & mask)], 1u);
+}
 
 template <typename KeyT>
 __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p) {
     extern __shared__ uint32_t s_cnt[];  // [P][bins], then kCountBlock/32+1 scan words
     __shared__ uint32_t s_last;
-    const uint32_t bins = 1u << p.digit_bits, mask = bins - 1u;
+    const uint32_t bins = 1u << p.digit_bits;
     const int ncnt = p.passes * (int)bins;
     uint32_t* s_scan = s_cnt + ncnt;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     for (int i = tid; i < ncnt; i += kCountBlock) s_cnt[i] = 0;
     for (size_t i = (size_t)blockIdx.x * kCountBlock + tid; i < p.zero_words; i += (size_t)gridDim.x * kCountBlock)
         p.zero_ptr[i] = 0;
     __syncthreads();
 
+    // keys before the first 16-byte boundary and after the last one are
+    // counted one by one; the body in between with 16-byte loads
+    constexpr int kPerVec = 16 / sizeof(KeyT);
     const KeyT* keys = static_cast<const KeyT*>(p.keys);
-    constexpr size_t kChunk = (size_t)kCountBlock * kCountItems;
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
+    size_t head = ((16 - (addr & 15)) & 15) / sizeof(KeyT);
+    if (head > p.n) head = p.n;
+    const size_t nvec = (p.n - head) / kPerVec;
+    const size_t tail0 = head + nvec * kPerVec;
     KeyT seen = 0;
-    for (size_t base = (size_t)blockIdx.x * kChunk; base < p.n; base += (size_t)gridDim.x * kChunk) {
-        const size_t wbase = base + (size_t)warp * (32 * kCountItems) + lane;
-        const bool full = base + kChunk <= p.n;
-        KeyT k[kCountItems];
+    const size_t gthreads = (size_t)gridDim.x * kCountBlock;
+    const size_t gtid = (size_t)blockIdx.x * kCountBlock + tid;
+    for (size_t i = gtid; i < head; i += gthreads)
+        count_key<KeyT>(s_cnt, keys[i], p.shift0, p.digit_bits, p.passes, bins, seen);
+    for (size_t i = tail0 + gtid; i < p.n; i += gthreads)
+        count_key<KeyT>(s_cnt, keys[i], p.shift0, p.digit_bits, p.passes, bins, seen);
+    const uint4* vec = reinterpret_cast<const uint4*>(keys + head);
+    constexpr size_t kChunk = (size_t)kCountBlock * kCountVecIters;
+    for (size_t base = (size_t)blockIdx.x * kChunk; base < nvec; base += (size_t)gridDim.x * kChunk) {
+        uint4 v[kCountVecIters];
 #pragma unroll
-        for (int i = 0; i < kCountItems; ++i) {
-            size_t idx = wbase + (size_t)i * 32;
-            k[i] = (full || idx < p.n) ? __ldcs(keys + idx) : (KeyT)0;
+        for (int j = 0; j < kCountVecIters; ++j) {
+            const size_t idx = base + (size_t)j * kCountBlock + tid;
+            v[j] = idx < nvec ? __ldcs(vec + idx) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
-        for (int i = 0; i < kCountItems; ++i) {
-            const bool valid = full || (wbase + (size_t)i * 32 < p.n);
-            if (valid) seen |= k[i];
-            for (int q = 0; q < p.passes; ++q) {
-                const uint32_t d = (uint32_t)(k[i] >> (p.shift0 + q * p.digit_bits)) & mask;
-                // all 32 lanes on one digit (sorted or narrow-range input):
-                // one shared atomic instead of 32 conflicting ones
-                const uint32_t d0 = __shfl_sync(kFullMask, d, 0);
-                if (__all_sync(kFullMask, valid && d == d0)) {
-                    if (lane == 0) atomicAdd(&s_cnt[q * bins + d], 32u);
-                } else if (valid) {
-                    atomicAdd(&s_cnt[q * bins + d], 1u);
-                }
+        for (int j = 0; j < kCountVecIters; ++j) {
+            const size_t idx = base + (size_t)j * kCountBlock + tid;
+            if (idx < nvec) {
+                const KeyT* kk = reinterpret_cast<const KeyT*>(&v[j]);
+#pragma unroll
+                for (int e = 0; e < kPerVec; ++e)
+                    count_key<KeyT>(s_cnt, kk[e], p.shift0, p.digit_bits, p.passes, bins, seen);
             }
         }
     }
@@ -152,48 +167,123 @@ template <typename KeyT, bool VALS, int BLOCK, int ITEMS>
 struct OnesweepShape {
     static constexpr int kWarps = BLOCK / 32;
     static constexpr int kTile = BLOCK * ITEMS;
-    static_assert(kTile < 65536, "per-warp counters are 16-bit");
+    static_assert(kTile < 65536, "tile offsets are 16-bit");
     static size_t smem_bytes(int digit_bits) {
         const size_t bins = (size_t)1 << digit_bits;
-        size_t b = (size_t)kTile * sizeof(KeyT);
-        if (VALS) b += (size_t)kTile * 4;
-        b += align_up((size_t)kWarps * bins * 2, 16);  // per-warp digit counters (u16)
-        b += bins * 4 * 3;                             // tile counts, local starts, scatter deltas
-        b += (kWarps + 1 + 3) * 4;                     // scan scratch, tile id
+        size_t b = (size_t)kWarps * bins * 8;  // per-warp rank table (64-bit entries)
+        b += (size_t)kTile * sizeof(KeyT);     // staged keys
+        if (VALS) b += (size_t)kTile * 4;      // staged values
+        b += bins * 4 * 2;                     // local starts, scatter deltas
+        b += (kWarps + 1 + 3) * 4;             // scan scratch
         return b;
     }
 };
 
-template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename DigitOp>
-__global__ void __launch_bounds__(BLOCK) k_onesweep(PassParams<DigitOp> p) {
-    using Shape = OnesweepShape<KeyT, VALS, BLOCK, ITEMS>;
-    constexpr int kWarps = Shape::kWarps;
-    constexpr int kTile = Shape::kTile;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const uint32_t bins = 1u << p.digit_bits;
-    KeyT* s_keys = reinterpret_cast<KeyT*>(smem);
-    uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kTile);
-    uint16_t* s_wcnt = reinterpret_cast<uint16_t*>(s_vals + (VALS ? kTile : 0));
-    uint32_t* s_tcnt = reinterpret_cast<uint32_t*>(
-        reinterpret_cast<unsigned char*>(s_wcnt) + align_up((size_t)kWarps * bins * 2, 16));
-    uint32_t* s_local = s_tcnt + bins;
-    uint32_t* s_delta = s_local + bins;
-    uint32_t* s_scan = s_delta + bins;  // kWarps + 1 words
-    uint32_t* s_tile = s_scan + kWarps + 1;
+// Stable rank of one key among the keys of its warp that carry the same
+// digit, in warp order (items in order, lanes in order within an item).
+// Entry d of the warp's table (8 bytes at tab + 8d): low word = peer mask of
+// the item being ranked (built with shared atomic OR, so the mask does not
+// depend on the order in which the hardware applies the ORs), high word =
+// number of keys with digit d in the warp's earlier items.  The highest lane
+// of each peer group advances the count and clears the mask.
+template <bool ALL>
+__device__ __forceinline__ uint32_t warp_rank(uint32_t tab, uint32_t d, bool ok, uint32_t lanebit, uint32_t lt,
+                                              uint32_t gt) {
+    const uint32_t addr = tab + 8u * d;
+    if (ALL)
+        asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(addr), "r"(lanebit) : "memory");
+    else
+        red_or_shared_if(addr, lanebit, ok);
+    __syncwarp();
+    const uint2 e = ld_shared_v2(addr);
+    __syncwarp();
+    const uint32_t peers = (ALL || ok) ? e.x : 0u;
+    st_shared_v2_if(addr, 0u, e.y + __popc(peers), (ALL || ok) && (peers & gt) == 0);
+    __syncwarp();
+    return e.y + __popc(peers & lt);
+}
 
+// Decoupled look-back for one digit: the number of keys with digit d in all
+// tiles before `tile`.  The status words of kLookbackWindow earlier tiles are
+// read per round trip (independent loads); their counts are added from the
+// nearest tile backwards until the first inclusive prefix.  A tile whose word
+// is still invalid is waited for (bounded: after spin_limit polls the error is
+// recorded and the partial sum, which never exceeds the true prefix, is
+// returned).  The first window can be fetched early (lookback_fetch) and
+// consumed later (lookback_finish) so that its latency overlaps other work.
+constexpr int kLookbackWindow = 4;
+
+struct LookbackWindow {
+    uint32_t w[kLookbackWindow];
+};
+
+__device__ __forceinline__ LookbackWindow lookback_fetch(const uint32_t* status, int t, uint32_t bins, uint32_t d) {
+    LookbackWindow lw;
+#pragma unroll
+    for (int j = 0; j < kLookbackWindow; ++j)
+        lw.w[j] = (t - j >= 0) ? ld_relaxed(status + (size_t)(t - j) * bins + d) : kFlagPrefix;
+    return lw;
+}
+
+__device__ __forceinline__ uint32_t lookback_finish(LookbackWindow lw, const uint32_t* status, uint32_t tile,
+                                                    uint32_t bins, uint32_t d, uint32_t spin_limit, WsHeader* hdr) {
+    uint32_t excl = 0;
+    int t = (int)tile - 1;  // nearest tile not yet added
+    uint32_t polls = 0;
+    while (t >= 0) {
+        bool done = false, blocked = false;
+        int used = 0;
+#pragma unroll
+        for (int j = 0; j < kLookbackWindow; ++j) {
+            if (!done && !blocked) {
+                const uint32_t flag = lw.w[j] & ~kCountMask;
+                if (flag == kFlagInvalid) {
+                    blocked = true;
+                } else {
+                    excl += lw.w[j] & kCountMask;
+                    ++used;
+                    done = flag == kFlagPrefix;
+                }
+            }
+        }
+        if (done) break;
+        t -= used;
+        if (blocked) {
+            if (++polls > spin_limit) {
+                set_device_error(hdr, RS_ERR_DEVICE_TIMEOUT, tile);
+                break;
+            }
+            if (polls > 8) __nanosleep(polls < 256 ? 64 : 512);
+        }
+        if (t >= 0) lw = lookback_fetch(status, t, bins, d);
+    }
+    return excl;
+}
+
+__device__ __forceinline__ uint32_t lookback_digit(const uint32_t* status, uint32_t tile, uint32_t bins, uint32_t d,
+                                                   uint32_t spin_limit, WsHeader* hdr) {
+    return lookback_finish(lookback_fetch(status, (int)tile - 1, bins, d), status, tile, bins, d, spin_limit, hdr);
+}
+
+// Shared-memory layout of one scatter-pass block.
+template <typename KeyT>
+struct PassSmem {
+    unsigned long long* tab;  // [warps][bins] rank table, later warp offsets (low words)
+    KeyT* keys;               // [tile] staged keys
+    uint32_t* vals;           // [tile] staged values
+    uint32_t* local;          // [bins] start of each digit inside the staged tile
+    uint32_t* delta;          // [bins] global position minus staged position
+    uint32_t* scan;           // [warps + 1] block-scan scratch
+};
+
+// The body of the pass for one tile; FULL tiles skip every bounds check.
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, bool FULL, typename DigitOp>
+__device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, const PassSmem<KeyT>& sm, uint32_t tile,
+                                              uint32_t tile_n, uint32_t bins, bool publish) {
+    constexpr int kWarps = BLOCK / 32;
+    constexpr int kTile = BLOCK * ITEMS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (uint32_t i = tid; i < (uint32_t)kWarps * bins; i += BLOCK) s_wcnt[i] = 0;
-    if (tid == 0) *s_tile = atomicAdd(p.tile_ctr, 1u);
-    __syncthreads();
-    const uint32_t tile = *s_tile;
-    if (tile >= p.num_tiles) return;  // uniform across the block
-    const bool publish = (int)tile != p.stall_tile;
-    if (p.status_next)
-        for (uint32_t d = tid; d < bins; d += BLOCK) p.status_next[(size_t)tile * bins + d] = 0u;
-
     const uint32_t tile_base = tile * (uint32_t)kTile;
-    const uint32_t tile_n = min((uint32_t)kTile, p.n - tile_base);
-    const bool full = tile_n == (uint32_t)kTile;
 
     // load: warp w owns keys [w*ITEMS*32, (w+1)*ITEMS*32) of the tile, lane l
     // holds item i = key w*ITEMS*32 + i*32 + l (warp-striped, coalesced)
@@ -204,89 +294,70 @@ __global__ void __launch_bounds__(BLOCK) k_onesweep(PassParams<DigitOp> p) {
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const uint32_t idx = wofs + i * 32;
-        const bool ok = full || idx < tile_n;
+        const bool ok = FULL || idx < tile_n;
         k[i] = ok ? kin[idx] : (KeyT)0;
         if (VALS) v[i] = ok ? p.vals_in[tile_base + idx] : 0u;
     }
 
-    // stable rank inside the warp: lanes with equal digits form one peer
-    // group; the group's last lane bumps the warp's counter for that digit
-    uint16_t* wc = s_wcnt + warp * bins;
-    uint32_t rank[ITEMS];
+    // rank every key inside its warp; keep (digit << 16 | rank) per item
+    const uint32_t tab = smem_addr(sm.tab + (size_t)warp * bins);
     const uint32_t lt = lanemask_lt();
+    const uint32_t lanebit = 1u << lane;
+    const uint32_t gt = ~(lt | lanebit);
+    uint32_t dr[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const bool ok = full || (wofs + i * 32) < tile_n;
-        const uint32_t d = ok ? p.op(k[i]) : bins;  // padding lanes group apart
-        const uint32_t peers = __match_any_sync(kFullMask, d);
-        const int leader = 31 - __clz(peers);
-        uint32_t before = 0;
-        if (lane == leader && ok) {
-            before = wc[d];
-            wc[d] = (uint16_t)(before + __popc(peers));
-        }
-        before = __shfl_sync(kFullMask, before, leader);
-        rank[i] = before + __popc(peers & lt);
-        __syncwarp();
+        const bool ok = FULL || (wofs + i * 32) < tile_n;
+        const uint32_t d = p.op(k[i]);
+        dr[i] = (d << 16) | warp_rank<FULL>(tab, d, ok, lanebit, lt, gt);
     }
     __syncthreads();
 
-    // per digit: warp-exclusive prefixes, tile count, publish the count
+    // per digit: tile count, publish it, then each warp's offset inside the
+    // tile (kept in the low word of the rank table)
     uint32_t* srow = p.status + (size_t)tile * bins;
     for (uint32_t d = tid; d < bins; d += BLOCK) {
         uint32_t sum = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = s_wcnt[w * bins + d];
-            s_wcnt[w * bins + d] = (uint16_t)sum;
-            sum += c;
-        }
-        s_tcnt[d] = sum;
-        s_local[d] = sum;
+        for (int w = 0; w < kWarps; ++w) sum += (uint32_t)(sm.tab[(size_t)w * bins + d] >> 32);
+        sm.local[d] = sum;
         if (publish) st_relaxed(srow + d, (tile == 0 ? kFlagPrefix : kFlagAggregate) | sum);
     }
+    // decoupled look-back right away, so this tile's inclusive prefix is
+    // published as early as possible; sm.delta holds the global start of d
+    for (uint32_t d = tid; d < bins; d += BLOCK) {
+        const uint32_t excl = tile == 0 ? 0u : lookback_digit(p.status, tile, bins, d, p.spin_limit, p.hdr);
+        if (tile != 0 && publish) st_relaxed(srow + d, kFlagPrefix | ((excl + sm.local[d]) & kCountMask));
+        sm.delta[d] = p.digit_base[d] + excl;
+    }
     __syncthreads();
-    block_exclusive_scan_smem<BLOCK>(s_local, (int)bins, s_scan);
+    block_exclusive_scan_smem<BLOCK>(sm.local, (int)bins, sm.scan);
+    for (uint32_t d = tid; d < bins; d += BLOCK) {
+        uint32_t run = sm.local[d];
+        sm.delta[d] -= run;
+        uint32_t* low = reinterpret_cast<uint32_t*>(sm.tab + d);
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = low[2 * (size_t)w * bins + 1];
+            low[2 * (size_t)w * bins] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
 
     // stage the tile in shared memory in digit order
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const bool ok = full || (wofs + i * 32) < tile_n;
+        const bool ok = FULL || (wofs + i * 32) < tile_n;
         if (ok) {
-            const uint32_t d = p.op(k[i]);
-            const uint32_t pos = s_local[d] + wc[d] + rank[i];
+            const uint32_t pos = ld_shared_u32(tab + 8u * (dr[i] >> 16)) + (dr[i] & 0xffffu);
             if (pos < (uint32_t)kTile) {
-                s_keys[pos] = k[i];
-                if (VALS) s_vals[pos] = v[i];
+                sm.keys[pos] = k[i];
+                if (VALS) sm.vals[pos] = v[i];
             }
         }
     }
 
-    // decoupled look-back: count of digit d in all earlier tiles
-    for (uint32_t d = tid; d < bins; d += BLOCK) {
-        uint32_t excl = 0;
-        if (tile != 0) {
-            int t = (int)tile - 1;
-            uint32_t polls = 0;
-            while (true) {
-                const uint32_t s = ld_relaxed(p.status + (size_t)t * bins + d);
-                const uint32_t flag = s & ~kCountMask;
-                if (flag == kFlagInvalid) {
-                    if (++polls > p.spin_limit) {
-                        set_device_error(p.hdr, RS_ERR_DEVICE_TIMEOUT, tile);
-                        break;  // partial prefix <= true prefix: writes stay in bounds
-                    }
-                    if (polls > 16) __nanosleep(polls < 256 ? 64 : 512);
-                    continue;
-                }
-                excl += s & kCountMask;
-                if (flag == kFlagPrefix || t == 0) break;
-                --t;
-            }
-            if (publish) st_relaxed(srow + d, kFlagPrefix | ((excl + s_tcnt[d]) & kCountMask));
-        }
-        s_delta[d] = p.digit_base[d] + excl - s_local[d];
-    }
     __syncthreads();
 
     // write runs of equal digits to their global places
@@ -294,15 +365,46 @@ __global__ void __launch_bounds__(BLOCK) k_onesweep(PassParams<DigitOp> p) {
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const uint32_t idx = j * BLOCK + tid;
-        if (full || idx < tile_n) {
-            const KeyT key = s_keys[idx];
-            const uint32_t pos = s_delta[p.op(key)] + idx;
+        if (FULL || idx < tile_n) {
+            const KeyT key = sm.keys[idx];
+            const uint32_t pos = sm.delta[p.op(key)] + idx;
             if (pos < p.n) {
                 kout[pos] = key;
-                if (VALS) p.vals_out[pos] = s_vals[idx];
+                if (VALS) p.vals_out[pos] = sm.vals[idx];
             }
         }
     }
+}
+
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB, typename DigitOp>
+__global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p) {
+    constexpr int kWarps = BLOCK / 32;
+    constexpr int kTile = BLOCK * ITEMS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_tile;
+    const uint32_t bins = 1u << p.digit_bits;
+    PassSmem<KeyT> sm;
+    sm.tab = reinterpret_cast<unsigned long long*>(smem);
+    sm.keys = reinterpret_cast<KeyT*>(sm.tab + (size_t)kWarps * bins);
+    sm.vals = reinterpret_cast<uint32_t*>(sm.keys + kTile);
+    sm.local = sm.vals + (VALS ? kTile : 0);
+    sm.delta = sm.local + bins;
+    sm.scan = sm.delta + bins;
+
+    const int tid = threadIdx.x;
+    for (uint32_t i = tid; i < (uint32_t)kWarps * bins; i += BLOCK) sm.tab[i] = 0ull;
+    if (tid == 0) s_tile = atomicAdd(p.tile_ctr, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= p.num_tiles) return;  // uniform across the block
+    const bool publish = (int)tile != p.stall_tile;
+    if (p.status_next)
+        for (uint32_t d = tid; d < bins; d += BLOCK) p.status_next[(size_t)tile * bins + d] = 0u;
+    const uint32_t tile_n = min((uint32_t)kTile, p.n - tile * (uint32_t)kTile);
+    if (tile_n == (uint32_t)kTile)
+        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, true>(p, sm, tile, tile_n, bins, publish);
+    else
+        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, false>(p, sm, tile, tile_n, bins, publish);
 }
 
 }  // namespace rs

@@ -10,15 +10,17 @@ namespace rs {
 
 namespace {
 
-template <typename KeyT, bool VALS, int BLOCK, int ITEMS>
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB>
 cudaError_t launch_pass(const PassParams<RadixDigit>& p, cudaStream_t s) {
     using Shape = OnesweepShape<KeyT, VALS, BLOCK, ITEMS>;
-    auto kern = k_onesweep<KeyT, VALS, BLOCK, ITEMS, RadixDigit>;
+    auto kern = k_onesweep<KeyT, VALS, BLOCK, ITEMS, MINB, RadixDigit>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)Shape::smem_bytes(kMaxDigitBits));
+        size_t most = 0;
+        for (int D = kMinDigitBits; D <= kMaxDigitBits; ++D)
+            if (Shape::smem_bytes(D) <= kMaxSmemPerBlock && Shape::smem_bytes(D) > most) most = Shape::smem_bytes(D);
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     });
     if (attr_err != cudaSuccess) return attr_err;
     KernelScope scope("onesweep_pass", s);
@@ -26,30 +28,29 @@ cudaError_t launch_pass(const PassParams<RadixDigit>& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <typename KeyT, bool VALS, int BLOCK, int ITEMS>
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB = 1024 / BLOCK>
 constexpr Variant make_variant() {
     return Variant{(int)sizeof(KeyT), VALS, BLOCK, ITEMS, BLOCK * ITEMS,
-                   &launch_pass<KeyT, VALS, BLOCK, ITEMS>};
+                   &launch_pass<KeyT, VALS, BLOCK, ITEMS, MINB>, &OnesweepShape<KeyT, VALS, BLOCK, ITEMS>::smem_bytes};
 }
 
 // Compiled kernel shapes.  The first entry of each (key width, values) group
 // is the default.
 const Variant kVariants[] = {
-    make_variant<uint32_t, false, 256, 15>(),
-    make_variant<uint32_t, false, 512, 15>(),
-    make_variant<uint32_t, false, 256, 20>(),
-    make_variant<uint32_t, true, 256, 12>(),
-    make_variant<uint32_t, true, 256, 15>(),
-    make_variant<uint64_t, false, 256, 12>(),
-    make_variant<uint64_t, false, 256, 9>(),
-    make_variant<uint64_t, true, 256, 10>(),
-    make_variant<uint64_t, true, 256, 8>(),
+    make_variant<uint32_t, false, 256, 18, 4>(),
+    make_variant<uint32_t, false, 256, 15, 4>(),
+    make_variant<uint32_t, false, 384, 16, 3>(),
+    make_variant<uint32_t, false, 512, 15, 2>(),
+    make_variant<uint32_t, true, 256, 12, 4>(),
+    make_variant<uint32_t, true, 256, 15, 3>(),
+    make_variant<uint64_t, false, 256, 12, 4>(),
+    make_variant<uint64_t, false, 256, 9, 4>(),
+    make_variant<uint64_t, true, 256, 10, 3>(),
+    make_variant<uint64_t, true, 256, 8, 4>(),
 };
-constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr int kDefaultDigitBits = 8;
 // digit widths offered to an autotuner for every kernel shape
 constexpr int kTuneDigitBits[] = {8, 4, 5, 6, 7, 9, 10, 11};
-constexpr int kNumTuneDigitBits = sizeof(kTuneDigitBits) / sizeof(kTuneDigitBits[0]);
 
 template <typename KeyT>
 cudaError_t launch_counts(const CountParams& p, size_t grid, cudaStream_t s) {
@@ -67,7 +68,7 @@ cudaError_t launch_counts(const CountParams& p, size_t grid, cudaStream_t s) {
 }
 
 size_t count_grid(size_t n) {
-    const size_t chunk = (size_t)kCountBlock * kCountItems;
+    const size_t chunk = (size_t)kCountBlock * kCountVecIters * 4;
     size_t g = (n + chunk - 1) / chunk;
     size_t cap = (size_t)device_sm_count() * 4;
     if (g > cap) g = cap;
@@ -148,7 +149,8 @@ rs_status resolve_config(int key_bytes, bool vals, const rs_config* cfg, const V
     if (cfg->digit_bits < kMinDigitBits || cfg->digit_bits > kMaxDigitBits) return RS_ERR_INVALID_ARG;
     *var = find_variant(key_bytes, vals, cfg->block_threads, cfg->items_per_thread);
     *digit_bits = cfg->digit_bits;
-    return *var ? RS_OK : RS_ERR_UNSUPPORTED;
+    if (!*var || (*var)->smem_bytes(cfg->digit_bits) > kMaxSmemPerBlock) return RS_ERR_UNSUPPORTED;
+    return RS_OK;
 }
 
 // Enqueue the digit-count kernel: counts (and their prefixes, if scan != null)
@@ -212,7 +214,7 @@ rs_status radix_sort_impl(int key_bytes, const void* keys_in, void* keys_out, co
     uint32_t* tmpv = vals ? reinterpret_cast<uint32_t*>(base + L.off_tmp_vals) : nullptr;
 
     // zero the per-call part of the header and the counts
-    RS_CUDA_TRY(cudaMemsetAsync(base + kHeaderZeroOffset, 0, sizeof(WsHeader) - kHeaderZeroOffset, stream));
+    RS_CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(WsHeader), stream));
     RS_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)L.passes * L.bins * 4, stream));
 
     const int P = L.passes;
@@ -288,7 +290,7 @@ rs_status counting_pass_impl(int key_bytes, const void* keys_in, void* keys_out,
     uint32_t* counts = reinterpret_cast<uint32_t*>(base + L.off_counts);
     uint32_t* scan = reinterpret_cast<uint32_t*>(base + L.off_scan);
     uint32_t* status = reinterpret_cast<uint32_t*>(base + L.off_status[0]);
-    RS_CUDA_TRY(cudaMemsetAsync(base + kHeaderZeroOffset, 0, sizeof(WsHeader) - kHeaderZeroOffset, stream));
+    RS_CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(WsHeader), stream));
     RS_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)L.bins * 4, stream));
     rs_status st = enqueue_digit_counts(key_bytes, keys_in, n, shift, digit_bits, 1, width, counts, scan, status,
                                         (size_t)L.tiles * L.bins, hdr, stream);
@@ -325,8 +327,7 @@ rs_status digit_counts_impl(int key_bytes, const void* keys, size_t n, int key_b
     if (ws_bytes < sizeof(WsHeader)) return RS_ERR_WORKSPACE;
     const int P = (key_bits + digit_bits - 1) / digit_bits;
     WsHeader* hdr = static_cast<WsHeader*>(ws);
-    RS_CUDA_TRY(cudaMemsetAsync(reinterpret_cast<unsigned char*>(ws) + kHeaderZeroOffset, 0,
-                                sizeof(WsHeader) - kHeaderZeroOffset, stream));
+    RS_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(WsHeader), stream));
     RS_CUDA_TRY(cudaMemsetAsync(counts_out, 0, (size_t)P * ((size_t)1 << digit_bits) * 4, stream));
     if (n == 0) return RS_OK;
     return enqueue_digit_counts(key_bytes, keys, n, 0, digit_bits, P, key_bits, counts_out, nullptr, nullptr, 0,
@@ -396,17 +397,29 @@ rs_status rs_default_config(int key_bytes, int has_values, size_t n, rs_config* 
 
 int rs_config_count(int key_bytes, int has_values) {
     if (key_bytes != 4 && key_bytes != 8) return 0;
-    return variant_count(key_bytes, has_values != 0) * kNumTuneDigitBits;
+    int c = 0;
+    for (int vi = 0; vi < variant_count(key_bytes, has_values != 0); ++vi) {
+        const Variant* v = variant_at(key_bytes, has_values != 0, vi);
+        for (int D : kTuneDigitBits) c += v->smem_bytes(D) <= kMaxSmemPerBlock;
+    }
+    return c;
 }
 
 rs_status rs_config_get(int key_bytes, int has_values, int i, rs_config* out) {
     if ((key_bytes != 4 && key_bytes != 8) || !out || i < 0) return RS_ERR_INVALID_ARG;
-    const Variant* v = variant_at(key_bytes, has_values != 0, i / kNumTuneDigitBits);
-    if (!v) return RS_ERR_INVALID_ARG;
-    out->digit_bits = kTuneDigitBits[i % kNumTuneDigitBits];
-    out->block_threads = v->block;
-    out->items_per_thread = v->items;
-    return RS_OK;
+    for (int vi = 0; vi < variant_count(key_bytes, has_values != 0); ++vi) {
+        const Variant* v = variant_at(key_bytes, has_values != 0, vi);
+        for (int D : kTuneDigitBits) {
+            if (v->smem_bytes(D) > kMaxSmemPerBlock) continue;
+            if (i-- == 0) {
+                out->digit_bits = D;
+                out->block_threads = v->block;
+                out->items_per_thread = v->items;
+                return RS_OK;
+            }
+        }
+    }
+    return RS_ERR_INVALID_ARG;
 }
 
 }  // extern "C"

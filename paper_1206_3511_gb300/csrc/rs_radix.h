@@ -14,7 +14,11 @@ struct Variant {
     int items;
     int tile_keys;
     cudaError_t (*launch)(const PassParams<RadixDigit>&, cudaStream_t);
+    size_t (*smem_bytes)(int digit_bits);
 };
+
+// Shared memory a block may use on sm_103a (opt-in maximum).
+constexpr size_t kMaxSmemPerBlock = 227 * 1024;
 
 // Byte offsets of the regions of a radix-sort workspace.
 struct RadixLayout {
