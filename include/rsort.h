@@ -165,6 +165,30 @@ RS_API rs_status rs_counting_pass_u64(const uint64_t* keys_in, uint64_t* keys_ou
                                size_t ws_bytes, rs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Sorting without a caller-provided workspace.  The paper has no counterpart:
+ * this exists for callers that cannot allocate device memory (code running
+ * where cudaMalloc is not allowed or not available, or that cannot own an
+ * extra buffer).
+ *
+ * rs_sort_u32_noalloc: same result as rs_sort_u32 (stable LSD radix sort of
+ * uint32 keys, optional uint32 values, key_bits 0..32), but its scratch is a
+ * fixed 9 MiB array inside the library's device memory, so the call allocates
+ * nothing.  Every GPU that loads the library holds that array until the
+ * process exits.  n must be <= RS_NOALLOC_MAX_KEYS, otherwise
+ * RS_ERR_INVALID_ARG is returned and nothing is enqueued.  All calls share
+ * the one array: calls that overlap on the GPU (other streams, or unordered
+ * host threads) race and give wrong results.  The first call on each device
+ * looks up the array's device address; make it before any stream capture on
+ * that device.  Device-side errors of these calls (a key above 2^key_bits, a
+ * bounded wait that gave up) are recorded in the shared array and are not
+ * readable through this API; use rs_sort_u32 with a workspace when they
+ * matter.  Argument rules otherwise as rs_sort_u32.
+ */
+#define RS_NOALLOC_MAX_KEYS ((size_t)1 << 20)
+RS_API rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
+                                     uint32_t* vals_out, size_t n, int key_bits, rs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Device status.
  *
  * rs_get_status: waits for `stream`, then reads and clears the status word

@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import (RS_ALGO_BUCKET, RS_ALGO_RADIX, STATUS, RsConfig, load, rs_config_count, rs_config_get,
                    rs_counting_pass_u32, rs_counting_pass_u64, rs_default_config, rs_digit_counts_u32,
                    rs_digit_counts_u64, rs_get_status, rs_launch_count, rs_profile_enable, rs_profile_read,
-                   rs_set_debug, rs_sort_u32, rs_sort_u32_ex, rs_sort_u64,
+                   rs_set_debug, rs_sort_u32, rs_sort_u32_ex, rs_sort_u32_noalloc, rs_sort_u64,
                    rs_sort_u64_ex, rs_status_string, rs_version, rs_workspace_bytes, rs_workspace_bytes_cfg)
 
 __all__ = [
@@ -26,7 +26,7 @@ __all__ = [
     "rs_digit_counts_u64", "rs_counting_pass_u32", "rs_counting_pass_u64", "rs_get_status", "rs_set_debug",
     "rs_status_string", "rs_version", "rs_workspace_bytes", "rs_workspace_bytes_cfg", "rs_default_config",
     "rs_config_count", "rs_config_get", "RsConfig", "RS_ALGO_RADIX", "RS_ALGO_BUCKET", "STATUS",
-    "rs_profile_enable", "rs_profile_read", "rs_launch_count",
+    "rs_profile_enable", "rs_profile_read", "rs_launch_count", "rs_sort_u32_noalloc",
 ]
 
 

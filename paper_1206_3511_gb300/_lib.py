@@ -53,6 +53,7 @@ SIGNATURES: dict[str, tuple] = {
     "rs_digit_counts_u64": (_I, [_P, _SZ, _I, _I, _P, _P, _SZ, _P]),
     "rs_counting_pass_u32": (_I, [_P, _P, _P, _P, _SZ, _I, _I, _P, _SZ, _P]),
     "rs_counting_pass_u64": (_I, [_P, _P, _P, _P, _SZ, _I, _I, _P, _SZ, _P]),
+    "rs_sort_u32_noalloc": (_I, [_P, _P, _P, _P, _SZ, _I, _P]),
     "rs_get_status": (_I, [_P, _P]),
     "rs_set_debug": (None, [_U32, _I]),
     "rs_profile_enable": (None, [_I]),
@@ -199,6 +200,17 @@ def rs_counting_pass_u64(keys_in, keys_out, vals_in, vals_out, n, shift, digit_b
                          stream=None) -> int:
     return _call("rs_counting_pass_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, shift,
                  digit_bits, ptr(ws), ws_bytes, stream_handle(stream))
+
+
+RS_NOALLOC_MAX_KEYS = 1 << 20
+
+
+def rs_sort_u32_noalloc(keys_in, keys_out, vals_in, vals_out, n, key_bits, stream=None) -> int:
+    """rs_sort_u32 for callers that cannot allocate: the scratch is a fixed
+    array inside the library (n <= RS_NOALLOC_MAX_KEYS; calls must not
+    overlap on the GPU)."""
+    return _call("rs_sort_u32_noalloc", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, key_bits,
+                 stream_handle(stream))
 
 
 def rs_get_status(ws, stream=None) -> int:
