@@ -165,6 +165,30 @@ RS_API rs_status rs_counting_pass_u64(const uint64_t* keys_in, uint64_t* keys_ou
                                size_t ws_bytes, rs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Segmented sort: many independent arrays in one call.  Segment s is
+ * [d_seg_offsets[s], d_seg_offsets[s+1]) of the key (and value) arrays; each
+ * segment is sorted as rs_sort_u32/u64 would sort it alone (Algorithm 4 per
+ * segment, stable).  d_seg_offsets: DEVICE array of nseg+1 nondecreasing
+ * uint64 offsets with d_seg_offsets[nseg] = n_total <= the length of the
+ * arrays; a segment may be empty; one segment may hold at most
+ * RS_MAX_KEYS - 1 keys.  Segments of up to 4096 keys are sorted inside one
+ * thread block in shared memory, larger ones by segmented scatter passes; the
+ * classification is done on the device, so the call never waits for the GPU.
+ * An offsets table that decreases or has a segment above the limit is
+ * reported as RS_ERR_INVALID_ARG by rs_get_status() (output unspecified).
+ * Workspace: rs_segmented_workspace_bytes(key_bytes, has_values, n_total,
+ * nseg, key_bits).  In place (keys_out == keys_in) is allowed.
+ */
+RS_API size_t rs_segmented_workspace_bytes(int key_bytes, int has_values, size_t n_total, size_t nseg,
+                                           int key_bits);
+RS_API rs_status rs_sort_segmented_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
+                                       uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg,
+                                       size_t n_total, int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream);
+RS_API rs_status rs_sort_segmented_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
+                                       uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg,
+                                       size_t n_total, int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Sorting without a caller-provided workspace.  The paper has no counterpart:
  * this exists for callers that cannot allocate device memory (code running
  * where cudaMalloc is not allowed or not available, or that cannot own an

@@ -14,7 +14,8 @@ bits are sorted as unsigned).  Values are 32-bit (uint32 or int32).
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (RS_ALGO_BUCKET, RS_ALGO_RADIX, STATUS, RsConfig, load, rs_config_count, rs_config_get,
+from ._lib import (rs_segmented_workspace_bytes, rs_sort_segmented_u32, rs_sort_segmented_u64,
+                   RS_ALGO_BUCKET, RS_ALGO_RADIX, STATUS, RsConfig, load, rs_config_count, rs_config_get,
                    rs_counting_pass_u32, rs_counting_pass_u64, rs_default_config, rs_digit_counts_u32,
                    rs_digit_counts_u64, rs_get_status, rs_launch_count, rs_profile_enable, rs_profile_read,
                    rs_set_debug, rs_sort_u32, rs_sort_u32_ex, rs_sort_u32_noalloc, rs_sort_u64,
@@ -27,6 +28,7 @@ __all__ = [
     "rs_status_string", "rs_version", "rs_workspace_bytes", "rs_workspace_bytes_cfg", "rs_default_config",
     "rs_config_count", "rs_config_get", "RsConfig", "RS_ALGO_RADIX", "RS_ALGO_BUCKET", "STATUS",
     "rs_profile_enable", "rs_profile_read", "rs_launch_count", "rs_sort_u32_noalloc",
+    "rs_segmented_workspace_bytes", "rs_sort_segmented_u32", "rs_sort_segmented_u64", "segmented_sort",
 ]
 
 
@@ -127,3 +129,24 @@ def digit_counts(keys, key_bits: int = 0, digit_bits: int = 8, ws=None, stream=N
 def get_status(ws, stream=None) -> int:
     """Read and clear the device status word of a workspace (syncs the stream)."""
     return rs_get_status(ws, stream)
+
+
+def segmented_sort(keys, offsets, values=None, key_bits: int = 0, out=None, out_values=None, ws=None, stream=None):
+    """Sort every segment [offsets[s], offsets[s+1]) of a 1-D CUDA tensor on
+    its own (rs_sort_segmented_u32/u64).  offsets: int64/uint64 CUDA tensor of
+    nseg+1 entries.  Returns (keys, values or None)."""
+    import torch
+
+    _check_tensor(keys, "keys")
+    _check_tensor(offsets, "offsets")
+    kb = key_bytes_of(keys)
+    n = keys.numel()
+    nseg = offsets.numel() - 1
+    out = torch.empty_like(keys) if out is None else out
+    if values is not None and out_values is None:
+        out_values = torch.empty_like(values)
+    if ws is None:
+        ws = workspace(rs_segmented_workspace_bytes(kb, values is not None, n, max(nseg, 1), key_bits), keys.device)
+    fn = rs_sort_segmented_u32 if kb == 4 else rs_sort_segmented_u64
+    check(fn(keys, out, values, out_values, offsets, nseg, n, key_bits, ws, ws.numel(), stream), "rs_sort_segmented")
+    return out, out_values

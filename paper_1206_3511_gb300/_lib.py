@@ -53,6 +53,9 @@ SIGNATURES: dict[str, tuple] = {
     "rs_digit_counts_u64": (_I, [_P, _SZ, _I, _I, _P, _P, _SZ, _P]),
     "rs_counting_pass_u32": (_I, [_P, _P, _P, _P, _SZ, _I, _I, _P, _SZ, _P]),
     "rs_counting_pass_u64": (_I, [_P, _P, _P, _P, _SZ, _I, _I, _P, _SZ, _P]),
+    "rs_segmented_workspace_bytes": (_SZ, [_I, _I, _SZ, _SZ, _I]),
+    "rs_sort_segmented_u32": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P]),
+    "rs_sort_segmented_u64": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P]),
     "rs_sort_u32_noalloc": (_I, [_P, _P, _P, _P, _SZ, _I, _P]),
     "rs_get_status": (_I, [_P, _P]),
     "rs_set_debug": (None, [_U32, _I]),
@@ -200,6 +203,22 @@ def rs_counting_pass_u64(keys_in, keys_out, vals_in, vals_out, n, shift, digit_b
                          stream=None) -> int:
     return _call("rs_counting_pass_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, shift,
                  digit_bits, ptr(ws), ws_bytes, stream_handle(stream))
+
+
+def rs_segmented_workspace_bytes(key_bytes, has_values, n_total, nseg, key_bits) -> int:
+    return _call("rs_segmented_workspace_bytes", key_bytes, int(bool(has_values)), n_total, nseg, key_bits)
+
+
+def rs_sort_segmented_u32(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, key_bits, ws, ws_bytes,
+                          stream=None) -> int:
+    return _call("rs_sort_segmented_u32", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out),
+                 ptr(d_seg_offsets), nseg, n_total, key_bits, ptr(ws), ws_bytes, stream_handle(stream))
+
+
+def rs_sort_segmented_u64(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, key_bits, ws, ws_bytes,
+                          stream=None) -> int:
+    return _call("rs_sort_segmented_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out),
+                 ptr(d_seg_offsets), nseg, n_total, key_bits, ptr(ws), ws_bytes, stream_handle(stream))
 
 
 RS_NOALLOC_MAX_KEYS = 1 << 20

@@ -1,0 +1,107 @@
+// rs_bucket.cuh -- the bucket function of the bucket sort (Sec. 2.3,
+// Algorithm 2) on the device, and the digit views of it that the counting,
+// scatter and shared-memory kernels use.
+//
+// The bucket of key k among nb buckets covering [min, max] is
+//     b(k) = floor((k - min) * nb / (max - min + 1)),
+// computed exactly: it is the paper's n * A[i] / M with the key range made
+// inclusive and kept inside [0, nb - 1].  b is nondecreasing in k, so sorting
+// by (bucket, key) is sorting by key.
+#pragma once
+
+#include "rs_segmented.cuh"
+
+namespace rs {
+
+struct BucketParams {
+    uint64_t min;    // lowest key of the range
+    uint64_t max;    // highest key of the range
+    uint64_t nb;     // number of buckets
+    uint64_t range;  // max - min + 1; 0 stands for 2^64
+    uint64_t recip;  // floor((2^64 - 1) / range) when range <= 2^32
+    uint32_t bbits;  // bit length of nb - 1 (0 when nb == 1)
+    uint32_t valid;  // 1 once the parameters are set
+};
+
+// Exact floor((k - min) * nb / range).
+//   32-bit keys: x = (k - min) * nb < 2^64 and range <= 2^32; the estimate
+//   q = mulhi(x, floor((2^64-1)/range)) is at most 2 below the quotient
+//   (division by an invariant integer through a precomputed reciprocal,
+//   Granlund & Montgomery 1994), and the remainder test corrects it.
+//   64-bit keys: 128-bit product divided exactly; range 2^64 is a plain
+//   high product.
+__device__ __forceinline__ uint64_t bucket_of(const BucketParams& bp, uint32_t k) {
+    const uint64_t x = (uint64_t)(k - (uint32_t)bp.min) * bp.nb;
+    uint64_t q = __umul64hi(x, bp.recip);
+    uint64_t r = x - q * bp.range;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        if (r >= bp.range) {
+            ++q;
+            r -= bp.range;
+        }
+    return q;
+}
+
+__device__ __forceinline__ uint64_t bucket_of(const BucketParams& bp, uint64_t k) {
+    const uint64_t u = k - bp.min;
+    if (bp.range == 0) return __umul64hi(u, bp.nb);
+    const unsigned __int128 x = (unsigned __int128)u * bp.nb;
+    return (uint64_t)(x / bp.range);
+}
+
+__device__ __forceinline__ BucketParams load_bucket_params(const BucketParams* p) {
+    BucketParams b;
+    b.min = __ldcg(&p->min);
+    b.max = __ldcg(&p->max);
+    b.nb = __ldcg(&p->nb);
+    b.range = __ldcg(&p->range);
+    b.recip = __ldcg(&p->recip);
+    b.bbits = __ldcg(&p->bbits);
+    b.valid = __ldcg(&p->valid);
+    return b;
+}
+
+// Digit of the bucket id for a scatter pass: (b(k) >> shift) & mask.
+struct BucketDigit {
+    const BucketParams* src;
+    int shift;
+    uint32_t mask;
+    BucketParams bp;
+    __device__ __forceinline__ void init() { bp = load_bucket_params(src); }
+    template <typename KeyT>
+    __device__ __forceinline__ uint32_t operator()(KeyT k) const {
+        return (uint32_t)(bucket_of(bp, k) >> shift) & mask;
+    }
+};
+
+// The same digit for the counting kernels (only pass q = 0 exists).
+struct BucketDigits {
+    const BucketParams* src;
+    int shift;
+    uint32_t mask;
+    BucketParams bp;
+    __device__ __forceinline__ void init() { bp = load_bucket_params(src); }
+    template <typename KeyT>
+    __device__ __forceinline__ uint32_t operator()(KeyT k, int) const {
+        return (uint32_t)(bucket_of(bp, k) >> shift) & mask;
+    }
+};
+
+// Bucket view for the shared-memory sort of one partition: the partition's
+// first bucket is kept in SegDesc::aux and the number of buckets it spans in
+// SegDesc::chunk0 (unused for shared-memory segments).
+struct SegBucketFn {
+    const BucketParams* src;
+    BucketParams bp;
+    __device__ __forceinline__ bool active() const { return src != nullptr; }
+    __device__ __forceinline__ void init() { bp = load_bucket_params(src); }
+    __device__ __forceinline__ uint64_t first_bucket(const SegDesc& s) const { return s.aux; }
+    __device__ __forceinline__ uint64_t bucket_span(const SegDesc& s) const { return s.chunk0; }
+    template <typename KeyT>
+    __device__ __forceinline__ uint64_t bucket(KeyT k) const {
+        return bucket_of(bp, k);
+    }
+};
+
+}  // namespace rs

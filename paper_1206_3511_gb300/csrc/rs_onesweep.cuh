@@ -23,6 +23,7 @@ namespace rs {
 struct RadixDigit {
     int shift;
     uint32_t mask;
+    __device__ __forceinline__ void init() {}
     template <typename KeyT>
     __device__ __forceinline__ uint32_t operator()(KeyT k) const {
         return (uint32_t)(k >> shift) & mask;
@@ -203,44 +204,36 @@ __device__ __forceinline__ uint32_t warp_rank(uint32_t tab, uint32_t d, bool ok,
     return e.y + __popc(peers & lt);
 }
 
-// Decoupled look-back for one digit: the number of keys with digit d in all
-// tiles before `tile`.  The status words of kLookbackWindow earlier tiles are
-// read per round trip (independent loads); their counts are added from the
-// nearest tile backwards until the first inclusive prefix.  A tile whose word
-// is still invalid is waited for (bounded: after spin_limit polls the error is
-// recorded and the partial sum, which never exceeds the true prefix, is
-// returned).  The first window can be fetched early (lookback_fetch) and
-// consumed later (lookback_finish) so that its latency overlaps other work.
+// Decoupled look-back for one digit: the number of keys with digit d in the
+// tiles first_tile .. tile-1.  The status words of kLookbackWindow earlier
+// tiles are read per round trip (independent loads); their counts are added
+// from the nearest tile backwards until the first inclusive prefix.  A tile
+// whose word is still invalid is waited for (bounded: after spin_limit polls
+// the error is recorded and the partial sum, which never exceeds the true
+// prefix, is returned).
 constexpr int kLookbackWindow = 4;
 
-struct LookbackWindow {
-    uint32_t w[kLookbackWindow];
-};
-
-__device__ __forceinline__ LookbackWindow lookback_fetch(const uint32_t* status, int t, uint32_t bins, uint32_t d) {
-    LookbackWindow lw;
-#pragma unroll
-    for (int j = 0; j < kLookbackWindow; ++j)
-        lw.w[j] = (t - j >= 0) ? ld_relaxed(status + (size_t)(t - j) * bins + d) : kFlagPrefix;
-    return lw;
-}
-
-__device__ __forceinline__ uint32_t lookback_finish(LookbackWindow lw, const uint32_t* status, uint32_t tile,
-                                                    uint32_t bins, uint32_t d, uint32_t spin_limit, WsHeader* hdr) {
+__device__ __forceinline__ uint32_t lookback_digit(const uint32_t* status, uint32_t tile, uint32_t first_tile,
+                                                   uint32_t bins, uint32_t d, uint32_t spin_limit, WsHeader* hdr) {
     uint32_t excl = 0;
-    int t = (int)tile - 1;  // nearest tile not yet added
+    int64_t t = (int64_t)tile - 1;  // nearest tile not yet added
+    const int64_t lo = first_tile;
     uint32_t polls = 0;
-    while (t >= 0) {
+    while (t >= lo) {
+        uint32_t w[kLookbackWindow];
+#pragma unroll
+        for (int j = 0; j < kLookbackWindow; ++j)
+            w[j] = (t - j >= lo) ? ld_relaxed(status + (size_t)(t - j) * bins + d) : kFlagPrefix;
         bool done = false, blocked = false;
         int used = 0;
 #pragma unroll
         for (int j = 0; j < kLookbackWindow; ++j) {
             if (!done && !blocked) {
-                const uint32_t flag = lw.w[j] & ~kCountMask;
+                const uint32_t flag = w[j] & ~kCountMask;
                 if (flag == kFlagInvalid) {
                     blocked = true;
                 } else {
-                    excl += lw.w[j] & kCountMask;
+                    excl += w[j] & kCountMask;
                     ++used;
                     done = flag == kFlagPrefix;
                 }
@@ -255,14 +248,8 @@ __device__ __forceinline__ uint32_t lookback_finish(LookbackWindow lw, const uin
             }
             if (polls > 8) __nanosleep(polls < 256 ? 64 : 512);
         }
-        if (t >= 0) lw = lookback_fetch(status, t, bins, d);
     }
     return excl;
-}
-
-__device__ __forceinline__ uint32_t lookback_digit(const uint32_t* status, uint32_t tile, uint32_t bins, uint32_t d,
-                                                   uint32_t spin_limit, WsHeader* hdr) {
-    return lookback_finish(lookback_fetch(status, (int)tile - 1, bins, d), status, tile, bins, d, spin_limit, hdr);
 }
 
 // Shared-memory layout of one scatter-pass block.
@@ -272,31 +259,60 @@ struct PassSmem {
     KeyT* keys;               // [tile] staged keys
     uint32_t* vals;           // [tile] staged values
     uint32_t* local;          // [bins] start of each digit inside the staged tile
-    uint32_t* delta;          // [bins] global position minus staged position
+    uint32_t* delta;          // [bins] segment position minus staged position
     uint32_t* scan;           // [warps + 1] block-scan scratch
+};
+
+template <typename KeyT, bool VALS, int BLOCK>
+__device__ __forceinline__ PassSmem<KeyT> carve_pass_smem(unsigned char* smem, uint32_t bins, int tile_keys) {
+    PassSmem<KeyT> sm;
+    sm.tab = reinterpret_cast<unsigned long long*>(smem);
+    sm.keys = reinterpret_cast<KeyT*>(sm.tab + (size_t)(BLOCK / 32) * bins);
+    sm.vals = reinterpret_cast<uint32_t*>(sm.keys + tile_keys);
+    sm.local = sm.vals + (VALS ? tile_keys : 0);
+    sm.delta = sm.local + bins;
+    sm.scan = sm.delta + bins;
+    return sm;
+}
+
+// What one tile works on: its keys (already offset to the tile), the output
+// of its segment (positions are relative to the segment), the segment's
+// digit bases, and the range of tiles its look-back may visit.
+template <typename KeyT>
+struct TileCtx {
+    const KeyT* kin;
+    const uint32_t* vin;
+    KeyT* kout;
+    uint32_t* vout;
+    const uint32_t* digit_base;  // [bins] exclusive digit prefix inside the segment
+    uint32_t tile;               // global tile index (status row)
+    uint32_t first_tile;         // first tile of the segment
+    uint32_t tile_n;             // keys in this tile
+    uint32_t seg_n;              // keys in the segment
+    KeyT key_lo;                 // subtracted from every key before its digit is taken
 };
 
 // The body of the pass for one tile; FULL tiles skip every bounds check.
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS, bool FULL, typename DigitOp>
-__device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, const PassSmem<KeyT>& sm, uint32_t tile,
-                                              uint32_t tile_n, uint32_t bins, bool publish) {
+__device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, const DigitOp& op,
+                                              const PassSmem<KeyT>& sm, const TileCtx<KeyT>& c, uint32_t bins,
+                                              bool publish) {
     constexpr int kWarps = BLOCK / 32;
     constexpr int kTile = BLOCK * ITEMS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t tile_base = tile * (uint32_t)kTile;
+    const bool first = c.tile == c.first_tile;
 
     // load: warp w owns keys [w*ITEMS*32, (w+1)*ITEMS*32) of the tile, lane l
     // holds item i = key w*ITEMS*32 + i*32 + l (warp-striped, coalesced)
-    const KeyT* kin = static_cast<const KeyT*>(p.keys_in) + tile_base;
     const uint32_t wofs = (uint32_t)warp * (ITEMS * 32) + lane;
     KeyT k[ITEMS];
     uint32_t v[VALS ? ITEMS : 1];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const uint32_t idx = wofs + i * 32;
-        const bool ok = FULL || idx < tile_n;
-        k[i] = ok ? kin[idx] : (KeyT)0;
-        if (VALS) v[i] = ok ? p.vals_in[tile_base + idx] : 0u;
+        const bool ok = FULL || idx < c.tile_n;
+        k[i] = ok ? c.kin[idx] : c.key_lo;
+        if (VALS) v[i] = ok ? c.vin[idx] : 0u;
     }
 
     // rank every key inside its warp; keep (digit << 16 | rank) per item
@@ -307,30 +323,32 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     uint32_t dr[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const bool ok = FULL || (wofs + i * 32) < tile_n;
-        const uint32_t d = p.op(k[i]);
+        const bool ok = FULL || (wofs + i * 32) < c.tile_n;
+        const uint32_t d = op((KeyT)(k[i] - c.key_lo));
         dr[i] = (d << 16) | warp_rank<FULL>(tab, d, ok, lanebit, lt, gt);
     }
     __syncthreads();
 
-    // per digit: tile count, publish it, then each warp's offset inside the
-    // tile (kept in the low word of the rank table)
-    uint32_t* srow = p.status + (size_t)tile * bins;
+    // per digit: tile count, publish it, then the look-back right away, so
+    // this tile's inclusive prefix is published as early as possible
+    uint32_t* srow = p.status + (size_t)c.tile * bins;
     for (uint32_t d = tid; d < bins; d += BLOCK) {
         uint32_t sum = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) sum += (uint32_t)(sm.tab[(size_t)w * bins + d] >> 32);
         sm.local[d] = sum;
-        if (publish) st_relaxed(srow + d, (tile == 0 ? kFlagPrefix : kFlagAggregate) | sum);
+        if (publish) st_relaxed(srow + d, (first ? kFlagPrefix : kFlagAggregate) | sum);
     }
-    // decoupled look-back right away, so this tile's inclusive prefix is
-    // published as early as possible; sm.delta holds the global start of d
     for (uint32_t d = tid; d < bins; d += BLOCK) {
-        const uint32_t excl = tile == 0 ? 0u : lookback_digit(p.status, tile, bins, d, p.spin_limit, p.hdr);
-        if (tile != 0 && publish) st_relaxed(srow + d, kFlagPrefix | ((excl + sm.local[d]) & kCountMask));
-        sm.delta[d] = p.digit_base[d] + excl;
+        const uint32_t excl =
+            first ? 0u : lookback_digit(p.status, c.tile, c.first_tile, bins, d, p.spin_limit, p.hdr);
+        if (!first && publish) st_relaxed(srow + d, kFlagPrefix | ((excl + sm.local[d]) & kCountMask));
+        sm.delta[d] = c.digit_base[d] + excl;
     }
     __syncthreads();
+
+    // each digit's start inside the staged tile, and each warp's offset
+    // inside that digit (kept in the low word of the rank table)
     block_exclusive_scan_smem<BLOCK>(sm.local, (int)bins, sm.scan);
     for (uint32_t d = tid; d < bins; d += BLOCK) {
         uint32_t run = sm.local[d];
@@ -338,9 +356,9 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
         uint32_t* low = reinterpret_cast<uint32_t*>(sm.tab + d);
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = low[2 * (size_t)w * bins + 1];
+            const uint32_t cnt = low[2 * (size_t)w * bins + 1];
             low[2 * (size_t)w * bins] = run;
-            run += c;
+            run += cnt;
         }
     }
     __syncthreads();
@@ -348,7 +366,7 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     // stage the tile in shared memory in digit order
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const bool ok = FULL || (wofs + i * 32) < tile_n;
+        const bool ok = FULL || (wofs + i * 32) < c.tile_n;
         if (ok) {
             const uint32_t pos = ld_shared_u32(tab + 8u * (dr[i] >> 16)) + (dr[i] & 0xffffu);
             if (pos < (uint32_t)kTile) {
@@ -357,20 +375,18 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
             }
         }
     }
-
     __syncthreads();
 
-    // write runs of equal digits to their global places
-    KeyT* kout = static_cast<KeyT*>(p.keys_out);
+    // write runs of equal digits to their places in the segment
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const uint32_t idx = j * BLOCK + tid;
-        if (FULL || idx < tile_n) {
+        if (FULL || idx < c.tile_n) {
             const KeyT key = sm.keys[idx];
-            const uint32_t pos = sm.delta[p.op(key)] + idx;
-            if (pos < p.n) {
-                kout[pos] = key;
-                if (VALS) p.vals_out[pos] = sm.vals[idx];
+            const uint32_t pos = sm.delta[op((KeyT)(key - c.key_lo))] + idx;
+            if (pos < c.seg_n) {
+                c.kout[pos] = key;
+                if (VALS) c.vout[pos] = sm.vals[idx];
             }
         }
     }
@@ -378,33 +394,39 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
 
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB, typename DigitOp>
 __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p) {
-    constexpr int kWarps = BLOCK / 32;
     constexpr int kTile = BLOCK * ITEMS;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_tile;
     const uint32_t bins = 1u << p.digit_bits;
-    PassSmem<KeyT> sm;
-    sm.tab = reinterpret_cast<unsigned long long*>(smem);
-    sm.keys = reinterpret_cast<KeyT*>(sm.tab + (size_t)kWarps * bins);
-    sm.vals = reinterpret_cast<uint32_t*>(sm.keys + kTile);
-    sm.local = sm.vals + (VALS ? kTile : 0);
-    sm.delta = sm.local + bins;
-    sm.scan = sm.delta + bins;
+    const PassSmem<KeyT> sm = carve_pass_smem<KeyT, VALS, BLOCK>(smem, bins, kTile);
+    DigitOp op = p.op;
+    op.init();
 
     const int tid = threadIdx.x;
-    for (uint32_t i = tid; i < (uint32_t)kWarps * bins; i += BLOCK) sm.tab[i] = 0ull;
+    for (uint32_t i = tid; i < (uint32_t)(BLOCK / 32) * bins; i += BLOCK) sm.tab[i] = 0ull;
     if (tid == 0) s_tile = atomicAdd(p.tile_ctr, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= p.num_tiles) return;  // uniform across the block
-    const bool publish = (int)tile != p.stall_tile;
     if (p.status_next)
         for (uint32_t d = tid; d < bins; d += BLOCK) p.status_next[(size_t)tile * bins + d] = 0u;
-    const uint32_t tile_n = min((uint32_t)kTile, p.n - tile * (uint32_t)kTile);
-    if (tile_n == (uint32_t)kTile)
-        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, true>(p, sm, tile, tile_n, bins, publish);
+    TileCtx<KeyT> c;
+    const uint32_t base = tile * (uint32_t)kTile;
+    c.kin = static_cast<const KeyT*>(p.keys_in) + base;
+    c.vin = VALS ? p.vals_in + base : nullptr;
+    c.kout = static_cast<KeyT*>(p.keys_out);
+    c.vout = p.vals_out;
+    c.digit_base = p.digit_base;
+    c.tile = tile;
+    c.first_tile = 0;
+    c.tile_n = min((uint32_t)kTile, p.n - base);
+    c.seg_n = p.n;
+    c.key_lo = 0;
+    const bool publish = (int)tile != p.stall_tile;
+    if (c.tile_n == (uint32_t)kTile)
+        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, true>(p, op, sm, c, bins, publish);
     else
-        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, false>(p, sm, tile, tile_n, bins, publish);
+        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, false>(p, op, sm, c, bins, publish);
 }
 
 }  // namespace rs

@@ -1,0 +1,315 @@
+// rs_segmented.cu -- many independent arrays sorted in one call: every
+// segment of an offset table is sorted as Algorithm 4 (Sec. 2.5) would sort
+// it alone.  Segments of at most kLocalCap keys are sorted inside one block in
+// shared memory; larger ones go through per-segment digit counts and
+// segmented one-sweep scatter passes.  Planning happens on the device, so a
+// call needs no host synchronisation and can be captured in a CUDA graph.
+#include <mutex>
+
+#include "rs_bucket.cuh"
+#include "rs_segmented.h"
+
+namespace rs {
+
+namespace {
+
+constexpr int kSegDigitBits = 8;
+
+template <typename KeyT, bool VALS>
+struct SegShape;
+template <>
+struct SegShape<uint32_t, false> {
+    static constexpr int kBlock = 256, kItems = 18, kMinB = 4;
+};
+template <>
+struct SegShape<uint32_t, true> {
+    static constexpr int kBlock = 256, kItems = 12, kMinB = 4;
+};
+template <>
+struct SegShape<uint64_t, false> {
+    static constexpr int kBlock = 256, kItems = 12, kMinB = 4;
+};
+template <>
+struct SegShape<uint64_t, true> {
+    static constexpr int kBlock = 256, kItems = 10, kMinB = 3;
+};
+
+template <typename KeyT, bool VALS, typename DigitOp>
+cudaError_t launch_seg_pass(const SegPassParams<DigitOp>& sp, size_t grid, cudaStream_t s) {
+    using S = SegShape<KeyT, VALS>;
+    using Shape = OnesweepShape<KeyT, VALS, S::kBlock, S::kItems>;
+    auto kern = k_onesweep_seg<KeyT, VALS, S::kBlock, S::kItems, S::kMinB, DigitOp>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)Shape::smem_bytes(kMaxDigitBits));
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    KernelScope scope("onesweep_seg_pass", s);
+    kern<<<(unsigned)grid, S::kBlock, Shape::smem_bytes(sp.base.digit_bits), s>>>(sp);
+    return cudaGetLastError();
+}
+
+template <typename KeyT, bool VALS, typename BucketFn>
+cudaError_t launch_local(const LocalParams& lp, BucketFn bfn, size_t grid, cudaStream_t s) {
+    using LS = LocalSmem<KeyT, VALS, kLocalBlock>;
+    auto kern = k_local_sort<KeyT, VALS, kLocalBlock, kLocalItems, BucketFn>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    const size_t smem = LS::bytes(kLocalCap);
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    KernelScope scope("local_sort", s);
+    kern<<<(unsigned)grid, kLocalBlock, smem, s>>>(lp, bfn);
+    return cudaGetLastError();
+}
+
+template <typename KeyT>
+cudaError_t launch_seg_counts(const KeyT* keys, const SegBuffers& B, RadixDigits dg, int passes, uint32_t bins,
+                              uint32_t* zero_ptr, size_t zero_words, cudaStream_t s) {
+    auto kern = k_seg_counts<KeyT, RadixDigits>;
+    const size_t smem = (size_t)passes * bins * 4;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)max_count_smem_bytes());
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    KernelScope scope("seg_counts", s);
+    kern<<<(unsigned)B.max_chunks, 512, smem, s>>>(keys, B.large, B.hdr, B.chunk_seg, dg, passes, bins, B.seg_rows,
+                                                    zero_ptr, zero_words);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+uint32_t seg_tile_keys(int key_bytes, bool vals) {
+    if (key_bytes == 4) return vals ? 256 * 12 : 256 * 18;
+    return vals ? 256 * 10 : 256 * 12;
+}
+
+SegLayout seg_layout(int key_bytes, bool vals, size_t n_total, size_t max_segs, int max_passes, int max_bins,
+                     size_t extra_head) {
+    SegLayout L{};
+    const uint32_t tk = seg_tile_keys(key_bytes, vals);
+    L.max_segs = max_segs ? max_segs : 1;
+    L.max_tiles = n_total / tk + L.max_segs + 1;
+    L.max_chunks = n_total / kSegChunk + L.max_segs + 1;
+    L.max_passes = max_passes;
+    L.max_bins = max_bins;
+    Carver c;
+    c.take(sizeof(WsHeader) + extra_head);
+    L.off_plan = c.take(sizeof(SegPlanHdr));
+    L.off_large = c.take(L.max_segs * sizeof(SegDesc));
+    L.off_small = c.take(L.max_segs * sizeof(SegDesc));
+    L.off_tile_seg = c.take(L.max_tiles * 4);
+    L.off_chunk_seg = c.take(L.max_chunks * 4);
+    L.off_rows = c.take(L.max_segs * (size_t)max_passes * max_bins * 4);
+    L.off_status0 = c.take(L.max_tiles * (size_t)max_bins * 4);
+    L.off_status1 = c.take(L.max_tiles * (size_t)max_bins * 4);
+    L.off_tmp_keys = c.take(n_total * key_bytes);
+    L.off_tmp_vals = vals ? c.take(n_total * 4) : 0;
+    L.total = c.off;
+    return L;
+}
+
+SegBuffers carve_seg_buffers(void* ws, const SegLayout& L) {
+    unsigned char* b = static_cast<unsigned char*>(ws);
+    SegBuffers B{};
+    B.ws_hdr = reinterpret_cast<WsHeader*>(b);
+    B.hdr = reinterpret_cast<SegPlanHdr*>(b + L.off_plan);
+    B.large = reinterpret_cast<SegDesc*>(b + L.off_large);
+    B.small = reinterpret_cast<SegDesc*>(b + L.off_small);
+    B.tile_seg = reinterpret_cast<uint32_t*>(b + L.off_tile_seg);
+    B.chunk_seg = reinterpret_cast<uint32_t*>(b + L.off_chunk_seg);
+    B.seg_rows = reinterpret_cast<uint32_t*>(b + L.off_rows);
+    B.status[0] = reinterpret_cast<uint32_t*>(b + L.off_status0);
+    B.status[1] = reinterpret_cast<uint32_t*>(b + L.off_status1);
+    B.tmp_keys = b + L.off_tmp_keys;
+    B.tmp_vals = L.off_tmp_vals ? reinterpret_cast<uint32_t*>(b + L.off_tmp_vals) : nullptr;
+    B.max_segs = L.max_segs;
+    B.max_tiles = L.max_tiles;
+    B.max_chunks = L.max_chunks;
+    B.max_passes = L.max_passes;
+    B.max_bins = L.max_bins;
+    return B;
+}
+
+template <typename KeyT, bool VALS>
+static rs_status large_passes_t(const void* src_k, const uint32_t* src_v, void* out_k, uint32_t* out_v,
+                                const SegBuffers& B, int passes, int D, cudaStream_t stream) {
+    const uint32_t bins = 1u << D;
+    const uint32_t tk = seg_tile_keys(sizeof(KeyT), VALS);
+    {
+        KernelScope scope("plan_maps", stream);
+        k_plan_maps<<<(unsigned)B.max_segs, 256, 0, stream>>>(B.large, B.hdr, tk, B.tile_seg, B.chunk_seg);
+        if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
+    }
+    RS_CUDA_TRY(cudaMemsetAsync(B.seg_rows, 0, B.max_segs * (size_t)passes * bins * 4, stream));
+    RadixDigits dg{0, D, bins - 1u};
+    if (launch_seg_counts<KeyT>(static_cast<const KeyT*>(src_k), B, dg, passes, bins, B.status[0],
+                                B.max_tiles * (size_t)bins, stream) != cudaSuccess)
+        return RS_ERR_CUDA;
+    {
+        KernelScope scope("seg_scan", stream);
+        k_seg_scan<<<(unsigned)(B.max_segs * passes), 256, (bins + 256 / 32 + 1) * 4, stream>>>(B.seg_rows, B.hdr,
+                                                                                                passes, bins, 0);
+        if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
+    }
+    SegPassParams<RadixDigit> sp{};
+    sp.base.digit_bits = D;
+    sp.base.hdr = B.ws_hdr;
+    sp.base.spin_limit = debug_spin_limit();
+    sp.base.stall_tile = debug_stall_tile();
+    sp.segs = B.large;
+    sp.hdr = B.hdr;
+    sp.tile_seg = B.tile_seg;
+    sp.seg_base = B.seg_rows;
+    sp.passes = passes;
+    const void* cur_k = src_k;
+    const uint32_t* cur_v = src_v;
+    for (int p = 0; p < passes; ++p) {
+        const bool to_out = ((passes - 1 - p) % 2) == 0;
+        void* dst_k = to_out ? out_k : B.tmp_keys;
+        uint32_t* dst_v = VALS ? (to_out ? out_v : B.tmp_vals) : nullptr;
+        sp.base.keys_in = cur_k;
+        sp.base.keys_out = dst_k;
+        sp.base.vals_in = cur_v;
+        sp.base.vals_out = dst_v;
+        sp.base.op = RadixDigit{p * D, bins - 1u};
+        sp.base.status = B.status[p & 1];
+        sp.base.status_next = (p + 1 < passes) ? B.status[(p + 1) & 1] : nullptr;
+        sp.base.tile_ctr = &B.ws_hdr->tile_ctr[p % kMaxPasses];
+        sp.pass = p;
+        if (launch_seg_pass<KeyT, VALS, RadixDigit>(sp, B.max_tiles, stream) != cudaSuccess) return RS_ERR_CUDA;
+        cur_k = dst_k;
+        cur_v = dst_v;
+    }
+    return RS_OK;
+}
+
+rs_status enqueue_large_passes(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,
+                               uint32_t* out_v, const SegBuffers& B, int passes, int digit_bits,
+                               cudaStream_t stream) {
+    if (passes < 1 || passes > kMaxPasses || passes > B.max_passes || (1 << digit_bits) > B.max_bins)
+        return RS_ERR_INVALID_ARG;
+    if (key_bytes == 4)
+        return vals ? large_passes_t<uint32_t, true>(src_k, src_v, out_k, out_v, B, passes, digit_bits, stream)
+                    : large_passes_t<uint32_t, false>(src_k, src_v, out_k, out_v, B, passes, digit_bits, stream);
+    return vals ? large_passes_t<uint64_t, true>(src_k, src_v, out_k, out_v, B, passes, digit_bits, stream)
+                : large_passes_t<uint64_t, false>(src_k, src_v, out_k, out_v, B, passes, digit_bits, stream);
+}
+
+rs_status enqueue_local_sorts(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,
+                              uint32_t* out_v, const SegDesc* segs, const uint32_t* count, size_t max_count,
+                              const void* bucket, cudaStream_t stream) {
+    LocalParams lp{src_k, out_k, src_v, out_v, segs, count, bucket};
+    const size_t grid = max_count ? max_count : 1;
+    cudaError_t e;
+    if (bucket) {
+        SegBucketFn f{static_cast<const BucketParams*>(bucket), {}};
+        if (key_bytes == 4)
+            e = vals ? launch_local<uint32_t, true>(lp, f, grid, stream)
+                     : launch_local<uint32_t, false>(lp, f, grid, stream);
+        else
+            e = vals ? launch_local<uint64_t, true>(lp, f, grid, stream)
+                     : launch_local<uint64_t, false>(lp, f, grid, stream);
+    } else {
+        NoBucket f;
+        if (key_bytes == 4)
+            e = vals ? launch_local<uint32_t, true>(lp, f, grid, stream)
+                     : launch_local<uint32_t, false>(lp, f, grid, stream);
+        else
+            e = vals ? launch_local<uint64_t, true>(lp, f, grid, stream)
+                     : launch_local<uint64_t, false>(lp, f, grid, stream);
+    }
+    return e == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
+size_t segmented_workspace_bytes(int key_bytes, bool vals, size_t n_total, size_t nseg, int key_bits) {
+    const int P = (key_bits + kSegDigitBits - 1) / kSegDigitBits;
+    return seg_layout(key_bytes, vals, n_total, nseg, P, 1 << kSegDigitBits, 0).total;
+}
+
+static rs_status segmented_impl(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                                uint32_t* vals_out, const uint64_t* d_offsets, size_t nseg, size_t n_total,
+                                int key_bits, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    const int width = 8 * key_bytes;
+    if (key_bits == 0) key_bits = width;
+    if (key_bits < 1 || key_bits > width) return RS_ERR_INVALID_ARG;
+    if ((vals_in == nullptr) != (vals_out == nullptr)) return RS_ERR_INVALID_ARG;
+    const bool vals = vals_in != nullptr;
+    if (nseg == 0 || n_total == 0) return RS_OK;
+    if (!d_offsets || !keys_in || !keys_out) return RS_ERR_INVALID_ARG;
+    if (nseg > ((size_t)1 << 31)) return RS_ERR_INVALID_ARG;
+    const size_t kb = n_total * key_bytes, vb = n_total * 4;
+    if (keys_in != keys_out && ranges_overlap(keys_in, kb, keys_out, kb)) return RS_ERR_INVALID_ARG;
+    if (vals && vals_in != vals_out && ranges_overlap(vals_in, vb, vals_out, vb)) return RS_ERR_INVALID_ARG;
+    if (((uintptr_t)keys_in | (uintptr_t)keys_out) % key_bytes) return RS_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws % 256)) return RS_ERR_WORKSPACE;
+    const int D = kSegDigitBits;
+    const int P = (key_bits + D - 1) / D;
+    const SegLayout L = seg_layout(key_bytes, vals, n_total, nseg, P, 1 << D, 0);
+    if (ws_bytes < L.total) return RS_ERR_WORKSPACE;
+    const SegBuffers B = carve_seg_buffers(ws, L);
+    RS_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(WsHeader), stream));
+    RS_CUDA_TRY(cudaMemsetAsync(B.hdr, 0, sizeof(SegPlanHdr), stream));
+    {
+        KernelScope scope("plan_segments", stream);
+        k_plan_from_offsets<<<(unsigned)((nseg + 255) / 256), 256, 0, stream>>>(
+            d_offsets, nseg, kLocalCap, seg_tile_keys(key_bytes, vals), key_bits, B.large, B.small, B.hdr, B.ws_hdr);
+        if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
+    }
+    // large segments: scatter passes from keys_in (in place with an odd pass
+    // count first copies the input to the workspace buffer)
+    const void* src_k = keys_in;
+    const uint32_t* src_v = vals_in;
+    const bool in_place = keys_in == keys_out || (vals && vals_in == vals_out);
+    if (in_place && (P % 2 == 1)) {
+        RS_CUDA_TRY(cudaMemcpyAsync(B.tmp_keys, keys_in, kb, cudaMemcpyDeviceToDevice, stream));
+        src_k = B.tmp_keys;
+        if (vals) {
+            RS_CUDA_TRY(cudaMemcpyAsync(B.tmp_vals, vals_in, vb, cudaMemcpyDeviceToDevice, stream));
+            src_v = B.tmp_vals;
+        }
+    }
+    rs_status st = enqueue_large_passes(key_bytes, vals, src_k, src_v, keys_out, vals_out, B, P, D, stream);
+    if (st != RS_OK) return st;
+    // small segments: one block each, straight from the input (a block reads
+    // its whole segment before writing, so in place is fine)
+    return enqueue_local_sorts(key_bytes, vals, keys_in, vals_in, keys_out, vals_out, B.small, &B.hdr->num_small,
+                               nseg, nullptr, stream);
+}
+
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+size_t rs_segmented_workspace_bytes(int key_bytes, int has_values, size_t n_total, size_t nseg, int key_bits) {
+    if (key_bytes != 4 && key_bytes != 8) return 0;
+    if (key_bits == 0) key_bits = 8 * key_bytes;
+    if (key_bits < 1 || key_bits > 8 * key_bytes) return 0;
+    return segmented_workspace_bytes(key_bytes, has_values != 0, n_total, nseg, key_bits);
+}
+
+rs_status rs_sort_segmented_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
+                                uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg, size_t n_total,
+                                int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream) {
+    return segmented_impl(4, keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, key_bits, ws,
+                          ws_bytes, stream);
+}
+
+rs_status rs_sort_segmented_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
+                                uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg, size_t n_total,
+                                int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream) {
+    return segmented_impl(8, keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, key_bits, ws,
+                          ws_bytes, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,386 @@
+// rs_segmented.cuh -- kernels that sort many independent segments of one
+// array: device-side planning, per-segment digit counts, a segmented
+// one-sweep scatter pass and a shared-memory sort for segments that fit in
+// one block.  Each segment is sorted exactly as Algorithm 4 (Sec. 2.5) would
+// sort it alone.  The bucket sort reuses these kernels for its partitions.
+#pragma once
+
+#include "rs_onesweep.cuh"
+
+namespace rs {
+
+// One segment of the arrays.  Keys are sorted on the low `bits` bits of
+// (key - key_lo).
+struct SegDesc {
+    uint64_t start;   // index of the segment's first key
+    uint64_t key_lo;  // subtracted from every key before digits are taken
+    uint32_t n;       // number of keys
+    uint32_t tile0;   // first global tile (scatter passes)
+    uint32_t chunk0;  // first counting chunk
+    uint32_t bits;    // key bits to sort on
+    uint64_t aux;     // planner data (bucket range of bucket-sort partitions)
+};
+static_assert(sizeof(SegDesc) == 40, "SegDesc layout");
+
+// Device-side totals of a plan (zeroed before planning).
+struct SegPlanHdr {
+    uint32_t num_large;     // segments sorted by scatter passes
+    uint32_t num_small;     // segments sorted in shared memory
+    uint32_t total_tiles;   // scatter-pass tiles over all large segments
+    uint32_t total_chunks;  // counting chunks over all large segments
+    uint32_t num_next;      // partitions handed to the next level (bucket sort)
+    uint32_t next_tiles;
+    uint32_t next_chunks;
+    uint32_t pad;
+};
+
+constexpr uint32_t kSegChunk = 32768;  // keys per counting block
+
+__device__ __forceinline__ uint32_t ceil_div_u32(uint32_t a, uint32_t b) { return (a + b - 1) / b; }
+
+// Append one segment to a list with its tile and chunk ranges reserved.
+__device__ __forceinline__ void append_large(SegDesc* list, uint32_t* count, uint32_t* tiles, uint32_t* chunks,
+                                             SegDesc d, uint32_t tile_keys) {
+    d.tile0 = atomicAdd(tiles, ceil_div_u32(d.n, tile_keys));
+    d.chunk0 = atomicAdd(chunks, ceil_div_u32(d.n, kSegChunk));
+    list[atomicAdd(count, 1u)] = d;
+}
+
+// Segments from an offset table: empty ones are dropped, those of at most
+// `small_cap` keys go to the shared-memory list, the others to the scatter
+// list.  One thread per segment.
+__global__ void k_plan_from_offsets(const uint64_t* __restrict__ offsets, size_t nseg, uint32_t small_cap,
+                                    uint32_t tile_keys, int bits, SegDesc* large, SegDesc* small, SegPlanHdr* hdr,
+                                    WsHeader* ws_hdr) {
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    const uint64_t a = offsets[s], b = offsets[s + 1];
+    if (b < a || b - a >= ((uint64_t)1 << 30)) {  // decreasing offsets or a segment above the single-sort limit
+        set_device_error(ws_hdr, RS_ERR_INVALID_ARG, (uint32_t)s);
+        return;
+    }
+    if (b == a) return;
+    SegDesc d{};
+    d.start = a;
+    d.key_lo = 0;
+    d.n = (uint32_t)(b - a);
+    d.bits = (uint32_t)bits;
+    if (d.n <= small_cap)
+        small[atomicAdd(&hdr->num_small, 1u)] = d;
+    else
+        append_large(large, &hdr->num_large, &hdr->total_tiles, &hdr->total_chunks, d, tile_keys);
+}
+
+// tile -> segment and chunk -> segment maps; one block per large segment.
+__global__ void k_plan_maps(const SegDesc* __restrict__ large, const SegPlanHdr* __restrict__ hdr,
+                            uint32_t tile_keys, uint32_t* tile_seg, uint32_t* chunk_seg) {
+    const uint32_t li = blockIdx.x;
+    if (li >= hdr->num_large) return;
+    const SegDesc d = large[li];
+    const uint32_t nt = ceil_div_u32(d.n, tile_keys), nc = ceil_div_u32(d.n, kSegChunk);
+    for (uint32_t i = threadIdx.x; i < nt; i += blockDim.x) tile_seg[d.tile0 + i] = li;
+    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) chunk_seg[d.chunk0 + i] = li;
+}
+
+// Digit q of a segment-relative key for the counting kernel: (x >> (shift0 +
+// q*D)) & (2^D - 1).
+struct RadixDigits {
+    int shift0;
+    int digit_bits;
+    uint32_t mask;
+    __device__ __forceinline__ void init() {}
+    template <typename KeyT>
+    __device__ __forceinline__ uint32_t operator()(KeyT x, int q) const {
+        return (uint32_t)(x >> (shift0 + q * digit_bits)) & mask;
+    }
+};
+
+// Per-segment digit counts of `passes` digits: seg_counts[li][q][d].  One
+// block per counting chunk of a large segment.  Also zeroes zero_words words
+// at zero_ptr (the first pass's look-back status).
+template <typename KeyT, typename Digits>
+__global__ void __launch_bounds__(512) k_seg_counts(const KeyT* __restrict__ keys, const SegDesc* __restrict__ large,
+                                                    const SegPlanHdr* __restrict__ hdr,
+                                                    const uint32_t* __restrict__ chunk_seg, Digits dg, int passes,
+                                                    uint32_t bins, uint32_t* seg_counts, uint32_t* zero_ptr,
+                                                    size_t zero_words) {
+    extern __shared__ uint32_t s_cnt[];  // [passes][bins]
+    const int tid = threadIdx.x;
+    const size_t used_words = (size_t)hdr->total_tiles * bins;  // only the rows of tiles that exist
+    if (zero_words > used_words) zero_words = used_words;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + tid; i < zero_words; i += (size_t)gridDim.x * blockDim.x)
+        zero_ptr[i] = 0u;
+    const uint32_t c = blockIdx.x;
+    if (c >= hdr->total_chunks) return;
+    dg.init();
+    const uint32_t li = chunk_seg[c];
+    const SegDesc d = large[li];
+    const uint32_t lo = (c - d.chunk0) * kSegChunk;
+    const uint32_t hi = min(d.n, lo + kSegChunk);
+    const int ncnt = passes * (int)bins;
+    for (int i = tid; i < ncnt; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
+    const KeyT* kp = keys + d.start;
+    const KeyT klo = (KeyT)d.key_lo;
+    for (uint32_t i = lo + tid; i < hi; i += blockDim.x) {
+        const KeyT x = (KeyT)(__ldcs(kp + i) - klo);
+        for (int q = 0; q < passes; ++q) atomicAdd(&s_cnt[q * bins + dg(x, q)], 1u);
+    }
+    __syncthreads();
+    uint32_t* out = seg_counts + (size_t)li * ncnt;
+    for (int i = tid; i < ncnt; i += blockDim.x)
+        if (s_cnt[i]) atomicAdd(&out[i], s_cnt[i]);
+}
+
+// Exclusive prefix of every (segment, pass) row of bins counts, in place.
+// One block of 256 threads per row.
+__global__ void __launch_bounds__(256) k_seg_scan(uint32_t* rows, const SegPlanHdr* __restrict__ hdr, int passes,
+                                                  uint32_t bins, int use_next) {
+    extern __shared__ uint32_t s_row[];  // [bins] + scan scratch
+    const uint32_t nrows = (use_next ? hdr->num_next : hdr->num_large) * (uint32_t)passes;
+    if (blockIdx.x >= nrows) return;
+    uint32_t* row = rows + (size_t)blockIdx.x * bins;
+    for (uint32_t d = threadIdx.x; d < bins; d += 256) s_row[d] = row[d];
+    __syncthreads();
+    block_exclusive_scan_smem<256>(s_row, (int)bins, s_row + bins);
+    for (uint32_t d = threadIdx.x; d < bins; d += 256) row[d] = s_row[d];
+}
+
+// Parameters of a segmented scatter pass.
+template <typename DigitOp>
+struct SegPassParams {
+    PassParams<DigitOp> base;      // keys, values, op, status, counters, hooks (n, num_tiles unused)
+    const SegDesc* segs;           // large segments
+    const SegPlanHdr* hdr;         // total_tiles
+    const uint32_t* tile_seg;      // global tile -> segment
+    const uint32_t* seg_base;      // [segment][passes][bins] exclusive prefixes
+    int pass;
+    int passes;
+};
+
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB, typename DigitOp>
+__global__ void __launch_bounds__(BLOCK, MINB) k_onesweep_seg(SegPassParams<DigitOp> sp) {
+    constexpr int kTile = BLOCK * ITEMS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_tile;
+    const PassParams<DigitOp>& p = sp.base;
+    const uint32_t bins = 1u << p.digit_bits;
+    const PassSmem<KeyT> sm = carve_pass_smem<KeyT, VALS, BLOCK>(smem, bins, kTile);
+    DigitOp op = p.op;
+    op.init();
+    const int tid = threadIdx.x;
+    for (uint32_t i = tid; i < (uint32_t)(BLOCK / 32) * bins; i += BLOCK) sm.tab[i] = 0ull;
+    if (tid == 0) s_tile = atomicAdd(p.tile_ctr, 1u);
+    __syncthreads();
+    const uint32_t g = s_tile;
+    if (g >= sp.hdr->total_tiles) return;  // uniform across the block
+    if (p.status_next)
+        for (uint32_t d = tid; d < bins; d += BLOCK) p.status_next[(size_t)g * bins + d] = 0u;
+    const uint32_t li = sp.tile_seg[g];
+    const SegDesc seg = sp.segs[li];
+    const uint32_t base = (g - seg.tile0) * (uint32_t)kTile;
+    TileCtx<KeyT> c;
+    c.kin = static_cast<const KeyT*>(p.keys_in) + seg.start + base;
+    c.vin = VALS ? p.vals_in + seg.start + base : nullptr;
+    c.kout = static_cast<KeyT*>(p.keys_out) + seg.start;
+    c.vout = VALS ? p.vals_out + seg.start : nullptr;
+    c.digit_base = sp.seg_base + ((size_t)li * sp.passes + sp.pass) * bins;
+    c.tile = g;
+    c.first_tile = seg.tile0;
+    c.tile_n = min((uint32_t)kTile, seg.n - base);
+    c.seg_n = seg.n;
+    c.key_lo = (KeyT)seg.key_lo;
+    const bool publish = (int)g != p.stall_tile;
+    if (c.tile_n == (uint32_t)kTile)
+        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, true>(p, op, sm, c, bins, publish);
+    else
+        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, false>(p, op, sm, c, bins, publish);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory sort of one small segment per block: load it, run stable LSD
+// passes of up to 8 bits over (key - key_lo) between two shared buffers
+// (each pass ranks keys inside their warps exactly like the scatter pass),
+// write it back.  In bucket mode the first pass sorts by the key's bucket
+// relative to the segment's first bucket (the insert step of Algorithm 2)
+// and each bucket is then insertion-sorted by one thread (Algorithm 1); a
+// segment with a bucket above kInsertionMax keys, or spanning more than 256
+// buckets, is sorted by its key bits instead, which gives the same order
+// because bucket ids grow with the key.
+constexpr uint32_t kInsertionMax = 48;
+
+template <typename KeyT, bool VALS, int BLOCK>
+struct LocalSmem {
+    static constexpr int kWarps = BLOCK / 32;
+    static size_t bytes(int cap) {
+        size_t b = (size_t)kWarps * 256 * 8;          // rank table
+        b += 2 * (size_t)cap * sizeof(KeyT);          // key buffers
+        if (VALS) b += 2 * (size_t)cap * 4;           // value buffers
+        b += 256 * 4 * 2 + (kWarps + 1 + 3) * 4 + 16; // starts, counts, scan scratch, flags
+        return b;
+    }
+};
+
+// One stable pass of the shared-memory sort: keys (and values) move from
+// (ka, va) to (kb, vb) ordered by digit dfun(key) < 256.
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename DFun>
+__device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, KeyT* kb, uint32_t* vb, uint32_t m,
+                                           unsigned long long* s_tab, uint32_t* s_start, uint32_t* s_cnt,
+                                           uint32_t* s_scan, DFun dfun) {
+    constexpr int kWarps = BLOCK / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t i = tid; i < (uint32_t)kWarps * 256; i += BLOCK) s_tab[i] = 0ull;
+    __syncthreads();
+    const uint32_t tab = smem_addr(s_tab + (size_t)warp * 256);
+    const uint32_t lt = lanemask_lt(), lanebit = 1u << lane, gt = ~(lt | lanebit);
+    const uint32_t wofs = (uint32_t)warp * (ITEMS * 32) + lane;
+    uint32_t dr[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t idx = wofs + i * 32;
+        const bool ok = idx < m;
+        const uint32_t d = ok ? dfun(ka[idx]) : 0u;
+        dr[i] = (d << 16) | warp_rank<false>(tab, d, ok, lanebit, lt, gt);
+    }
+    __syncthreads();
+    for (uint32_t d = tid; d < 256; d += BLOCK) {
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) sum += (uint32_t)(s_tab[(size_t)w * 256 + d] >> 32);
+        s_cnt[d] = sum;
+        s_start[d] = sum;
+    }
+    __syncthreads();
+    block_exclusive_scan_smem<BLOCK>(s_start, 256, s_scan);
+    for (uint32_t d = tid; d < 256; d += BLOCK) {
+        uint32_t run = s_start[d];
+        uint32_t* low = reinterpret_cast<uint32_t*>(s_tab + d);
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t cnt = low[2 * (size_t)w * 256 + 1];
+            low[2 * (size_t)w * 256] = run;
+            run += cnt;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t idx = wofs + i * 32;
+        if (idx < m) {
+            const uint32_t pos = ld_shared_u32(tab + 8u * (dr[i] >> 16)) + (dr[i] & 0xffffu);
+            if (pos < m) {
+                kb[pos] = ka[idx];
+                if (VALS) vb[pos] = va[idx];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+struct LocalParams {
+    const void* keys_in;
+    void* keys_out;
+    const uint32_t* vals_in;
+    uint32_t* vals_out;
+    const SegDesc* segs;
+    const uint32_t* count;  // number of segments in segs
+    const void* bucket;     // BucketParams (bucket mode) or null
+};
+
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename BucketFn>
+__global__ void __launch_bounds__(BLOCK) k_local_sort(LocalParams lp, BucketFn bfn) {
+    constexpr int kCap = BLOCK * ITEMS;
+    constexpr int kWarps = BLOCK / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (blockIdx.x >= *lp.count) return;
+    const SegDesc seg = lp.segs[blockIdx.x];
+    const uint32_t m = seg.n;
+    unsigned long long* s_tab = reinterpret_cast<unsigned long long*>(smem);
+    KeyT* kbuf[2];
+    kbuf[0] = reinterpret_cast<KeyT*>(s_tab + kWarps * 256);
+    kbuf[1] = kbuf[0] + kCap;
+    uint32_t* vbuf[2];
+    vbuf[0] = reinterpret_cast<uint32_t*>(kbuf[1] + kCap);
+    vbuf[1] = vbuf[0] + (VALS ? kCap : 0);
+    uint32_t* s_start = vbuf[1] + (VALS ? kCap : 0);
+    uint32_t* s_cnt = s_start + 256;
+    uint32_t* s_scan = s_cnt + 256;
+    uint32_t* s_flag = s_scan + kWarps + 1;
+
+    const KeyT* kin = static_cast<const KeyT*>(lp.keys_in) + seg.start;
+    for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
+        kbuf[0][i] = kin[i];
+        if (VALS) vbuf[0][i] = lp.vals_in[seg.start + i];
+    }
+    const KeyT klo = (KeyT)seg.key_lo;
+    int cur = 0;
+    bool by_keys = true;
+    if (bfn.active()) {
+        bfn.init();
+        const uint64_t b_lo = bfn.first_bucket(seg), span = bfn.bucket_span(seg);
+        if (threadIdx.x == 0) *s_flag = 0u;
+        __syncthreads();
+        if (span <= 256) {
+            local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[0], vbuf[0], kbuf[1], vbuf[1], m, s_tab, s_start, s_cnt, s_scan,
+                                                 [&](KeyT k) { return (uint32_t)(bfn.bucket(k) - b_lo); });
+            cur = 1;
+            for (uint32_t d = threadIdx.x; d < 256; d += BLOCK)
+                if (s_cnt[d] > kInsertionMax) *s_flag = 1u;
+            __syncthreads();
+            if (*s_flag == 0u) {
+                by_keys = false;
+                // Algorithm 1 on every bucket: thread d sorts bucket d in place
+                for (uint32_t d = threadIdx.x; d < 256; d += BLOCK) {
+                    KeyT* A = kbuf[1] + s_start[d];
+                    uint32_t* V = vbuf[1] + (VALS ? s_start[d] : 0);
+                    const uint32_t len = s_cnt[d];
+                    for (uint32_t j = 1; j < len; ++j) {
+                        const KeyT key = A[j];
+                        uint32_t val = 0;
+                        if (VALS) val = V[j];
+                        uint32_t i = j;
+                        while (i > 0 && A[i - 1] > key) {
+                            A[i] = A[i - 1];
+                            if (VALS) V[i] = V[i - 1];
+                            --i;
+                        }
+                        A[i] = key;
+                        if (VALS) V[i] = val;
+                    }
+                }
+                __syncthreads();
+            }
+        } else {
+            __syncthreads();
+        }
+    } else {
+        __syncthreads();
+    }
+    if (by_keys) {
+        for (uint32_t shift = 0; shift < seg.bits; shift += 8) {
+            local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1], m, s_tab, s_start,
+                                                 s_cnt, s_scan,
+                                                 [&](KeyT k) { return (uint32_t)((KeyT)(k - klo) >> shift) & 255u; });
+            cur ^= 1;
+        }
+    }
+    KeyT* kout = static_cast<KeyT*>(lp.keys_out) + seg.start;
+    for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
+        kout[i] = kbuf[cur][i];
+        if (VALS) lp.vals_out[seg.start + i] = vbuf[cur][i];
+    }
+}
+
+// Bucket function placeholder for plain segmented sorts (no bucket step).
+struct NoBucket {
+    __device__ __forceinline__ bool active() const { return false; }
+    __device__ __forceinline__ void init() {}
+    __device__ __forceinline__ uint64_t first_bucket(const SegDesc&) const { return 0; }
+    __device__ __forceinline__ uint64_t bucket_span(const SegDesc&) const { return 0; }
+    template <typename KeyT>
+    __device__ __forceinline__ uint64_t bucket(KeyT) const {
+        return 0;
+    }
+};
+
+}  // namespace rs

@@ -1,0 +1,61 @@
+// rs_segmented.h -- internal interface of the segmented-sort host code,
+// shared with the bucket sort.
+#pragma once
+
+#include "rs_radix.h"
+#include "rs_segmented.cuh"
+
+namespace rs {
+
+// Shared-memory sort capacity: segments of at most this many keys are
+// sorted inside one block.
+constexpr int kLocalBlock = 256;
+constexpr int kLocalItems = 16;
+constexpr uint32_t kLocalCap = kLocalBlock * kLocalItems;
+
+// Device buffers of one segmented sort (all carved from the workspace).
+struct SegBuffers {
+    WsHeader* ws_hdr;
+    SegPlanHdr* hdr;
+    SegDesc* large;        // [max_segs]
+    SegDesc* small;        // [max_segs]
+    uint32_t* tile_seg;    // [max_tiles]
+    uint32_t* chunk_seg;   // [max_chunks]
+    uint32_t* seg_rows;    // [max_segs][max_passes][max_bins]
+    uint32_t* status[2];   // [max_tiles][max_bins] each
+    void* tmp_keys;        // [n_total]
+    uint32_t* tmp_vals;    // [n_total] or null
+    size_t max_segs, max_tiles, max_chunks;
+    int max_passes, max_bins;
+};
+
+// Workspace layout of a segmented sort: sizes for every region, the offsets
+// filled in by carve_seg_buffers.
+struct SegLayout {
+    size_t off_plan, off_large, off_small, off_tile_seg, off_chunk_seg, off_rows, off_status0, off_status1,
+        off_tmp_keys, off_tmp_vals, total;
+    size_t max_segs, max_tiles, max_chunks;
+    int max_passes, max_bins;
+};
+
+SegLayout seg_layout(int key_bytes, bool vals, size_t n_total, size_t max_segs, int max_passes, int max_bins,
+                     size_t extra_head);
+SegBuffers carve_seg_buffers(void* ws, const SegLayout& L);
+uint32_t seg_tile_keys(int key_bytes, bool vals);
+
+// Scatter passes over the large segments already listed in B (their tile and
+// chunk ranges reserved, totals in B.hdr): maps, counts, scans and `passes`
+// passes of `digit_bits` bits over (key - key_lo).  Pass 0 reads src; pass p
+// writes out when (passes-1-p) is even, else the workspace buffer, so the
+// last pass lands in out.  src must not be the buffer pass 0 writes.
+rs_status enqueue_large_passes(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,
+                               uint32_t* out_v, const SegBuffers& B, int passes, int digit_bits,
+                               cudaStream_t stream);
+
+// Shared-memory sorts of a device list of segments (count on the device).
+// bucket: device BucketParams for bucket mode, or null.
+rs_status enqueue_local_sorts(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,
+                              uint32_t* out_v, const SegDesc* segs, const uint32_t* count, size_t max_count,
+                              const void* bucket, cudaStream_t stream);
+
+}  // namespace rs

@@ -1,0 +1,98 @@
+"""GPU parity of the segmented sort: every segment must equal the oracle's
+sort of that segment alone (keys and values, zero tolerance)."""
+import numpy as np
+import pytest
+
+import synth
+from tests._util import assert_same, from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(rs, keys, sizes, vals=None, key_bits=0, in_place=False):
+    import torch
+
+    off = synth.segment_offsets(sizes)
+    kd = to_dev(keys)
+    vd = to_dev(vals) if vals is not None else None
+    od = to_dev(off.astype(np.uint64))
+    if in_place:
+        ok, ov = rs.segmented_sort(kd, od, vd, key_bits, out=kd, out_values=vd)
+    else:
+        ok, ov = rs.segmented_sort(kd, od, vd, key_bits)
+    torch.cuda.synchronize()
+    return off, from_dev(ok, keys.dtype), (from_dev(ov, np.uint32) if vals is not None else None)
+
+
+def _check(rs, oracle, keys, sizes, vals=None, key_bits=0, in_place=False, what=""):
+    kbits = key_bits or 8 * keys.dtype.itemsize
+    off, gk, gv = _run(rs, keys, sizes, vals, key_bits, in_place)
+    if vals is None:
+        want = oracle.segmented_radix_sort(keys, off, None, kbits)
+        assert_same(gk, want, what)
+    else:
+        wk, wv = oracle.segmented_radix_sort(keys, off, vals, kbits)
+        assert_same(gk, wk, what + " keys")
+        assert_same(gv, wv, what + " values")
+
+
+EDGE_SIZES = [0, 1, 2, 3, 0, 255, 256, 4095, 4096, 4097, 4608, 4609, 9217, 70_001, 0, 1, 3072, 3073, 200_000]
+
+
+@pytest.mark.parametrize("kb,with_values", [(4, False), (4, True), (8, False), (8, True)])
+def test_segment_size_edges(rs, oracle, kb, with_values):
+    n = sum(EDGE_SIZES)
+    keys = synth.u32(n, 40, 0) if kb == 4 else synth.keys_u64(n, 64, seed=41)
+    vals = synth.index_values(n) if with_values else None
+    _check(rs, oracle, keys, EDGE_SIZES, vals, what=f"edges kb={kb} v={with_values}")
+
+
+def test_log_uniform_batch_like_the_batched_workload(rs, oracle):
+    """300 arrays with sizes log-uniform in [256, 200000] (the batched
+    workload's size law, scaled down), uniform u32 keys."""
+    sizes = synth.log_uniform_sizes(300, 256, 200_000, seed=0)
+    n = int(sizes.sum())
+    keys = synth.u32(n, 42, 0)
+    _check(rs, oracle, keys, sizes, None, what="log-uniform")
+    _check(rs, oracle, keys, sizes, synth.index_values(n), what="log-uniform kv")
+
+
+@pytest.mark.parametrize("dist", [1, 3, 4, 6, 8])
+def test_distributions(rs, oracle, dist):
+    sizes = [5000, 300, 100_000, 4096, 17]
+    n = sum(sizes)
+    keys = synth.keys_u32(n, dist, seed=dist)
+    _check(rs, oracle, keys, sizes, synth.index_values(n), what=synth.DISTS[dist])
+
+
+@pytest.mark.parametrize("key_bits", [1, 12, 24, 31])
+def test_key_bits(rs, oracle, key_bits):
+    sizes = [10_000, 3000, 50_000]
+    n = sum(sizes)
+    keys = synth.u32(n, 43 + key_bits, 0) >> np.uint32(32 - key_bits)
+    _check(rs, oracle, keys, sizes, synth.index_values(n), key_bits, what=f"key_bits {key_bits}")
+
+
+@pytest.mark.parametrize("key_bits", [32, 24])
+def test_in_place(rs, oracle, key_bits):
+    sizes = [7000, 100, 60_000, 0, 4096]
+    n = sum(sizes)
+    keys = synth.u32(n, 44, 0) >> np.uint32(32 - key_bits)
+    _check(rs, oracle, keys, sizes, synth.index_values(n), key_bits, in_place=True, what=f"in place {key_bits}")
+
+
+def test_single_segment_equals_plain_sort(rs, oracle):
+    n = 1_000_003
+    keys = synth.u32(n, 45, 0)
+    _check(rs, oracle, keys, [n], None, what="one segment")
+
+
+def test_bad_offsets_are_reported(rs):
+    import torch
+
+    keys = to_dev(synth.u32(100, 46, 0))
+    off = to_dev(np.array([0, 50, 40, 100], np.uint64))  # decreasing
+    ws = rs.workspace(rs.rs_segmented_workspace_bytes(4, 0, 100, 3, 32))
+    out = torch.empty_like(keys)
+    assert rs.rs_sort_segmented_u32(keys, out, None, None, off, 3, 100, 32, ws, ws.numel()) == 0
+    assert rs.get_status(ws) == 1  # RS_ERR_INVALID_ARG recorded on the device
