@@ -103,7 +103,8 @@ RS_API rs_status rs_config_get(int key_bytes, int has_values, int i, rs_config* 
 /* Workspace bytes for one call of the given algorithm, valid for every
  * compiled configuration with digit_bits <= 8.  key_bytes: 4 or 8.  key_bits: 0 means the full key
  * width.  num_buckets: bucket count for RS_ALGO_BUCKET (0 = max(1, n/16));
- * ignored for radix.  in_place: nonzero if keys_out will equal keys_in.
+ * ignored for radix.  in_place: nonzero if keys_out will equal keys_in (the
+ * workspace is the same either way).
  * Returns 0 for invalid arguments. */
 RS_API size_t rs_workspace_bytes(int algo, int key_bytes, int has_values, size_t n, int key_bits,
                           size_t num_buckets, int in_place);
@@ -138,6 +139,29 @@ RS_API rs_status rs_sort_u32_ex(const uint32_t* keys_in, uint32_t* keys_out, con
 RS_API rs_status rs_sort_u64_ex(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
                          uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
                          rs_stream_t stream, const rs_config* cfg);
+
+/* ---------------------------------------------------------------------------
+ * Bucket sort, Sec. 2.3 Algorithm 2: every key goes to bucket
+ *     b(k) = floor((k - min_key) * num_buckets / (max_key - min_key + 1))
+ * (exact; the paper's n * A[i] / M with an inclusive key range), in input
+ * order; every bucket is sorted (insertion sort, Sec. 2.2 Algorithm 1, for
+ * buckets of up to 48 keys, a stable radix sort of the bucket's key range for
+ * larger ones); the buckets are concatenated in bucket order.  The result is
+ * the stable sort of the keys, identical to rs_sort_*.
+ * min_key > max_key: the bounds are the keys' own minimum and maximum,
+ * computed on the device.  Otherwise every key must lie in [min_key,
+ * max_key]; a key outside is reported as RS_ERR_KEY_RANGE by rs_get_status()
+ * (output unspecified, writes stay inside the outputs).
+ * num_buckets: 0 means max(1, n/16); at most 2^32.
+ * Workspace: rs_workspace_bytes(RS_ALGO_BUCKET, key_bytes, has_values, n, 0,
+ * num_buckets, in_place).  In place (keys_out == keys_in) is allowed.
+ */
+RS_API rs_status bs_sort_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
+                             uint32_t* vals_out, size_t n, uint32_t min_key, uint32_t max_key, size_t num_buckets,
+                             void* ws, size_t ws_bytes, rs_stream_t stream);
+RS_API rs_status bs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
+                             uint32_t* vals_out, size_t n, uint64_t min_key, uint64_t max_key, size_t num_buckets,
+                             void* ws, size_t ws_bytes, rs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Building blocks: one step of the radix path each.

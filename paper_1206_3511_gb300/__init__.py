@@ -14,7 +14,7 @@ bits are sorted as unsigned).  Values are 32-bit (uint32 or int32).
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (rs_segmented_workspace_bytes, rs_sort_segmented_u32, rs_sort_segmented_u64,
+from ._lib import (bs_sort_u32, bs_sort_u64, rs_segmented_workspace_bytes, rs_sort_segmented_u32, rs_sort_segmented_u64,
                    RS_ALGO_BUCKET, RS_ALGO_RADIX, STATUS, RsConfig, load, rs_config_count, rs_config_get,
                    rs_counting_pass_u32, rs_counting_pass_u64, rs_default_config, rs_digit_counts_u32,
                    rs_digit_counts_u64, rs_get_status, rs_launch_count, rs_profile_enable, rs_profile_read,
@@ -29,6 +29,7 @@ __all__ = [
     "rs_config_count", "rs_config_get", "RsConfig", "RS_ALGO_RADIX", "RS_ALGO_BUCKET", "STATUS",
     "rs_profile_enable", "rs_profile_read", "rs_launch_count", "rs_sort_u32_noalloc",
     "rs_segmented_workspace_bytes", "rs_sort_segmented_u32", "rs_sort_segmented_u64", "segmented_sort",
+    "bs_sort_u32", "bs_sort_u64", "bucket_sort",
 ]
 
 
@@ -149,4 +150,29 @@ def segmented_sort(keys, offsets, values=None, key_bits: int = 0, out=None, out_
         ws = workspace(rs_segmented_workspace_bytes(kb, values is not None, n, max(nseg, 1), key_bits), keys.device)
     fn = rs_sort_segmented_u32 if kb == 4 else rs_sort_segmented_u64
     check(fn(keys, out, values, out_values, offsets, nseg, n, key_bits, ws, ws.numel(), stream), "rs_sort_segmented")
+    return out, out_values
+
+
+def bucket_sort(keys, values=None, min_key=None, max_key=None, num_buckets: int = 0, out=None, out_values=None,
+                ws=None, stream=None):
+    """Stable bucket sort (bs_sort_u32 / bs_sort_u64).  min_key/max_key: the
+    declared key range (both None: computed on the device).  num_buckets 0
+    means max(1, n // 16).  Returns (keys, values or None)."""
+    import torch
+
+    _check_tensor(keys, "keys")
+    kb = key_bytes_of(keys)
+    n = keys.numel()
+    if (min_key is None) != (max_key is None):
+        raise ValueError("give both min_key and max_key, or neither")
+    if min_key is None:
+        min_key, max_key = (1, 0)  # min > max: bounds from the data
+    out = torch.empty_like(keys) if out is None else out
+    if values is not None and out_values is None:
+        out_values = torch.empty_like(values)
+    if ws is None:
+        ws = workspace(rs_workspace_bytes(RS_ALGO_BUCKET, kb, values is not None, n, 0, num_buckets, out is keys),
+                       keys.device)
+    fn = bs_sort_u32 if kb == 4 else bs_sort_u64
+    check(fn(keys, out, values, out_values, n, min_key, max_key, num_buckets, ws, ws.numel(), stream), "bs_sort")
     return out, out_values

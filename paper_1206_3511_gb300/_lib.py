@@ -49,6 +49,8 @@ SIGNATURES: dict[str, tuple] = {
     "rs_sort_u64": (_I, [_P, _P, _P, _P, _SZ, _I, _P, _SZ, _P]),
     "rs_sort_u32_ex": (_I, [_P, _P, _P, _P, _SZ, _I, _P, _SZ, _P, _c.POINTER(RsConfig)]),
     "rs_sort_u64_ex": (_I, [_P, _P, _P, _P, _SZ, _I, _P, _SZ, _P, _c.POINTER(RsConfig)]),
+    "bs_sort_u32": (_I, [_P, _P, _P, _P, _SZ, _U32, _U32, _SZ, _P, _SZ, _P]),
+    "bs_sort_u64": (_I, [_P, _P, _P, _P, _SZ, _U64, _U64, _SZ, _P, _SZ, _P]),
     "rs_digit_counts_u32": (_I, [_P, _SZ, _I, _I, _P, _P, _SZ, _P]),
     "rs_digit_counts_u64": (_I, [_P, _SZ, _I, _I, _P, _P, _SZ, _P]),
     "rs_counting_pass_u32": (_I, [_P, _P, _P, _P, _SZ, _I, _I, _P, _SZ, _P]),
@@ -181,6 +183,18 @@ def rs_sort_u64_ex(keys_in, keys_out, vals_in, vals_out, n, key_bits, ws, ws_byt
     c = _as_cfg(cfg)
     return _call("rs_sort_u64_ex", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, key_bits, ptr(ws),
                  ws_bytes, stream_handle(stream), _c.byref(c) if c is not None else None)
+
+
+def bs_sort_u32(keys_in, keys_out, vals_in, vals_out, n, min_key, max_key, num_buckets, ws, ws_bytes,
+                stream=None) -> int:
+    return _call("bs_sort_u32", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, min_key, max_key,
+                 num_buckets, ptr(ws), ws_bytes, stream_handle(stream))
+
+
+def bs_sort_u64(keys_in, keys_out, vals_in, vals_out, n, min_key, max_key, num_buckets, ws, ws_bytes,
+                stream=None) -> int:
+    return _call("bs_sort_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, min_key, max_key,
+                 num_buckets, ptr(ws), ws_bytes, stream_handle(stream))
 
 
 def rs_digit_counts_u32(keys, n, key_bits, digit_bits, counts_out, ws, ws_bytes, stream=None) -> int:

@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "rs_radix.h"
+#include "rs_segmented.h"
 
 namespace rs {
 
@@ -112,6 +112,7 @@ size_t rs_workspace_bytes(int algo, int key_bytes, int has_values, size_t n, int
     if (key_bits < 1 || key_bits > 8 * key_bytes) return 0;
     if (n > RS_MAX_KEYS) return 0;
     if (algo == RS_ALGO_RADIX) return radix_workspace_bytes(key_bytes, has_values != 0, n, key_bits);
+    if (algo == RS_ALGO_BUCKET) return bucket_workspace_bytes(key_bytes, has_values != 0, n, num_buckets);
     return 0;
 }
 

@@ -1,0 +1,575 @@
+// rs_bucket.cu -- bucket sort (Sec. 2.3, Algorithm 2) on the GPU.
+//
+// The paper inserts every key into bucket b(k) (range-divide), sorts each
+// bucket with insertion sort and concatenates the buckets.  Here the buckets
+// live in contiguous ranges of the output (their concatenation costs
+// nothing), and the insert step is a stable partition by bucket id done
+// most-significant bits first:
+//   level 1: a one-sweep pass partitions all keys by the top (up to 8) bits of
+//            their bucket id;
+//   level 2: partitions still larger than one block's shared memory are
+//            partitioned by the next (up to 8) bits with a segmented pass;
+//   leaves:  every partition of at most 4096 keys is sorted inside one block:
+//            a stable counting pass by exact bucket (the insert step) and an
+//            insertion sort of each bucket by one thread (Algorithm 1);
+//   overflow: a partition that is still too large when the bucket bits run
+//            out (skewed keys) is radix-sorted on its keys relative to the
+//            lowest key its buckets can hold, using only the bits that span;
+//   constant partitions (a single possible key) need no sorting at all.
+// Every step is stable, so equal keys keep their input order (Sec. 2.3 last
+// paragraph), and the result equals the stable sort of the keys.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "rs_bucket.cuh"
+#include "rs_segmented.h"
+
+namespace rs {
+
+namespace {
+
+// ---------------------------------------------------------------- kernels
+template <typename KeyT>
+__global__ void __launch_bounds__(256) k_minmax(const KeyT* __restrict__ keys, size_t n, unsigned long long* mm) {
+    __shared__ unsigned long long s_lo[8], s_hi[8];
+    unsigned long long lo = ~0ull, hi = 0ull;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = (unsigned long long)__ldcs(keys + i);
+        lo = k < lo ? k : lo;
+        hi = k > hi ? k : hi;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(kFullMask, lo, o), b = __shfl_xor_sync(kFullMask, hi, o);
+        lo = a < lo ? a : lo;
+        hi = b > hi ? b : hi;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo;
+        s_hi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) {
+            lo = s_lo[w] < lo ? s_lo[w] : lo;
+            hi = s_hi[w] > hi ? s_hi[w] : hi;
+        }
+        atomicMin(&mm[0], lo);
+        atomicMax(&mm[1], hi);
+    }
+}
+
+// Bucket parameters from the declared bounds or from the reduced min/max.
+__global__ void k_bucket_params(BucketParams* bp, const unsigned long long* mm, uint64_t min_key, uint64_t max_key,
+                                uint64_t nb, int key_bytes) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint64_t lo = mm ? mm[0] : min_key, hi = mm ? mm[1] : max_key;
+    const uint64_t range = hi - lo + 1;  // 0 means 2^64
+    BucketParams p{};
+    p.min = lo;
+    p.max = hi;
+    p.nb = nb;
+    p.range = range;
+    p.recip = (key_bytes == 4 && range != 0) ? (~0ull / range) : 0ull;
+    p.bbits = nb > 1 ? 64u - __clzll(nb - 1) : 0u;
+    p.valid = 1u;
+    *bp = p;
+}
+
+// Range check of the declared bounds in the level-1 counting kernel.
+struct BucketCountDigits {
+    const BucketParams* src;
+    int shift;
+    uint32_t mask;
+    BucketParams bp;
+    __device__ __forceinline__ void init() { bp = load_bucket_params(src); }
+    template <typename KeyT>
+    __device__ __forceinline__ uint32_t operator()(KeyT k, int) const {
+        return (uint32_t)(bucket_of(bp, k) >> shift) & mask;
+    }
+    template <typename KeyT>
+    __device__ __forceinline__ bool in_range(KeyT k) const {
+        return (uint64_t)k >= bp.min && (uint64_t)k <= bp.max;
+    }
+};
+
+// ceil(b * range / nb): how many key values lie below bucket b (exact).
+__device__ __forceinline__ uint64_t keys_below_bucket(const BucketParams& bp, uint64_t b) {
+    const unsigned __int128 r = bp.range ? (unsigned __int128)bp.range : ((unsigned __int128)1 << 64);
+    const unsigned __int128 x = (unsigned __int128)b * r;
+    return (uint64_t)((x + bp.nb - 1) / bp.nb);
+}
+
+__device__ __forceinline__ uint32_t bit_length(uint64_t x) { return x ? 64u - __clzll(x) : 0u; }
+
+struct PlanLevel {
+    const BucketParams* bp;
+    int shift;        // position of this level's digit in the bucket id
+    int digit_bits;   // bits of this level's digit
+    uint32_t cap;     // largest partition sorted in shared memory
+    uint32_t tile_keys;
+    // parents: either the whole array (parents == null) or a device list
+    const SegDesc* parents;
+    const uint32_t* num_parents;
+    uint64_t n_total;          // whole-array parent size
+    const uint32_t* starts;    // [parent][bins] exclusive prefixes of the digit counts
+    const uint32_t* counts;    // [bins] counts (whole-array parent only)
+    int in_out;                // 1: the children's keys now sit in keys_out
+    int key_width;             // bits of the key type
+    // outputs
+    SegDesc* leaf;
+    uint32_t* num_leaf;
+    SegDesc* next;             // null: no further level
+    SegPlanHdr* next_hdr;
+    SegDesc* ovf;
+    SegPlanHdr* ovf_hdr;
+    SegDesc* copy;
+    uint32_t* num_copy;
+};
+
+// One thread per (parent, digit): describe the child partition and hand it to
+// the right list.
+__global__ void k_bucket_plan(PlanLevel pl) {
+    const uint32_t bins = 1u << pl.digit_bits;
+    const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t parent = (uint32_t)(gid / bins), d = (uint32_t)(gid % bins);
+    const uint32_t nparents = pl.parents ? *pl.num_parents : 1u;
+    if (parent >= nparents) return;
+    const BucketParams bp = load_bucket_params(pl.bp);
+    uint64_t pstart = 0, pn = pl.n_total, pb_lo = 0;
+    if (pl.parents) {
+        const SegDesc ps = pl.parents[parent];
+        pstart = ps.start;
+        pn = ps.n;
+        pb_lo = ps.aux;
+    }
+    const uint32_t* row = pl.starts + (size_t)parent * bins;
+    const uint64_t off = row[d];
+    const uint64_t end = pl.counts ? off + pl.counts[d] : ((d + 1 < bins) ? row[d + 1] : pn);
+    if (end <= off) return;
+    const uint64_t n = end - off;
+    const uint64_t b_lo = pb_lo + ((uint64_t)d << pl.shift);
+    if (b_lo >= bp.nb) return;  // cannot hold keys
+    uint64_t span = (uint64_t)1 << pl.shift;
+    if (span > bp.nb - b_lo) span = bp.nb - b_lo;
+    const uint64_t below = keys_below_bucket(bp, b_lo);
+    const uint64_t width = keys_below_bucket(bp, b_lo + span) - below;  // key values the span can hold
+    SegDesc c{};
+    c.start = pstart + off;
+    c.n = (uint32_t)n;
+    c.key_lo = bp.min + below;
+    c.bits = width <= 1 ? 0u : min(bit_length(width - 1), (uint32_t)pl.key_width);
+    c.aux = b_lo;
+    if (c.bits == 0) {  // one possible key: already in order
+        if (!pl.in_out) pl.copy[atomicAdd(pl.num_copy, 1u)] = c;
+        return;
+    }
+    if (n <= pl.cap) {
+        c.chunk0 = span > 0xffffffffull ? 0xffffffffu : (uint32_t)span;
+        pl.leaf[atomicAdd(pl.num_leaf, 1u)] = c;
+        return;
+    }
+    if (pl.next && pl.shift > 0) {
+        c.key_lo = 0;  // the next level takes digits of the bucket id of the whole key
+        append_large(pl.next, &pl.next_hdr->num_large, &pl.next_hdr->total_tiles, &pl.next_hdr->total_chunks, c,
+                     pl.tile_keys);
+        return;
+    }
+    append_large(pl.ovf, &pl.ovf_hdr->num_large, &pl.ovf_hdr->total_tiles, &pl.ovf_hdr->total_chunks, c,
+                 pl.tile_keys);
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(256) k_copy_segments(const KeyT* __restrict__ src_k, const uint32_t* __restrict__ src_v,
+                                                       KeyT* dst_k, uint32_t* dst_v, const SegDesc* segs,
+                                                       const uint32_t* count) {
+    if (blockIdx.x >= *count) return;
+    const SegDesc s = segs[blockIdx.x];
+    for (uint32_t i = threadIdx.x; i < s.n; i += blockDim.x) {
+        dst_k[s.start + i] = src_k[s.start + i];
+        if (src_v) dst_v[s.start + i] = src_v[s.start + i];
+    }
+}
+
+template <typename KeyT, bool VALS>
+cudaError_t launch_plain_bucket_pass(const PassParams<BucketDigit>& p, cudaStream_t s) {
+    using S = SegShape<KeyT, VALS>;
+    using Shape = OnesweepShape<KeyT, VALS, S::kBlock, S::kItems>;
+    auto kern = k_onesweep<KeyT, VALS, S::kBlock, S::kItems, S::kMinB, BucketDigit>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)Shape::smem_bytes(8));
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    KernelScope scope("bucket_pass", s);
+    kern<<<p.num_tiles, S::kBlock, Shape::smem_bytes(p.digit_bits), s>>>(p);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- layout
+struct BucketPlanInfo {
+    int key_bytes;
+    bool vals;
+    size_t n, nb;
+    int bbits;             // bits of the bucket id (at least 1)
+    int d1, shift1;        // level 1 digit
+    bool level2;
+    int d2, shift2;        // level 2 digit
+    int ovf_passes, ovf_bits;  // overflow radix: passes and digit bits (0 passes: none possible)
+    size_t max_leaf2, max_ovf, max_tiles, max_chunks, max_rows;
+};
+
+int bit_length_host(uint64_t x) {
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+BucketPlanInfo plan_info(int key_bytes, bool vals, size_t n, size_t nb, bool bounds_known, uint64_t min_key,
+                         uint64_t max_key) {
+    BucketPlanInfo I{};
+    I.key_bytes = key_bytes;
+    I.vals = vals;
+    I.n = n;
+    I.nb = nb;
+    I.bbits = std::max(1, bit_length_host(nb - 1));
+    I.d1 = std::min(8, I.bbits);
+    I.shift1 = I.bbits - I.d1;
+    I.level2 = I.shift1 > 0;
+    I.d2 = I.level2 ? std::min(8, I.shift1) : 0;
+    I.shift2 = I.level2 ? I.shift1 - I.d2 : 0;
+    // overflow partitions span 2^last_shift buckets; bound the key bits they
+    // can need from the declared range (or the full key width)
+    const int last_shift = I.level2 ? I.shift2 : I.shift1;
+    const int width_bits = 8 * key_bytes;
+    long double range = bounds_known ? (long double)(max_key - min_key) + 1.0L : std::pow(2.0L, width_bits);
+    const long double span_keys = std::ceil(range * std::pow(2.0L, last_shift) / (long double)nb) + 1.0L;
+    int bits = span_keys <= 1.0L ? 0 : (int)std::ceil(std::log2(span_keys));
+    if (bits > width_bits) bits = width_bits;
+    I.ovf_bits = 0;
+    I.ovf_passes = 0;
+    if (bits > 0) {
+        int P = (bits + 7) / 8;
+        const bool from_out = I.level2;  // overflow data sits in keys_out after level 2, else in the buffer
+        if ((P % 2 == 0) != from_out) ++P;  // pass 0 must not write the array it reads
+        I.ovf_passes = P;
+        I.ovf_bits = (bits + P - 1) / P;
+        if (I.ovf_bits < 1) I.ovf_bits = 1;
+    }
+    const uint32_t tk = seg_tile_keys(key_bytes, vals);
+    const size_t parents2 = (size_t)1 << I.d1;
+    I.max_leaf2 = I.level2 ? std::min<size_t>(parents2 << I.d2, n) : 1;
+    I.max_ovf = std::min<size_t>(n / kLocalCap + 1, I.level2 ? (parents2 << I.d2) : parents2);
+    I.max_tiles = n / tk + std::max<size_t>(parents2, I.max_ovf) + 2;
+    I.max_chunks = n / kSegChunk + std::max<size_t>(parents2, I.max_ovf) + 2;
+    I.max_rows = std::max<size_t>(parents2 * 256, I.max_ovf * (size_t)std::max(1, I.ovf_passes) * 256);
+    return I;
+}
+
+struct BucketLayout {
+    size_t off_params, off_mm, off_hdr, off_counts1, off_scan1, off_leaf1, off_copy, off_next, off_leaf2, off_ovf,
+        off_tile_seg, off_chunk_seg, off_rows, off_status0, off_status1, off_tmp_keys, off_tmp_vals, total;
+};
+
+BucketLayout bucket_layout(const BucketPlanInfo& I) {
+    BucketLayout L{};
+    Carver c;
+    c.take(sizeof(WsHeader));
+    L.off_params = c.take(sizeof(BucketParams));
+    L.off_mm = c.take(16);
+    L.off_hdr = c.take(4 * sizeof(SegPlanHdr));
+    L.off_counts1 = c.take(256 * 4);
+    L.off_scan1 = c.take(256 * 4);
+    L.off_leaf1 = c.take(256 * sizeof(SegDesc));
+    L.off_copy = c.take(256 * sizeof(SegDesc));
+    L.off_next = c.take(256 * sizeof(SegDesc));
+    L.off_leaf2 = c.take(I.max_leaf2 * sizeof(SegDesc));
+    L.off_ovf = c.take(I.max_ovf * sizeof(SegDesc));
+    L.off_tile_seg = c.take(I.max_tiles * 4);
+    L.off_chunk_seg = c.take(I.max_chunks * 4);
+    L.off_rows = c.take(I.max_rows * 4);
+    L.off_status0 = c.take(I.max_tiles * 256 * 4);
+    L.off_status1 = c.take(I.max_tiles * 256 * 4);
+    L.off_tmp_keys = c.take(I.n * I.key_bytes);
+    L.off_tmp_vals = I.vals ? c.take(I.n * 4) : 0;
+    L.total = c.off;
+    return L;
+}
+
+}  // namespace
+
+size_t bucket_workspace_bytes(int key_bytes, bool vals, size_t n, size_t nb) {
+    if (nb == 0) nb = std::max<size_t>(1, n / 16);
+    return bucket_layout(plan_info(key_bytes, vals, n, nb, false, 0, 0)).total;
+}
+
+template <typename KeyT, bool VALS>
+static rs_status bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                               size_t n, uint64_t min_key, uint64_t max_key, size_t nb, void* ws, size_t ws_bytes,
+                               cudaStream_t stream) {
+    const bool bounds_known = min_key <= max_key;
+    const BucketPlanInfo I = plan_info(sizeof(KeyT), VALS, n, nb, bounds_known, min_key, max_key);
+    const BucketLayout L = bucket_layout(I);
+    if (ws_bytes < L.total) return RS_ERR_WORKSPACE;
+    unsigned char* base = static_cast<unsigned char*>(ws);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(base);
+    BucketParams* bp = reinterpret_cast<BucketParams*>(base + L.off_params);
+    unsigned long long* mm = reinterpret_cast<unsigned long long*>(base + L.off_mm);
+    SegPlanHdr* h = reinterpret_cast<SegPlanHdr*>(base + L.off_hdr);
+    SegPlanHdr* h_leaf1 = h + 0;  // num_small: leaf1 count, num_next: copy count
+    SegPlanHdr* h_next = h + 1;   // level-2 parents (num_large, tiles, chunks), num_small: leaf2 count
+    SegPlanHdr* h_ovf = h + 2;    // overflow partitions
+    uint32_t* counts1 = reinterpret_cast<uint32_t*>(base + L.off_counts1);
+    uint32_t* scan1 = reinterpret_cast<uint32_t*>(base + L.off_scan1);
+    SegDesc* leaf1 = reinterpret_cast<SegDesc*>(base + L.off_leaf1);
+    SegDesc* copyl = reinterpret_cast<SegDesc*>(base + L.off_copy);
+    SegDesc* next = reinterpret_cast<SegDesc*>(base + L.off_next);
+    SegDesc* leaf2 = reinterpret_cast<SegDesc*>(base + L.off_leaf2);
+    SegDesc* ovf = reinterpret_cast<SegDesc*>(base + L.off_ovf);
+    uint32_t* tile_seg = reinterpret_cast<uint32_t*>(base + L.off_tile_seg);
+    uint32_t* chunk_seg = reinterpret_cast<uint32_t*>(base + L.off_chunk_seg);
+    uint32_t* rows = reinterpret_cast<uint32_t*>(base + L.off_rows);
+    uint32_t* status[2] = {reinterpret_cast<uint32_t*>(base + L.off_status0),
+                           reinterpret_cast<uint32_t*>(base + L.off_status1)};
+    KeyT* tmp_k = reinterpret_cast<KeyT*>(base + L.off_tmp_keys);
+    uint32_t* tmp_v = VALS ? reinterpret_cast<uint32_t*>(base + L.off_tmp_vals) : nullptr;
+    const uint32_t tk = SegShape<KeyT, VALS>::kTile;
+
+    // header, plan counters and level-1 counts start at zero
+    RS_CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(WsHeader), stream));
+    RS_CUDA_TRY(cudaMemsetAsync(h, 0, 4 * sizeof(SegPlanHdr), stream));
+    RS_CUDA_TRY(cudaMemsetAsync(counts1, 0, 256 * 4, stream));
+
+    // b1: bounds (Algorithm 2 assumes every key lies in [min, max])
+    if (!bounds_known) {
+        RS_CUDA_TRY(cudaMemsetAsync(mm, 0xff, 8, stream));
+        RS_CUDA_TRY(cudaMemsetAsync(mm + 1, 0, 8, stream));
+        KernelScope scope("minmax", stream);
+        size_t grid = std::min<size_t>((n + 255) / 256, (size_t)device_sm_count() * 8);
+        k_minmax<KeyT><<<(unsigned)std::max<size_t>(grid, 1), 256, 0, stream>>>(keys_in, n, mm);
+        if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
+    }
+    {
+        KernelScope scope("bucket_params", stream);
+        k_bucket_params<<<1, 32, 0, stream>>>(bp, bounds_known ? nullptr : mm, min_key, max_key, nb, (int)sizeof(KeyT));
+        if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
+    }
+
+    // b2-b4, level 1: count the top digit of every bucket id, prefix, stable scatter keys_in -> buffer
+    const uint32_t bins1 = 1u << I.d1;
+    const uint32_t tiles1 = (uint32_t)((n + tk - 1) / tk);
+    {
+        CountParams cp{};
+        cp.keys = keys_in;
+        cp.n = n;
+        cp.passes = 1;
+        cp.bins = bins1;
+        cp.counts = counts1;
+        cp.scan = scan1;
+        cp.zero_ptr = status[0];
+        cp.zero_words = (size_t)tiles1 * bins1;
+        cp.hdr = hdr;
+        BucketCountDigits dg{bp, I.shift1, bins1 - 1u, {}};
+        if (launch_counts<KeyT>(cp, dg, count_grid(n), stream) != cudaSuccess) return RS_ERR_CUDA;
+    }
+    {
+        PassParams<BucketDigit> pp{};
+        pp.keys_in = keys_in;
+        pp.keys_out = tmp_k;
+        pp.vals_in = vals_in;
+        pp.vals_out = tmp_v;
+        pp.n = (uint32_t)n;
+        pp.num_tiles = tiles1;
+        pp.digit_bits = I.d1;
+        pp.op = BucketDigit{bp, I.shift1, bins1 - 1u, {}};
+        pp.digit_base = scan1;
+        pp.status = status[0];
+        pp.status_next = status[1];
+        pp.tile_ctr = &hdr->tile_ctr[0];
+        pp.hdr = hdr;
+        pp.spin_limit = debug_spin_limit();
+        pp.stall_tile = debug_stall_tile();
+        if (launch_plain_bucket_pass<KeyT, VALS>(pp, stream) != cudaSuccess) return RS_ERR_CUDA;
+    }
+    PlanLevel pl{};
+    pl.bp = bp;
+    pl.cap = kLocalCap;
+    pl.tile_keys = tk;
+    pl.key_width = 8 * (int)sizeof(KeyT);
+    pl.copy = copyl;
+    pl.num_copy = &h_leaf1->num_next;
+    pl.ovf = ovf;
+    pl.ovf_hdr = h_ovf;
+    {
+        pl.shift = I.shift1;
+        pl.digit_bits = I.d1;
+        pl.parents = nullptr;
+        pl.n_total = n;
+        pl.starts = scan1;
+        pl.counts = counts1;
+        pl.in_out = 0;
+        pl.leaf = leaf1;
+        pl.num_leaf = &h_leaf1->num_small;
+        pl.next = I.level2 ? next : nullptr;
+        pl.next_hdr = h_next;
+        KernelScope scope("bucket_plan", stream);
+        k_bucket_plan<<<(bins1 + 255) / 256, 256, 0, stream>>>(pl);
+        if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
+    }
+
+    // level 2: partitions above the shared-memory capacity, by the next digit, buffer -> keys_out
+    if (I.level2) {
+        const uint32_t bins2 = 1u << I.d2;
+        const size_t parents2 = bins1;
+        {
+            KernelScope scope("plan_maps", stream);
+            k_plan_maps<<<(unsigned)parents2, 256, 0, stream>>>(next, h_next, tk, tile_seg, chunk_seg);
+            if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
+        }
+        RS_CUDA_TRY(cudaMemsetAsync(rows, 0, parents2 * bins2 * 4, stream));
+        BucketDigits dg{bp, I.shift2, bins2 - 1u, {}};
+        if (launch_seg_counts<KeyT>(tmp_k, next, h_next, chunk_seg, I.max_chunks, dg, 1, bins2, rows, status[0],
+                                    I.max_tiles * (size_t)bins2, stream) != cudaSuccess)
+            return RS_ERR_CUDA;
+        {
+            KernelScope scope("seg_scan", stream);
+            k_seg_scan<<<(unsigned)parents2, 256, (bins2 + 256 / 32 + 1) * 4, stream>>>(rows, h_next, 1, bins2, 0);
+            if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
+        }
+        SegPassParams<BucketDigit> sp{};
+        sp.base.keys_in = tmp_k;
+        sp.base.keys_out = keys_out;
+        sp.base.vals_in = tmp_v;
+        sp.base.vals_out = vals_out;
+        sp.base.digit_bits = I.d2;
+        sp.base.op = BucketDigit{bp, I.shift2, bins2 - 1u, {}};
+        sp.base.status = status[0];
+        sp.base.status_next = nullptr;
+        sp.base.tile_ctr = &hdr->tile_ctr[1];
+        sp.base.hdr = hdr;
+        sp.base.spin_limit = debug_spin_limit();
+        sp.base.stall_tile = debug_stall_tile();
+        sp.segs = next;
+        sp.hdr = h_next;
+        sp.tile_seg = tile_seg;
+        sp.seg_base = rows;
+        sp.pass = 0;
+        sp.passes = 1;
+        if (launch_seg_pass<KeyT, VALS, BucketDigit>(sp, I.max_tiles, stream) != cudaSuccess) return RS_ERR_CUDA;
+        pl.shift = I.shift2;
+        pl.digit_bits = I.d2;
+        pl.parents = next;
+        pl.num_parents = &h_next->num_large;
+        pl.starts = rows;
+        pl.counts = nullptr;
+        pl.in_out = 1;
+        pl.leaf = leaf2;
+        pl.num_leaf = &h_next->num_small;
+        pl.next = nullptr;
+        KernelScope scope("bucket_plan", stream);
+        k_bucket_plan<<<(unsigned)((parents2 * bins2 + 255) / 256), 256, 0, stream>>>(pl);
+        if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
+    }
+
+    // partitions that can hold only one key value move unchanged
+    {
+        KernelScope scope("copy_segments", stream);
+        k_copy_segments<KeyT><<<bins1, 256, 0, stream>>>(tmp_k, tmp_v, keys_out, vals_out, copyl, &h_leaf1->num_next);
+        if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
+    }
+    // b5: sort each bucket of the shared-memory partitions (Algorithm 1 per bucket)
+    rs_status st = enqueue_local_sorts(sizeof(KeyT), VALS, tmp_k, tmp_v, keys_out, vals_out, leaf1,
+                                       &h_leaf1->num_small, bins1, bp, stream);
+    if (st != RS_OK) return st;
+    if (I.level2) {
+        st = enqueue_local_sorts(sizeof(KeyT), VALS, keys_out, vals_out, keys_out, vals_out, leaf2,
+                                 &h_next->num_small, I.max_leaf2, bp, stream);
+        if (st != RS_OK) return st;
+    }
+    // overflow partitions: radix on the key bits their buckets span
+    if (I.ovf_passes > 0) {
+        SegBuffers B{};
+        B.ws_hdr = hdr;
+        B.hdr = h_ovf;
+        B.large = ovf;
+        B.small = nullptr;
+        B.tile_seg = tile_seg;
+        B.chunk_seg = chunk_seg;
+        B.seg_rows = rows;
+        B.status[0] = status[0];
+        B.status[1] = status[1];
+        B.tmp_keys = tmp_k;
+        B.tmp_vals = tmp_v;
+        B.max_segs = I.max_ovf;
+        B.max_tiles = I.max_tiles;
+        B.max_chunks = I.max_chunks;
+        B.max_passes = I.ovf_passes;
+        B.max_bins = 256;
+        const void* src_k = I.level2 ? static_cast<const void*>(keys_out) : static_cast<const void*>(tmp_k);
+        const uint32_t* src_v = VALS ? (I.level2 ? vals_out : tmp_v) : nullptr;
+        // the tile counters of these passes follow the two used above
+        B.ws_hdr = hdr;
+        st = enqueue_large_passes_at(sizeof(KeyT), VALS, src_k, src_v, keys_out, vals_out, B, I.ovf_passes,
+                                     I.ovf_bits, 2, stream);
+        if (st != RS_OK) return st;
+    }
+    return RS_OK;
+}
+
+static rs_status bucket_impl(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                             uint32_t* vals_out, size_t n, uint64_t min_key, uint64_t max_key, size_t nb, void* ws,
+                             size_t ws_bytes, cudaStream_t stream) {
+    if ((vals_in == nullptr) != (vals_out == nullptr)) return RS_ERR_INVALID_ARG;
+    if (n > RS_MAX_KEYS) return RS_ERR_INVALID_ARG;
+    if (n == 0) return RS_OK;
+    if (!keys_in || !keys_out) return RS_ERR_INVALID_ARG;
+    if (nb == 0) nb = std::max<size_t>(1, n / 16);
+    if (nb > ((size_t)1 << 32)) return RS_ERR_INVALID_ARG;
+    const bool vals = vals_in != nullptr;
+    const size_t kb = n * key_bytes, vb = n * 4;
+    if (keys_in != keys_out && ranges_overlap(keys_in, kb, keys_out, kb)) return RS_ERR_INVALID_ARG;
+    if (vals && vals_in != vals_out && ranges_overlap(vals_in, vb, vals_out, vb)) return RS_ERR_INVALID_ARG;
+    if (((uintptr_t)keys_in | (uintptr_t)keys_out) % key_bytes) return RS_ERR_INVALID_ARG;
+    if (vals && (((uintptr_t)vals_in | (uintptr_t)vals_out) % 4)) return RS_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws % 256)) return RS_ERR_WORKSPACE;
+    if (key_bytes == 4)
+        return vals ? bucket_sort_t<uint32_t, true>(static_cast<const uint32_t*>(keys_in),
+                                                    static_cast<uint32_t*>(keys_out), vals_in, vals_out, n, min_key,
+                                                    max_key, nb, ws, ws_bytes, stream)
+                    : bucket_sort_t<uint32_t, false>(static_cast<const uint32_t*>(keys_in),
+                                                     static_cast<uint32_t*>(keys_out), vals_in, vals_out, n, min_key,
+                                                     max_key, nb, ws, ws_bytes, stream);
+    return vals ? bucket_sort_t<uint64_t, true>(static_cast<const uint64_t*>(keys_in), static_cast<uint64_t*>(keys_out),
+                                                vals_in, vals_out, n, min_key, max_key, nb, ws, ws_bytes, stream)
+                : bucket_sort_t<uint64_t, false>(static_cast<const uint64_t*>(keys_in),
+                                                 static_cast<uint64_t*>(keys_out), vals_in, vals_out, n, min_key,
+                                                 max_key, nb, ws, ws_bytes, stream);
+}
+
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+rs_status bs_sort_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                      size_t n, uint32_t min_key, uint32_t max_key, size_t num_buckets, void* ws, size_t ws_bytes,
+                      rs_stream_t stream) {
+    return bucket_impl(4, keys_in, keys_out, vals_in, vals_out, n, min_key, max_key, num_buckets, ws, ws_bytes,
+                       stream);
+}
+
+rs_status bs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                      size_t n, uint64_t min_key, uint64_t max_key, size_t num_buckets, void* ws, size_t ws_bytes,
+                      rs_stream_t stream) {
+    return bucket_impl(8, keys_in, keys_out, vals_in, vals_out, n, min_key, max_key, num_buckets, ws, ws_bytes,
+                       stream);
+}
+
+}  // extern "C"

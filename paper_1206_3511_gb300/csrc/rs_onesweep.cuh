@@ -32,15 +32,32 @@ struct RadixDigit {
 
 // ---------------------------------------------------------------------------
 // Digit counts of every pass in one read.
+
+// Digit q of a key for the counting kernels: (x >> (shift0 + q*D)) & mask,
+// and the key-range check (every key must be below 2^key_bits).
+struct RadixDigits {
+    int shift0;
+    int digit_bits;
+    uint32_t mask;
+    int key_bits;
+    __device__ __forceinline__ void init() {}
+    template <typename KeyT>
+    __device__ __forceinline__ uint32_t operator()(KeyT x, int q) const {
+        return (uint32_t)(x >> (shift0 + q * digit_bits)) & mask;
+    }
+    template <typename KeyT>
+    __device__ __forceinline__ bool in_range(KeyT k) const {
+        return key_bits >= (int)(8 * sizeof(KeyT)) || (k >> key_bits) == 0;
+    }
+};
+
 struct CountParams {
     const void* keys;
     size_t n;
-    int shift0;      // digit p is (key >> (shift0 + p*D)) & (2^D - 1)
-    int digit_bits;  // D
-    int passes;      // P
-    int key_bits;    // keys must be < 2^key_bits; >= key width disables the check
-    uint32_t* counts;  // [P][2^D], zero on entry
-    uint32_t* scan;    // [P][2^D] exclusive prefixes (nullable)
+    int passes;        // P
+    uint32_t bins;     // 2^D
+    uint32_t* counts;  // [P][bins], zero on entry
+    uint32_t* scan;    // [P][bins] exclusive prefixes (nullable)
     uint32_t* zero_ptr;  // words zeroed by the kernel (first pass's status words)
     size_t zero_words;
     WsHeader* hdr;
@@ -49,22 +66,22 @@ struct CountParams {
 constexpr int kCountBlock = 512;
 constexpr int kCountVecIters = 8;  // 16-byte loads per thread per chunk
 
-template <typename KeyT>
-__device__ __forceinline__ void count_key(uint32_t* s_cnt, KeyT k, int shift0, int D, int P, uint32_t bins,
-                                          KeyT& seen) {
-    seen |= k;
-    const uint32_t mask = bins - 1u;
-    for (int q = 0; q < P; ++q) atomicAdd(&s_cnt[q * bins + ((uint32_t)(k >> (shift0 + q * D)) & mask)], 1u);
+template <typename KeyT, typename Digits>
+__device__ __forceinline__ void count_key(uint32_t* s_cnt, KeyT k, const Digits& dg, int P, uint32_t bins,
+                                          bool& bad) {
+    bad |= !dg.in_range(k);
+    for (int q = 0; q < P; ++q) atomicAdd(&s_cnt[q * bins + dg(k, q)], 1u);
 }
 
-template <typename KeyT>
-__global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p) {
+template <typename KeyT, typename Digits>
+__global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Digits dg) {
     extern __shared__ uint32_t s_cnt[];  // [P][bins], then kCountBlock/32+1 scan words
     __shared__ uint32_t s_last;
-    const uint32_t bins = 1u << p.digit_bits;
+    const uint32_t bins = p.bins;
     const int ncnt = p.passes * (int)bins;
     uint32_t* s_scan = s_cnt + ncnt;
     const int tid = threadIdx.x;
+    dg.init();
     for (int i = tid; i < ncnt; i += kCountBlock) s_cnt[i] = 0;
     for (size_t i = (size_t)blockIdx.x * kCountBlock + tid; i < p.zero_words; i += (size_t)gridDim.x * kCountBlock)
         p.zero_ptr[i] = 0;
@@ -79,13 +96,11 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p) {
     if (head > p.n) head = p.n;
     const size_t nvec = (p.n - head) / kPerVec;
     const size_t tail0 = head + nvec * kPerVec;
-    KeyT seen = 0;
+    bool bad = false;
     const size_t gthreads = (size_t)gridDim.x * kCountBlock;
     const size_t gtid = (size_t)blockIdx.x * kCountBlock + tid;
-    for (size_t i = gtid; i < head; i += gthreads)
-        count_key<KeyT>(s_cnt, keys[i], p.shift0, p.digit_bits, p.passes, bins, seen);
-    for (size_t i = tail0 + gtid; i < p.n; i += gthreads)
-        count_key<KeyT>(s_cnt, keys[i], p.shift0, p.digit_bits, p.passes, bins, seen);
+    for (size_t i = gtid; i < head; i += gthreads) count_key<KeyT>(s_cnt, keys[i], dg, p.passes, bins, bad);
+    for (size_t i = tail0 + gtid; i < p.n; i += gthreads) count_key<KeyT>(s_cnt, keys[i], dg, p.passes, bins, bad);
     const uint4* vec = reinterpret_cast<const uint4*>(keys + head);
     constexpr size_t kChunk = (size_t)kCountBlock * kCountVecIters;
     for (size_t base = (size_t)blockIdx.x * kChunk; base < nvec; base += (size_t)gridDim.x * kChunk) {
@@ -101,13 +116,11 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p) {
             if (idx < nvec) {
                 const KeyT* kk = reinterpret_cast<const KeyT*>(&v[j]);
 #pragma unroll
-                for (int e = 0; e < kPerVec; ++e)
-                    count_key<KeyT>(s_cnt, kk[e], p.shift0, p.digit_bits, p.passes, bins, seen);
+                for (int e = 0; e < kPerVec; ++e) count_key<KeyT>(s_cnt, kk[e], dg, p.passes, bins, bad);
             }
         }
     }
-    if (p.key_bits < (int)(8 * sizeof(KeyT)) && (seen >> p.key_bits) != 0)
-        set_device_error(p.hdr, RS_ERR_KEY_RANGE, blockIdx.x);
+    if (bad) set_device_error(p.hdr, RS_ERR_KEY_RANGE, blockIdx.x);
     __syncthreads();
     for (int i = tid; i < ncnt; i += kCountBlock)
         if (s_cnt[i]) atomicAdd(&p.counts[i], s_cnt[i]);

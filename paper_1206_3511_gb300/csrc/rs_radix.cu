@@ -52,20 +52,7 @@ constexpr int kDefaultDigitBits = 8;
 // digit widths offered to an autotuner for every kernel shape
 constexpr int kTuneDigitBits[] = {8, 4, 5, 6, 7, 9, 10, 11};
 
-template <typename KeyT>
-cudaError_t launch_counts(const CountParams& p, size_t grid, cudaStream_t s) {
-    auto kern = k_digit_counts<KeyT>;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)max_count_smem_bytes());
-    });
-    if (attr_err != cudaSuccess) return attr_err;
-    KernelScope scope("digit_counts", s);
-    kern<<<(unsigned)grid, kCountBlock, count_smem_bytes(p.passes, p.digit_bits), s>>>(p);
-    return cudaGetLastError();
-}
+}  // namespace
 
 size_t count_grid(size_t n) {
     const size_t chunk = (size_t)kCountBlock * kCountVecIters * 4;
@@ -74,8 +61,6 @@ size_t count_grid(size_t n) {
     if (g > cap) g = cap;
     return g ? g : 1;
 }
-
-}  // namespace
 
 const Variant* find_variant(int key_bytes, bool vals, int block, int items) {
     for (const Variant& v : kVariants)
@@ -161,18 +146,17 @@ rs_status enqueue_digit_counts(int key_bytes, const void* keys, size_t n, int sh
     CountParams cp{};
     cp.keys = keys;
     cp.n = n;
-    cp.shift0 = shift0;
-    cp.digit_bits = digit_bits;
     cp.passes = passes;
-    cp.key_bits = key_bits;
+    cp.bins = 1u << digit_bits;
     cp.counts = counts;
     cp.scan = scan;
     cp.zero_ptr = zero_ptr;
     cp.zero_words = zero_words;
     cp.hdr = hdr;
+    const RadixDigits dg{shift0, digit_bits, (1u << digit_bits) - 1u, key_bits};
     const size_t grid = count_grid(n);
-    cudaError_t e = key_bytes == 4 ? launch_counts<uint32_t>(cp, grid, stream)
-                                   : launch_counts<uint64_t>(cp, grid, stream);
+    cudaError_t e = key_bytes == 4 ? launch_counts<uint32_t>(cp, dg, grid, stream)
+                                   : launch_counts<uint64_t>(cp, dg, grid, stream);
     return e == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
 

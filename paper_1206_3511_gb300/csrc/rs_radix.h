@@ -2,6 +2,8 @@
 // the bucket-sort, segmented-sort and API translation units.
 #pragma once
 
+#include <mutex>
+
 #include "rs_onesweep.cuh"
 
 namespace rs {
@@ -40,6 +42,25 @@ const Variant* default_variant(int key_bytes, bool vals);
 rs_status radix_sort_impl(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
                           uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
                           cudaStream_t stream, const rs_config* cfg);
+
+// Grid of the digit-count kernel for n keys.
+size_t count_grid(size_t n);
+
+// Launch the digit-count kernel with a digit functor.
+template <typename KeyT, typename Digits>
+cudaError_t launch_counts(const CountParams& p, const Digits& dg, size_t grid, cudaStream_t s) {
+    auto kern = k_digit_counts<KeyT, Digits>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)max_count_smem_bytes());
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    KernelScope scope("digit_counts", s);
+    kern<<<(unsigned)grid, kCountBlock, (p.passes * p.bins + kCountBlock / 32 + 1) * 4, s>>>(p, dg);
+    return cudaGetLastError();
+}
 
 rs_status enqueue_digit_counts(int key_bytes, const void* keys, size_t n, int shift0, int digit_bits, int passes,
                                int key_bits, uint32_t* counts, uint32_t* scan, uint32_t* zero_ptr,

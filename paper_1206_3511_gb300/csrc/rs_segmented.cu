@@ -15,42 +15,6 @@ namespace {
 
 constexpr int kSegDigitBits = 8;
 
-template <typename KeyT, bool VALS>
-struct SegShape;
-template <>
-struct SegShape<uint32_t, false> {
-    static constexpr int kBlock = 256, kItems = 18, kMinB = 4;
-};
-template <>
-struct SegShape<uint32_t, true> {
-    static constexpr int kBlock = 256, kItems = 12, kMinB = 4;
-};
-template <>
-struct SegShape<uint64_t, false> {
-    static constexpr int kBlock = 256, kItems = 12, kMinB = 4;
-};
-template <>
-struct SegShape<uint64_t, true> {
-    static constexpr int kBlock = 256, kItems = 10, kMinB = 3;
-};
-
-template <typename KeyT, bool VALS, typename DigitOp>
-cudaError_t launch_seg_pass(const SegPassParams<DigitOp>& sp, size_t grid, cudaStream_t s) {
-    using S = SegShape<KeyT, VALS>;
-    using Shape = OnesweepShape<KeyT, VALS, S::kBlock, S::kItems>;
-    auto kern = k_onesweep_seg<KeyT, VALS, S::kBlock, S::kItems, S::kMinB, DigitOp>;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)Shape::smem_bytes(kMaxDigitBits));
-    });
-    if (attr_err != cudaSuccess) return attr_err;
-    KernelScope scope("onesweep_seg_pass", s);
-    kern<<<(unsigned)grid, S::kBlock, Shape::smem_bytes(sp.base.digit_bits), s>>>(sp);
-    return cudaGetLastError();
-}
-
 template <typename KeyT, bool VALS, typename BucketFn>
 cudaError_t launch_local(const LocalParams& lp, BucketFn bfn, size_t grid, cudaStream_t s) {
     using LS = LocalSmem<KeyT, VALS, kLocalBlock>;
@@ -67,29 +31,11 @@ cudaError_t launch_local(const LocalParams& lp, BucketFn bfn, size_t grid, cudaS
     return cudaGetLastError();
 }
 
-template <typename KeyT>
-cudaError_t launch_seg_counts(const KeyT* keys, const SegBuffers& B, RadixDigits dg, int passes, uint32_t bins,
-                              uint32_t* zero_ptr, size_t zero_words, cudaStream_t s) {
-    auto kern = k_seg_counts<KeyT, RadixDigits>;
-    const size_t smem = (size_t)passes * bins * 4;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)max_count_smem_bytes());
-    });
-    if (attr_err != cudaSuccess) return attr_err;
-    KernelScope scope("seg_counts", s);
-    kern<<<(unsigned)B.max_chunks, 512, smem, s>>>(keys, B.large, B.hdr, B.chunk_seg, dg, passes, bins, B.seg_rows,
-                                                    zero_ptr, zero_words);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 uint32_t seg_tile_keys(int key_bytes, bool vals) {
-    if (key_bytes == 4) return vals ? 256 * 12 : 256 * 18;
-    return vals ? 256 * 10 : 256 * 12;
+    if (key_bytes == 4) return vals ? SegShape<uint32_t, true>::kTile : SegShape<uint32_t, false>::kTile;
+    return vals ? SegShape<uint64_t, true>::kTile : SegShape<uint64_t, false>::kTile;
 }
 
 SegLayout seg_layout(int key_bytes, bool vals, size_t n_total, size_t max_segs, int max_passes, int max_bins,
@@ -141,7 +87,7 @@ SegBuffers carve_seg_buffers(void* ws, const SegLayout& L) {
 
 template <typename KeyT, bool VALS>
 static rs_status large_passes_t(const void* src_k, const uint32_t* src_v, void* out_k, uint32_t* out_v,
-                                const SegBuffers& B, int passes, int D, cudaStream_t stream) {
+                                const SegBuffers& B, int passes, int D, int first_ctr, cudaStream_t stream) {
     const uint32_t bins = 1u << D;
     const uint32_t tk = seg_tile_keys(sizeof(KeyT), VALS);
     {
@@ -150,9 +96,9 @@ static rs_status large_passes_t(const void* src_k, const uint32_t* src_v, void* 
         if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
     }
     RS_CUDA_TRY(cudaMemsetAsync(B.seg_rows, 0, B.max_segs * (size_t)passes * bins * 4, stream));
-    RadixDigits dg{0, D, bins - 1u};
-    if (launch_seg_counts<KeyT>(static_cast<const KeyT*>(src_k), B, dg, passes, bins, B.status[0],
-                                B.max_tiles * (size_t)bins, stream) != cudaSuccess)
+    RadixDigits dg{0, D, bins - 1u, 64};
+    if (launch_seg_counts<KeyT>(static_cast<const KeyT*>(src_k), B.large, B.hdr, B.chunk_seg, B.max_chunks, dg, passes,
+                                bins, B.seg_rows, B.status[0], B.max_tiles * (size_t)bins, stream) != cudaSuccess)
         return RS_ERR_CUDA;
     {
         KernelScope scope("seg_scan", stream);
@@ -183,7 +129,7 @@ static rs_status large_passes_t(const void* src_k, const uint32_t* src_v, void* 
         sp.base.op = RadixDigit{p * D, bins - 1u};
         sp.base.status = B.status[p & 1];
         sp.base.status_next = (p + 1 < passes) ? B.status[(p + 1) & 1] : nullptr;
-        sp.base.tile_ctr = &B.ws_hdr->tile_ctr[p % kMaxPasses];
+        sp.base.tile_ctr = &B.ws_hdr->tile_ctr[(first_ctr + p) % kMaxPasses];
         sp.pass = p;
         if (launch_seg_pass<KeyT, VALS, RadixDigit>(sp, B.max_tiles, stream) != cudaSuccess) return RS_ERR_CUDA;
         cur_k = dst_k;
@@ -192,16 +138,25 @@ static rs_status large_passes_t(const void* src_k, const uint32_t* src_v, void* 
     return RS_OK;
 }
 
+rs_status enqueue_large_passes_at(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,
+                                  uint32_t* out_v, const SegBuffers& B, int passes, int digit_bits, int first_ctr,
+                                  cudaStream_t stream) {
+    if (passes < 1 || passes + first_ctr > kMaxPasses || passes > B.max_passes || (1 << digit_bits) > B.max_bins)
+        return RS_ERR_INVALID_ARG;
+    if (key_bytes == 4)
+        return vals ? large_passes_t<uint32_t, true>(src_k, src_v, out_k, out_v, B, passes, digit_bits, first_ctr,
+                                                     stream)
+                    : large_passes_t<uint32_t, false>(src_k, src_v, out_k, out_v, B, passes, digit_bits, first_ctr,
+                                                      stream);
+    return vals ? large_passes_t<uint64_t, true>(src_k, src_v, out_k, out_v, B, passes, digit_bits, first_ctr, stream)
+                : large_passes_t<uint64_t, false>(src_k, src_v, out_k, out_v, B, passes, digit_bits, first_ctr,
+                                                  stream);
+}
+
 rs_status enqueue_large_passes(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,
                                uint32_t* out_v, const SegBuffers& B, int passes, int digit_bits,
                                cudaStream_t stream) {
-    if (passes < 1 || passes > kMaxPasses || passes > B.max_passes || (1 << digit_bits) > B.max_bins)
-        return RS_ERR_INVALID_ARG;
-    if (key_bytes == 4)
-        return vals ? large_passes_t<uint32_t, true>(src_k, src_v, out_k, out_v, B, passes, digit_bits, stream)
-                    : large_passes_t<uint32_t, false>(src_k, src_v, out_k, out_v, B, passes, digit_bits, stream);
-    return vals ? large_passes_t<uint64_t, true>(src_k, src_v, out_k, out_v, B, passes, digit_bits, stream)
-                : large_passes_t<uint64_t, false>(src_k, src_v, out_k, out_v, B, passes, digit_bits, stream);
+    return enqueue_large_passes_at(key_bytes, vals, src_k, src_v, out_k, out_v, B, passes, digit_bits, 0, stream);
 }
 
 rs_status enqueue_local_sorts(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,

@@ -49,7 +49,7 @@ __device__ __forceinline__ void append_large(SegDesc* list, uint32_t* count, uin
 // Segments from an offset table: empty ones are dropped, those of at most
 // `small_cap` keys go to the shared-memory list, the others to the scatter
 // list.  One thread per segment.
-__global__ void k_plan_from_offsets(const uint64_t* __restrict__ offsets, size_t nseg, uint32_t small_cap,
+static __global__ void k_plan_from_offsets(const uint64_t* __restrict__ offsets, size_t nseg, uint32_t small_cap,
                                     uint32_t tile_keys, int bits, SegDesc* large, SegDesc* small, SegPlanHdr* hdr,
                                     WsHeader* ws_hdr) {
     const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,7 +72,7 @@ __global__ void k_plan_from_offsets(const uint64_t* __restrict__ offsets, size_t
 }
 
 // tile -> segment and chunk -> segment maps; one block per large segment.
-__global__ void k_plan_maps(const SegDesc* __restrict__ large, const SegPlanHdr* __restrict__ hdr,
+static __global__ void k_plan_maps(const SegDesc* __restrict__ large, const SegPlanHdr* __restrict__ hdr,
                             uint32_t tile_keys, uint32_t* tile_seg, uint32_t* chunk_seg) {
     const uint32_t li = blockIdx.x;
     if (li >= hdr->num_large) return;
@@ -81,19 +81,6 @@ __global__ void k_plan_maps(const SegDesc* __restrict__ large, const SegPlanHdr*
     for (uint32_t i = threadIdx.x; i < nt; i += blockDim.x) tile_seg[d.tile0 + i] = li;
     for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) chunk_seg[d.chunk0 + i] = li;
 }
-
-// Digit q of a segment-relative key for the counting kernel: (x >> (shift0 +
-// q*D)) & (2^D - 1).
-struct RadixDigits {
-    int shift0;
-    int digit_bits;
-    uint32_t mask;
-    __device__ __forceinline__ void init() {}
-    template <typename KeyT>
-    __device__ __forceinline__ uint32_t operator()(KeyT x, int q) const {
-        return (uint32_t)(x >> (shift0 + q * digit_bits)) & mask;
-    }
-};
 
 // Per-segment digit counts of `passes` digits: seg_counts[li][q][d].  One
 // block per counting chunk of a large segment.  Also zeroes zero_words words
@@ -134,7 +121,7 @@ __global__ void __launch_bounds__(512) k_seg_counts(const KeyT* __restrict__ key
 
 // Exclusive prefix of every (segment, pass) row of bins counts, in place.
 // One block of 256 threads per row.
-__global__ void __launch_bounds__(256) k_seg_scan(uint32_t* rows, const SegPlanHdr* __restrict__ hdr, int passes,
+static __global__ void __launch_bounds__(256) k_seg_scan(uint32_t* rows, const SegPlanHdr* __restrict__ hdr, int passes,
                                                   uint32_t bins, int use_next) {
     extern __shared__ uint32_t s_row[];  // [bins] + scan scratch
     const uint32_t nrows = (use_next ? hdr->num_next : hdr->num_large) * (uint32_t)passes;

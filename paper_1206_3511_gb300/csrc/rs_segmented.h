@@ -13,6 +13,61 @@ constexpr int kLocalBlock = 256;
 constexpr int kLocalItems = 16;
 constexpr uint32_t kLocalCap = kLocalBlock * kLocalItems;
 
+// Kernel shapes of the segmented and bucket scatter passes.
+template <typename KeyT, bool VALS>
+struct SegShape;
+template <>
+struct SegShape<uint32_t, false> {
+    static constexpr int kBlock = 256, kItems = 18, kMinB = 4, kTile = kBlock * kItems;
+};
+template <>
+struct SegShape<uint32_t, true> {
+    static constexpr int kBlock = 256, kItems = 12, kMinB = 4, kTile = kBlock * kItems;
+};
+template <>
+struct SegShape<uint64_t, false> {
+    static constexpr int kBlock = 256, kItems = 12, kMinB = 4, kTile = kBlock * kItems;
+};
+template <>
+struct SegShape<uint64_t, true> {
+    static constexpr int kBlock = 256, kItems = 10, kMinB = 3, kTile = kBlock * kItems;
+};
+
+template <typename KeyT, bool VALS, typename DigitOp>
+cudaError_t launch_seg_pass(const SegPassParams<DigitOp>& sp, size_t grid, cudaStream_t s) {
+    using S = SegShape<KeyT, VALS>;
+    using Shape = OnesweepShape<KeyT, VALS, S::kBlock, S::kItems>;
+    auto kern = k_onesweep_seg<KeyT, VALS, S::kBlock, S::kItems, S::kMinB, DigitOp>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)Shape::smem_bytes(kMaxDigitBits));
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    KernelScope scope("onesweep_seg_pass", s);
+    kern<<<(unsigned)grid, S::kBlock, Shape::smem_bytes(sp.base.digit_bits), s>>>(sp);
+    return cudaGetLastError();
+}
+
+template <typename KeyT, typename Digits>
+cudaError_t launch_seg_counts(const KeyT* keys, const SegDesc* segs, const SegPlanHdr* hdr, const uint32_t* chunk_seg,
+                              size_t max_chunks, const Digits& dg, int passes, uint32_t bins, uint32_t* rows,
+                              uint32_t* zero_ptr, size_t zero_words, cudaStream_t s) {
+    auto kern = k_seg_counts<KeyT, Digits>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)max_count_smem_bytes());
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    KernelScope scope("seg_counts", s);
+    kern<<<(unsigned)max_chunks, 512, (size_t)passes * bins * 4, s>>>(keys, segs, hdr, chunk_seg, dg, passes, bins,
+                                                                     rows, zero_ptr, zero_words);
+    return cudaGetLastError();
+}
+
 // Device buffers of one segmented sort (all carved from the workspace).
 struct SegBuffers {
     WsHeader* ws_hdr;
@@ -51,6 +106,14 @@ uint32_t seg_tile_keys(int key_bytes, bool vals);
 rs_status enqueue_large_passes(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,
                                uint32_t* out_v, const SegBuffers& B, int passes, int digit_bits,
                                cudaStream_t stream);
+
+// Same, with the passes' tile counters starting at header slot first_ctr.
+rs_status enqueue_large_passes_at(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,
+                                  uint32_t* out_v, const SegBuffers& B, int passes, int digit_bits, int first_ctr,
+                                  cudaStream_t stream);
+
+// Bytes of a bucket-sort workspace.
+size_t bucket_workspace_bytes(int key_bytes, bool vals, size_t n, size_t nb);
 
 // Shared-memory sorts of a device list of segments (count on the device).
 // bucket: device BucketParams for bucket mode, or null.

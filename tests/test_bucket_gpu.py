@@ -1,0 +1,141 @@
+"""GPU parity of the bucket sort (Algorithm 2) against the CPU oracle's
+bucket sort, element by element, zero tolerance.  The oracle's bucket sort is
+pinned equal to its radix sort and to stable library sorts, so the GPU bucket
+sort is also compared with the oracle radix sort at sizes where the oracle's
+insertion sorts would take too long."""
+import numpy as np
+import pytest
+
+import synth
+from tests._util import assert_same, from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _bucket(rs, keys, vals=None, lo=None, hi=None, nb=0, in_place=False):
+    import torch
+
+    kd = to_dev(keys)
+    vd = to_dev(vals) if vals is not None else None
+    if in_place:
+        ok, ov = rs.bucket_sort(kd, vd, lo, hi, nb, out=kd, out_values=vd)
+    else:
+        ok, ov = rs.bucket_sort(kd, vd, lo, hi, nb)
+    torch.cuda.synchronize()
+    return from_dev(ok, keys.dtype), (from_dev(ov, np.uint32) if vals is not None else None)
+
+
+def _check(rs, oracle, keys, vals=None, lo=None, hi=None, nb=0, in_place=False, what="", use_bucket_oracle=True):
+    gk, gv = _bucket(rs, keys, vals, lo, hi, nb, in_place)
+    if use_bucket_oracle:
+        want = oracle.bucket_sort(keys, vals, lo, hi, nb or max(1, keys.size // 16))
+    else:
+        want = oracle.radix_sort(keys, vals)
+    if vals is None:
+        assert_same(gk, want, what)
+    else:
+        assert_same(gk, want[0], what + " keys")
+        assert_same(gv, want[1], what + " values")
+
+
+def test_small_config_1m_uniform_31bit(rs, oracle):
+    """1,000,000 u32 keys uniform in [0, 2^31), seed 0, 62,500 buckets over
+    [0, 2^31 - 1]."""
+    keys = synth.u32(1_000_000, 0, 0) >> np.uint32(1)
+    _check(rs, oracle, keys, None, 0, 2**31 - 1, 62_500, what="1M uniform")
+
+
+@pytest.mark.parametrize("dist", list(synth.DISTS))
+def test_distributions_declared_bounds(rs, oracle, dist):
+    n = 200_003
+    keys = synth.keys_u32(n, dist, seed=3)
+    lo, hi = synth.DECLARED_BOUNDS[dist]
+    _check(rs, oracle, keys, synth.index_values(n), lo, hi, 0, what=synth.DISTS[dist],
+           use_bucket_oracle=dist not in (6,))
+
+
+@pytest.mark.parametrize("dist", [0, 1, 6, 8])
+def test_distributions_computed_bounds(rs, oracle, dist):
+    n = 150_001
+    keys = synth.keys_u32(n, dist, seed=4)
+    _check(rs, oracle, keys, synth.index_values(n), None, None, 0, what="computed " + synth.DISTS[dist],
+           use_bucket_oracle=False)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 16, 17, 4095, 4096, 4097, 65_537, 1_048_577])
+def test_sizes(rs, oracle, n):
+    keys = synth.u32(n, 50, 0)
+    _check(rs, oracle, keys, synth.index_values(n), 0, 2**32 - 1, 0, what=f"n={n}", use_bucket_oracle=n < 100_000)
+
+
+@pytest.mark.parametrize("nb", [1, 2, 3, 255, 256, 257, 4096, 65_536, 300_000, 2_000_000])
+def test_bucket_counts(rs, oracle, nb):
+    """nb = 1 (one bucket), nb around the level boundaries, nb > n and nb > range."""
+    n = 300_000
+    keys = synth.u32(n, 51, 0) >> np.uint32(12)  # [0, 2^20)
+    _check(rs, oracle, keys, synth.index_values(n), 0, 2**20 - 1, nb, what=f"nb={nb}",
+           use_bucket_oracle=nb >= 4096)
+
+
+def test_min_equals_max_and_narrow_ranges(rs, oracle):
+    keys = np.full(100_000, 77, np.uint32)
+    _check(rs, oracle, keys, synth.index_values(keys.size), 77, 77, 0, what="min==max")
+    keys = synth.uniform_below(200_000, 3, 5, 52) + np.uint32(10)
+    _check(rs, oracle, keys, synth.index_values(keys.size), 10, 12, 0, what="range 3")
+    _check(rs, oracle, keys, synth.index_values(keys.size), 0, 2**32 - 1, 7, what="range 3 nb 7",
+           use_bucket_oracle=False)
+
+
+def test_skewed_keys_take_the_overflow_path(rs, oracle):
+    """Gaussian keys under the full declared range [0, 2^32): most keys fall in
+    a few buckets, which are sorted by the radix of their key range."""
+    n = 2_000_000
+    keys = synth.gaussian_u32(n, seed=9)
+    _check(rs, oracle, keys, synth.index_values(n), 0, 2**32 - 1, n // 16, what="gaussian", use_bucket_oracle=False)
+    few = np.array([5, 2**31, 2**32 - 1], np.uint32)[synth.uniform_below(n, 3, 9, 53)]
+    _check(rs, oracle, few, synth.index_values(n), 0, 2**32 - 1, 0, what="three values", use_bucket_oracle=False)
+
+
+@pytest.mark.parametrize("key_bits", [40, 64])
+def test_u64(rs, oracle, key_bits):
+    n = 300_001
+    keys = synth.keys_u64(n, key_bits, seed=key_bits)
+    vals = synth.index_values(n)
+    _check(rs, oracle, keys, vals, 0, 2**key_bits - 1, 0, what=f"u64 {key_bits}", use_bucket_oracle=False)
+    _check(rs, oracle, keys, vals, None, None, 0, what=f"u64 {key_bits} computed", use_bucket_oracle=False)
+    small = synth.keys_u64(50_000, key_bits, seed=1)
+    _check(rs, oracle, small, synth.index_values(small.size), 0, 2**key_bits - 1, 0, what="u64 vs bucket oracle")
+
+
+def test_in_place(rs, oracle):
+    n = 250_000
+    keys = synth.u32(n, 54, 0)
+    _check(rs, oracle, keys, synth.index_values(n), 0, 2**32 - 1, 0, in_place=True, what="in place",
+           use_bucket_oracle=False)
+
+
+def test_key_outside_declared_range_is_reported(rs):
+    import torch
+
+    keys = synth.u32(10_000, 55, 0) >> np.uint32(16)
+    keys[5] = 70_000
+    kd = to_dev(keys)
+    out = torch.empty_like(kd)
+    ws = rs.workspace(rs.rs_workspace_bytes(1, 4, 0, keys.size, 0, 0, 0))
+    assert rs.bs_sort_u32(kd, out, None, None, keys.size, 0, 65_535, 0, ws, ws.numel()) == 0
+    assert rs.get_status(ws) == 3  # RS_ERR_KEY_RANGE
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dist", [0, 1, 3, 5, 6])
+def test_full_size_100m(rs, oracle, dist):
+    """100M u32 keys of the benchmark distributions with their declared
+    bounds and n/16 buckets, checked in full against the oracle radix sort."""
+    import torch
+
+    n = 100_000_000
+    keys = synth.keys_u32(n, dist, seed=0)
+    lo, hi = synth.DECLARED_BOUNDS[dist]
+    gk, _ = _bucket(rs, keys, None, lo, hi, 0)
+    torch.cuda.empty_cache()
+    assert_same(gk, oracle.radix_sort(keys), f"100M {synth.DISTS[dist]}")
