@@ -44,6 +44,23 @@ WORKLOADS = {
     "radix_u64_40bit_50m": ("radix", 8, False, 50_000_000, 40, None,
                             "LSD radix sort, 50M uint64 keys uniform [0,2^40), key_bits=40, 5 passes"),
 }
+# the seven 100M-key u32 distributions, radix (key_bits 32) and bucket (declared bounds, n/16 buckets)
+for _d in range(7):
+    _name = ["uniform", "small1000", "large", "sorted", "reverse", "nearly", "gauss"][_d]
+    WORKLOADS[f"radix_u32_{_name}_100m"] = ("radix", 4, False, 100_000_000, 32, _d,
+                                           f"LSD radix sort, 100M uint32 keys, distribution {_d}, 4 passes")
+    WORKLOADS[f"bucket_u32_{_name}_100m"] = ("bucket", 4, False, 100_000_000, 32, _d,
+                                            f"bucket sort, 100M uint32 keys, distribution {_d}, declared bounds, "
+                                            f"n/16 buckets")
+WORKLOADS["bucket_u32_1m"] = ("bucket", 4, False, 1_000_000, 31, 10,
+                              "bucket sort, 1M uint32 keys uniform [0,2^31), 62,500 buckets over [0,2^31-1]")
+WORKLOADS["radix_u32_1m"] = ("radix", 4, False, 1_000_000, 32, 10,
+                             "LSD radix sort, 1M uint32 keys uniform [0,2^31), 8-bit digits, 4 passes")
+
+# kernels whose algorithmic bytes per launch are 2 n (w + v) (one read and one
+# write of every key) and n w (one read)
+SCATTER_KERNELS = ("onesweep_pass", "bucket_pass", "onesweep_seg_pass", "local_sort")
+READ_KERNELS = ("digit_counts", "seg_counts", "minmax")
 
 
 def parse_args():
@@ -147,28 +164,47 @@ def ncu_traffic(kernel: str, workload: str):
 
 
 def make_keys(wl, n, seed=0):
+    import numpy as np
+
     import synth
 
     algo, kb, has_v, _, key_bits, dist, _ = WORKLOADS[wl]
     if kb == 4:
-        keys = synth.keys_u32(n, dist, seed=seed)
+        if dist == 10:  # uniform [0, 2^31)
+            keys = synth.keys_u32(n, 0, seed=seed) >> np.uint32(1)
+        else:
+            keys = synth.keys_u32(n, dist, seed=seed)
     else:
         keys = synth.keys_u64(n, key_bits, seed=seed)
     vals = synth.index_values(n) if has_v else None
     return keys, vals
 
 
+def bucket_bounds(wl):
+    import synth
+
+    dist = WORKLOADS[wl][5]
+    if dist == 10:
+        return 0, 2**31 - 1
+    return synth.DECLARED_BOUNDS[dist]
+
+
 def cpu_oracle_rate(wl, n_sample, keys=None, vals=None) -> tuple[float, float]:
-    """Oracle radix sort of n_sample keys of the workload: (Gkeys/s, seconds)."""
+    """The oracle's sort of n_sample keys of the workload (radix, or bucket
+    for bucket workloads): (Gkeys/s, seconds)."""
     import oracle
 
     if keys is None:
         keys, vals = make_keys(wl, n_sample, seed=1)
-    key_bits = WORKLOADS[wl][4]
+    algo, _, _, _, key_bits, _, _ = WORKLOADS[wl]
     t0 = time.perf_counter()
-    oracle.radix_sort(keys, vals, key_bits, 8)
+    if algo == "bucket":
+        lo, hi = bucket_bounds(wl)
+        oracle.bucket_sort(keys, vals, lo, hi, max(1, keys.size // 16))
+    else:
+        oracle.radix_sort(keys, vals, key_bits, 8)
     dt = time.perf_counter() - t0
-    return n_sample / dt / 1e9, dt
+    return keys.size / dt / 1e9, dt
 
 
 # ------------------------------------------------------------------ reference arm
@@ -229,6 +265,8 @@ def run_ours(args):
     rs.load()
     wl = args.workload
     algo, kb, has_v, n_def, key_bits, _, desc = WORKLOADS[wl]
+    if algo == "bucket":
+        key_bits = 8 * kb
     n = args.n or n_def
     keys_np, vals_np = make_keys(wl, n, seed=rank)
     sdt = np.int32 if kb == 4 else np.int64
@@ -238,13 +276,25 @@ def run_ours(args):
     d_vals = h_vals.to(dev) if has_v else None
     d_out = torch.empty_like(d_keys)
     d_outv = torch.empty_like(d_vals) if has_v else None
-    nbytes = rs.rs_workspace_bytes(rs.RS_ALGO_RADIX, kb, has_v, n, key_bits, 0, 0)
-    ws = rs.workspace(nbytes, d_keys.device)
     stream = torch.cuda.current_stream()
-    fn = rs.rs_sort_u32 if kb == 4 else rs.rs_sort_u64
+    if algo == "bucket":
+        lo, hi = bucket_bounds(wl)
+        nb = max(1, n // 16)
+        nbytes = rs.rs_workspace_bytes(rs.RS_ALGO_BUCKET, kb, has_v, n, 0, nb, 0)
+        bfn = rs.bs_sort_u32 if kb == 4 else rs.bs_sort_u64
+
+        def call(ws):
+            return bfn(d_keys, d_out, d_vals, d_outv, n, lo, hi, nb, ws, ws.numel(), stream)
+    else:
+        nbytes = rs.rs_workspace_bytes(rs.RS_ALGO_RADIX, kb, has_v, n, key_bits, 0, 0)
+        rfn = rs.rs_sort_u32 if kb == 4 else rs.rs_sort_u64
+
+        def call(ws):
+            return rfn(d_keys, d_out, d_vals, d_outv, n, key_bits, ws, ws.numel(), stream)
+    ws = rs.workspace(nbytes, d_keys.device)
 
     def step():
-        rc = fn(d_keys, d_out, d_vals, d_outv, n, key_bits, ws, ws.numel(), stream)
+        rc = call(ws)
         if rc:
             raise rs.SortError(rc, "sort")
 
@@ -325,22 +375,38 @@ def run_ours(args):
     peak_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6800.0
     w = kb + (4 if has_v else 0)
+    # dominant kernel by time inside the timed region: its algorithmic bytes
+    # per step over its device time per step (for a kernel launched once per
+    # pass this is bytes per launch over the mean launch time)
     roofline = None
-    if "onesweep_pass" in kstats:
-        nl, tot = kstats["onesweep_pass"]
-        avg_s = tot / nl / 1e3
-        alg_bytes = 2 * n * w
-        achieved = alg_bytes / avg_s / 1e9
-        traffic = ncu_traffic("onesweep_pass", wl)
-        roofline = {"kernel": "onesweep_pass", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                    "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
-                    "peak_source": f"{peak_src} copy bandwidth", "algorithmic_bytes_per_launch": alg_bytes,
-                    "avg_launch_ms": avg_s * 1e3, "launches": nl}
-    passes = -(-key_bits // 8)
-    whole_bytes = n * kb + passes * 2 * n * w
+    if kstats:
+        top = max(kstats, key=lambda k: kstats[k][1])
+        nl, tot = kstats[top]
+        per_step_launches = nl / args.steps
+        if top == "onesweep_pass":
+            step_bytes = 2 * n * w * per_step_launches
+        elif top in SCATTER_KERNELS:
+            step_bytes = 2 * n * w  # the launches of one step move every key once
+        else:
+            step_bytes = n * kb * per_step_launches
+        step_s = tot / args.steps / 1e3
+        achieved = step_bytes / step_s / 1e9
+        traffic = ncu_traffic(top, wl)
+        roofline = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": f"{peak_src} copy bandwidth",
+                    "algorithmic_bytes_per_launch": step_bytes / per_step_launches,
+                    "avg_launch_ms": tot / nl, "launches": nl}
+    if algo == "bucket":
+        # one read to count, one read+write to scatter into buckets, one
+        # read+write to sort the buckets
+        whole_bytes = n * kb + 4 * n * w
+    else:
+        passes = -(-key_bits // 8)
+        whole_bytes = n * kb + passes * 2 * n * w
+    step_s = ms / args.steps / 1e3
     whole = {"algorithmic_bytes_per_step": whole_bytes,
-             "achieved_gbs": whole_bytes / (ms / args.steps / 1e3) / 1e9,
-             "frac_of_peak": whole_bytes / (ms / args.steps / 1e3) / 1e9 / hbm_peak,
+             "achieved_gbs": whole_bytes / step_s / 1e9,
+             "frac_of_peak": whole_bytes / step_s / 1e9 / hbm_peak,
              "kernels": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kstats.items()}}
 
     cpu = None

@@ -5,6 +5,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "rs_segmented.h"
@@ -66,6 +67,23 @@ KernelScope::~KernelScope() {
     if (slot_ < 0) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if ((size_t)slot_ < g_records.size()) cudaEventRecord(g_records[slot_].stop, stream_);
+}
+
+int resident_grid_cached(const void* kern, int block, size_t smem, int (*query)(const void*, int, size_t)) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(kern, block, smem, dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    const int grid = query(kern, block, smem) * device_sm_count();
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = grid;
+    return grid;
 }
 
 int device_sm_count() {

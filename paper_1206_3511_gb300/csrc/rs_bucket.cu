@@ -96,6 +96,8 @@ struct BucketCountDigits {
 
 // ceil(b * range / nb): how many key values lie below bucket b (exact).
 __device__ __forceinline__ uint64_t keys_below_bucket(const BucketParams& bp, uint64_t b) {
+    if (bp.range != 0 && bp.range <= 0xffffffffull + 1 && b <= 0xffffffffull)  // b * range < 2^64
+        return (b * bp.range + bp.nb - 1) / bp.nb;
     const unsigned __int128 r = bp.range ? (unsigned __int128)bp.range : ((unsigned __int128)1 << 64);
     const unsigned __int128 x = (unsigned __int128)b * r;
     return (uint64_t)((x + bp.nb - 1) / bp.nb);
@@ -128,67 +130,146 @@ struct PlanLevel {
     uint32_t* num_copy;
 };
 
-// One thread per (parent, digit): describe the child partition and hand it to
-// the right list.
-__global__ void k_bucket_plan(PlanLevel pl) {
-    const uint32_t bins = 1u << pl.digit_bits;
-    const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t parent = (uint32_t)(gid / bins), d = (uint32_t)(gid % bins);
-    const uint32_t nparents = pl.parents ? *pl.num_parents : 1u;
-    if (parent >= nparents) return;
-    const BucketParams bp = load_bucket_params(pl.bp);
-    uint64_t pstart = 0, pn = pl.n_total, pb_lo = 0;
-    if (pl.parents) {
-        const SegDesc ps = pl.parents[parent];
-        pstart = ps.start;
-        pn = ps.n;
-        pb_lo = ps.aux;
+// A run of consecutive sibling partitions being grouped into one leaf.
+struct LeafRun {
+    uint64_t start, n, b_lo, span, key_lo, width;
+};
+
+// Per-parent staging of the planner's output in shared memory, written to the
+// global lists with one atomic reservation per list.
+struct PlanStage {
+    SegDesc leaf[256];
+    SegDesc copy[256];
+    SegDesc big[256];  // to the next level or to the overflow radix
+    uint32_t n_leaf, n_copy, n_big, big_tiles, big_chunks;
+};
+
+__device__ __forceinline__ void stage_run(const PlanLevel& pl, PlanStage& st, LeafRun& r) {
+    if (r.n == 0) {
+        r.span = 0;
+        return;
     }
-    const uint32_t* row = pl.starts + (size_t)parent * bins;
-    const uint64_t off = row[d];
-    const uint64_t end = pl.counts ? off + pl.counts[d] : ((d + 1 < bins) ? row[d + 1] : pn);
-    if (end <= off) return;
-    const uint64_t n = end - off;
-    const uint64_t b_lo = pb_lo + ((uint64_t)d << pl.shift);
-    if (b_lo >= bp.nb) return;  // cannot hold keys
-    uint64_t span = (uint64_t)1 << pl.shift;
-    if (span > bp.nb - b_lo) span = bp.nb - b_lo;
-    const uint64_t below = keys_below_bucket(bp, b_lo);
-    const uint64_t width = keys_below_bucket(bp, b_lo + span) - below;  // key values the span can hold
     SegDesc c{};
-    c.start = pstart + off;
-    c.n = (uint32_t)n;
-    c.key_lo = bp.min + below;
-    c.bits = width <= 1 ? 0u : min(bit_length(width - 1), (uint32_t)pl.key_width);
-    c.aux = b_lo;
-    if (c.bits == 0) {  // one possible key: already in order
-        if (!pl.in_out) pl.copy[atomicAdd(pl.num_copy, 1u)] = c;
-        return;
+    c.start = r.start;
+    c.n = (uint32_t)r.n;
+    c.key_lo = r.key_lo;
+    c.aux = r.b_lo;
+    c.bits = r.width <= 1 ? 0u : min(bit_length(r.width - 1), (uint32_t)pl.key_width);
+    c.chunk0 = r.span > 0xffffffffull ? 0xffffffffu : (uint32_t)r.span;
+    if (c.bits == 0) {  // one possible key: already in order, only moved if needed
+        if (!pl.in_out) st.copy[st.n_copy++] = c;
+    } else {
+        st.leaf[st.n_leaf++] = c;
     }
-    if (n <= pl.cap) {
-        c.chunk0 = span > 0xffffffffull ? 0xffffffffu : (uint32_t)span;
-        pl.leaf[atomicAdd(pl.num_leaf, 1u)] = c;
-        return;
+    r.n = 0;
+    r.span = 0;
+}
+
+// One block per parent.  Its threads describe the children (digit values)
+// in parallel; then one thread walks them in order.  A child above the
+// shared-memory capacity goes to the next level (while bucket bits remain) or
+// to the overflow radix; the others are grouped, in order, into runs of at
+// most `cap` keys and 256 buckets, each sorted by one block: a run's buckets
+// are contiguous and ordered, so sorting the run by bucket and then each
+// bucket is sorting each child.
+__global__ void __launch_bounds__(256) k_bucket_plan(PlanLevel pl) {
+    __shared__ uint64_t s_off[256], s_n[256], s_below[257];
+    __shared__ PlanStage st;
+    __shared__ uint32_t s_base[5];
+    const uint32_t bins = 1u << pl.digit_bits;
+    const uint32_t nparents = pl.parents ? *pl.num_parents : 1u;
+    const BucketParams bp = load_bucket_params(pl.bp);
+    const bool to_next = pl.next && pl.shift > 0;
+    for (uint32_t parent = blockIdx.x; parent < nparents; parent += gridDim.x) {
+        uint64_t pstart = 0, pn = pl.n_total, pb_lo = 0;
+        if (pl.parents) {
+            const SegDesc ps = pl.parents[parent];
+            pstart = ps.start;
+            pn = ps.n;
+            pb_lo = ps.aux;
+        }
+        const uint32_t* row = pl.starts + (size_t)parent * bins;
+        __syncthreads();
+        for (uint32_t d = threadIdx.x; d <= bins; d += blockDim.x) {
+            uint64_t b = pb_lo + ((uint64_t)d << pl.shift);
+            if (b > bp.nb) b = bp.nb;
+            s_below[d] = keys_below_bucket(bp, b);
+            if (d < bins) {
+                const uint64_t off = row[d];
+                const uint64_t end = pl.counts ? off + pl.counts[d] : ((d + 1 < bins) ? row[d + 1] : pn);
+                s_off[d] = off;
+                s_n[d] = end > off ? end - off : 0;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st.n_leaf = st.n_copy = st.n_big = st.big_tiles = st.big_chunks = 0;
+            LeafRun run{};
+            for (uint32_t d = 0; d < bins; ++d) {
+                const uint64_t b_lo = pb_lo + ((uint64_t)d << pl.shift);
+                if (b_lo >= bp.nb) break;  // no bucket, no key beyond this point
+                uint64_t span = (uint64_t)1 << pl.shift;
+                if (span > bp.nb - b_lo) span = bp.nb - b_lo;
+                const uint64_t off = s_off[d], n = s_n[d];
+                const uint64_t below = s_below[d];
+                const uint64_t width = s_below[d + 1] - below;  // key values the span can hold
+                if (n > pl.cap && width > 1) {
+                    stage_run(pl, st, run);
+                    SegDesc c{};
+                    c.start = pstart + off;
+                    c.n = (uint32_t)n;
+                    c.aux = b_lo;
+                    c.key_lo = to_next ? 0 : bp.min + below;  // the next level digits the whole key's bucket id
+                    c.bits = to_next ? 0u : min(bit_length(width - 1), (uint32_t)pl.key_width);
+                    c.tile0 = st.big_tiles;  // offsets inside this parent's reservation
+                    c.chunk0 = st.big_chunks;
+                    st.big_tiles += ceil_div_u32(c.n, pl.tile_keys);
+                    st.big_chunks += ceil_div_u32(c.n, kSegChunk);
+                    st.big[st.n_big++] = c;
+                    continue;
+                }
+                if (run.span > 0 && (run.n + n > pl.cap || run.span + span > 256)) stage_run(pl, st, run);
+                if (run.span == 0) {
+                    run.start = pstart + off;
+                    run.b_lo = b_lo;
+                    run.key_lo = bp.min + below;
+                    run.width = 0;
+                }
+                run.n += n;
+                run.span += span;
+                run.width += width;
+            }
+            stage_run(pl, st, run);
+            SegPlanHdr* bh = to_next ? pl.next_hdr : pl.ovf_hdr;
+            s_base[0] = st.n_leaf ? atomicAdd(pl.num_leaf, st.n_leaf) : 0u;
+            s_base[1] = st.n_copy ? atomicAdd(pl.num_copy, st.n_copy) : 0u;
+            s_base[2] = st.n_big ? atomicAdd(&bh->num_large, st.n_big) : 0u;
+            s_base[3] = st.n_big ? atomicAdd(&bh->total_tiles, st.big_tiles) : 0u;
+            s_base[4] = st.n_big ? atomicAdd(&bh->total_chunks, st.big_chunks) : 0u;
+        }
+        __syncthreads();
+        SegDesc* big_list = to_next ? pl.next : pl.ovf;
+        for (uint32_t i = threadIdx.x; i < st.n_leaf; i += blockDim.x) pl.leaf[s_base[0] + i] = st.leaf[i];
+        for (uint32_t i = threadIdx.x; i < st.n_copy; i += blockDim.x) pl.copy[s_base[1] + i] = st.copy[i];
+        for (uint32_t i = threadIdx.x; i < st.n_big; i += blockDim.x) {
+            SegDesc c = st.big[i];
+            c.tile0 += s_base[3];
+            c.chunk0 += s_base[4];
+            big_list[s_base[2] + i] = c;
+        }
     }
-    if (pl.next && pl.shift > 0) {
-        c.key_lo = 0;  // the next level takes digits of the bucket id of the whole key
-        append_large(pl.next, &pl.next_hdr->num_large, &pl.next_hdr->total_tiles, &pl.next_hdr->total_chunks, c,
-                     pl.tile_keys);
-        return;
-    }
-    append_large(pl.ovf, &pl.ovf_hdr->num_large, &pl.ovf_hdr->total_tiles, &pl.ovf_hdr->total_chunks, c,
-                 pl.tile_keys);
 }
 
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_copy_segments(const KeyT* __restrict__ src_k, const uint32_t* __restrict__ src_v,
                                                        KeyT* dst_k, uint32_t* dst_v, const SegDesc* segs,
                                                        const uint32_t* count) {
-    if (blockIdx.x >= *count) return;
-    const SegDesc s = segs[blockIdx.x];
-    for (uint32_t i = threadIdx.x; i < s.n; i += blockDim.x) {
-        dst_k[s.start + i] = src_k[s.start + i];
-        if (src_v) dst_v[s.start + i] = src_v[s.start + i];
+    for (uint32_t si = blockIdx.x; si < *count; si += gridDim.x) {
+        const SegDesc s = segs[si];
+        for (uint32_t i = threadIdx.x; i < s.n; i += blockDim.x) {
+            dst_k[s.start + i] = src_k[s.start + i];
+            if (src_v) dst_v[s.start + i] = src_v[s.start + i];
+        }
     }
 }
 
@@ -204,8 +285,10 @@ cudaError_t launch_plain_bucket_pass(const PassParams<BucketDigit>& p, cudaStrea
                                         (int)Shape::smem_bytes(8));
     });
     if (attr_err != cudaSuccess) return attr_err;
+    const size_t smem = Shape::smem_bytes(p.digit_bits);
+    const size_t grid = std::min<size_t>(p.num_tiles, (size_t)resident_grid(kern, S::kBlock, smem));
     KernelScope scope("bucket_pass", s);
-    kern<<<p.num_tiles, S::kBlock, Shape::smem_bytes(p.digit_bits), s>>>(p);
+    kern<<<(unsigned)(grid ? grid : 1), S::kBlock, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -419,7 +502,7 @@ static rs_status bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const uint32
         pl.next = I.level2 ? next : nullptr;
         pl.next_hdr = h_next;
         KernelScope scope("bucket_plan", stream);
-        k_bucket_plan<<<(bins1 + 255) / 256, 256, 0, stream>>>(pl);
+        k_bucket_plan<<<1, 256, 0, stream>>>(pl);
         if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
     }
 
@@ -429,7 +512,8 @@ static rs_status bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const uint32
         const size_t parents2 = bins1;
         {
             KernelScope scope("plan_maps", stream);
-            k_plan_maps<<<(unsigned)parents2, 256, 0, stream>>>(next, h_next, tk, tile_seg, chunk_seg);
+            k_plan_maps<<<(unsigned)std::min<size_t>(parents2, (size_t)device_sm_count() * 2), 256, 0, stream>>>(
+                next, h_next, tk, tile_seg, chunk_seg);
             if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
         }
         RS_CUDA_TRY(cudaMemsetAsync(rows, 0, parents2 * bins2 * 4, stream));
@@ -439,7 +523,8 @@ static rs_status bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const uint32
             return RS_ERR_CUDA;
         {
             KernelScope scope("seg_scan", stream);
-            k_seg_scan<<<(unsigned)parents2, 256, (bins2 + 256 / 32 + 1) * 4, stream>>>(rows, h_next, 1, bins2, 0);
+            k_seg_scan<<<(unsigned)std::min<size_t>(parents2, (size_t)device_sm_count() * 2), 256,
+                         (bins2 + 256 / 32 + 1) * 4, stream>>>(rows, h_next, 1, bins2, 0);
             if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
         }
         SegPassParams<BucketDigit> sp{};
@@ -473,7 +558,7 @@ static rs_status bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const uint32
         pl.num_leaf = &h_next->num_small;
         pl.next = nullptr;
         KernelScope scope("bucket_plan", stream);
-        k_bucket_plan<<<(unsigned)((parents2 * bins2 + 255) / 256), 256, 0, stream>>>(pl);
+        k_bucket_plan<<<(unsigned)parents2, 256, 0, stream>>>(pl);
         if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
     }
 

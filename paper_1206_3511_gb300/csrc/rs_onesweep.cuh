@@ -405,6 +405,9 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     }
 }
 
+// Persistent: every block claims tiles from the pass's counter until none is
+// left.  A block holds one tile at a time and only waits on tiles claimed
+// earlier, whose blocks are running, so the waits always end.
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB, typename DigitOp>
 __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p) {
     constexpr int kTile = BLOCK * ITEMS;
@@ -414,32 +417,52 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p)
     const PassSmem<KeyT> sm = carve_pass_smem<KeyT, VALS, BLOCK>(smem, bins, kTile);
     DigitOp op = p.op;
     op.init();
-
     const int tid = threadIdx.x;
-    for (uint32_t i = tid; i < (uint32_t)(BLOCK / 32) * bins; i += BLOCK) sm.tab[i] = 0ull;
-    if (tid == 0) s_tile = atomicAdd(p.tile_ctr, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    if (tile >= p.num_tiles) return;  // uniform across the block
-    if (p.status_next)
-        for (uint32_t d = tid; d < bins; d += BLOCK) p.status_next[(size_t)tile * bins + d] = 0u;
-    TileCtx<KeyT> c;
-    const uint32_t base = tile * (uint32_t)kTile;
-    c.kin = static_cast<const KeyT*>(p.keys_in) + base;
-    c.vin = VALS ? p.vals_in + base : nullptr;
-    c.kout = static_cast<KeyT*>(p.keys_out);
-    c.vout = p.vals_out;
-    c.digit_base = p.digit_base;
-    c.tile = tile;
-    c.first_tile = 0;
-    c.tile_n = min((uint32_t)kTile, p.n - base);
-    c.seg_n = p.n;
-    c.key_lo = 0;
-    const bool publish = (int)tile != p.stall_tile;
-    if (c.tile_n == (uint32_t)kTile)
-        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, true>(p, op, sm, c, bins, publish);
-    else
-        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, false>(p, op, sm, c, bins, publish);
+    while (true) {
+        for (uint32_t i = tid; i < (uint32_t)(BLOCK / 32) * bins; i += BLOCK) sm.tab[i] = 0ull;
+        if (tid == 0) s_tile = atomicAdd(p.tile_ctr, 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= p.num_tiles) return;  // uniform across the block
+        if (p.status_next)
+            for (uint32_t d = tid; d < bins; d += BLOCK) p.status_next[(size_t)tile * bins + d] = 0u;
+        TileCtx<KeyT> c;
+        const uint32_t base = tile * (uint32_t)kTile;
+        c.kin = static_cast<const KeyT*>(p.keys_in) + base;
+        c.vin = VALS ? p.vals_in + base : nullptr;
+        c.kout = static_cast<KeyT*>(p.keys_out);
+        c.vout = p.vals_out;
+        c.digit_base = p.digit_base;
+        c.tile = tile;
+        c.first_tile = 0;
+        c.tile_n = min((uint32_t)kTile, p.n - base);
+        c.seg_n = p.n;
+        c.key_lo = 0;
+        const bool publish = (int)tile != p.stall_tile;
+        if (c.tile_n == (uint32_t)kTile)
+            onesweep_tile<KeyT, VALS, BLOCK, ITEMS, true>(p, op, sm, c, bins, publish);
+        else
+            onesweep_tile<KeyT, VALS, BLOCK, ITEMS, false>(p, op, sm, c, bins, publish);
+        __syncthreads();
+    }
+}
+
+// Blocks of a kernel that fit on the GPU at once (the grid of a persistent
+// launch); at least 1.  The occupancy query is cached per (kernel, shared
+// memory, device): it costs host time on every launch otherwise.
+int resident_grid_cached(const void* kern, int block, size_t smem, int (*query)(const void*, int, size_t));
+
+template <typename Kernel>
+int resident_grid(Kernel kern, int block, size_t smem) {
+    return resident_grid_cached(
+        reinterpret_cast<const void*>(kern), block, smem, [](const void* k, int b, size_t sm) -> int {
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<Kernel>(const_cast<void*>(k)),
+                                                              b, sm) != cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+            return per_sm;
+        });
 }
 
 }  // namespace rs

@@ -1,6 +1,7 @@
 // rs_radix.cu -- LSD radix sort (Sec. 2.5, Algorithm 4) on the GPU: one
 // digit-count kernel, then ceil(key_bits / D) one-sweep scatter passes that
 // ping-pong between keys_out and a workspace buffer and end in keys_out.
+#include <algorithm>
 #include <mutex>
 
 #include "rs_onesweep.cuh"
@@ -23,8 +24,10 @@ cudaError_t launch_pass(const PassParams<RadixDigit>& p, cudaStream_t s) {
         attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     });
     if (attr_err != cudaSuccess) return attr_err;
+    const size_t smem = Shape::smem_bytes(p.digit_bits);
+    const unsigned grid = (unsigned)std::min<size_t>(p.num_tiles, (size_t)resident_grid(kern, BLOCK, smem));
     KernelScope scope("onesweep_pass", s);
-    kern<<<p.num_tiles, BLOCK, Shape::smem_bytes(p.digit_bits), s>>>(p);
+    kern<<<grid ? grid : 1, BLOCK, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -26,8 +26,9 @@ cudaError_t launch_local(const LocalParams& lp, BucketFn bfn, size_t grid, cudaS
         attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
     if (attr_err != cudaSuccess) return attr_err;
+    grid = std::min<size_t>(grid, (size_t)resident_grid(kern, kLocalBlock, smem));
     KernelScope scope("local_sort", s);
-    kern<<<(unsigned)grid, kLocalBlock, smem, s>>>(lp, bfn);
+    kern<<<(unsigned)(grid ? grid : 1), kLocalBlock, smem, s>>>(lp, bfn);
     return cudaGetLastError();
 }
 
@@ -92,7 +93,8 @@ static rs_status large_passes_t(const void* src_k, const uint32_t* src_v, void* 
     const uint32_t tk = seg_tile_keys(sizeof(KeyT), VALS);
     {
         KernelScope scope("plan_maps", stream);
-        k_plan_maps<<<(unsigned)B.max_segs, 256, 0, stream>>>(B.large, B.hdr, tk, B.tile_seg, B.chunk_seg);
+        k_plan_maps<<<(unsigned)std::min<size_t>(B.max_segs, (size_t)device_sm_count() * 8), 256, 0, stream>>>(
+            B.large, B.hdr, tk, B.tile_seg, B.chunk_seg);
         if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
     }
     RS_CUDA_TRY(cudaMemsetAsync(B.seg_rows, 0, B.max_segs * (size_t)passes * bins * 4, stream));
@@ -102,8 +104,8 @@ static rs_status large_passes_t(const void* src_k, const uint32_t* src_v, void* 
         return RS_ERR_CUDA;
     {
         KernelScope scope("seg_scan", stream);
-        k_seg_scan<<<(unsigned)(B.max_segs * passes), 256, (bins + 256 / 32 + 1) * 4, stream>>>(B.seg_rows, B.hdr,
-                                                                                                passes, bins, 0);
+        k_seg_scan<<<(unsigned)std::min<size_t>(B.max_segs * passes, (size_t)device_sm_count() * 8), 256,
+                     (bins + 256 / 32 + 1) * 4, stream>>>(B.seg_rows, B.hdr, passes, bins, 0);
         if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
     }
     SegPassParams<RadixDigit> sp{};

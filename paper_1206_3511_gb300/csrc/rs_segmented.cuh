@@ -74,12 +74,12 @@ static __global__ void k_plan_from_offsets(const uint64_t* __restrict__ offsets,
 // tile -> segment and chunk -> segment maps; one block per large segment.
 static __global__ void k_plan_maps(const SegDesc* __restrict__ large, const SegPlanHdr* __restrict__ hdr,
                             uint32_t tile_keys, uint32_t* tile_seg, uint32_t* chunk_seg) {
-    const uint32_t li = blockIdx.x;
-    if (li >= hdr->num_large) return;
-    const SegDesc d = large[li];
-    const uint32_t nt = ceil_div_u32(d.n, tile_keys), nc = ceil_div_u32(d.n, kSegChunk);
-    for (uint32_t i = threadIdx.x; i < nt; i += blockDim.x) tile_seg[d.tile0 + i] = li;
-    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) chunk_seg[d.chunk0 + i] = li;
+    for (uint32_t li = blockIdx.x; li < hdr->num_large; li += gridDim.x) {
+        const SegDesc d = large[li];
+        const uint32_t nt = ceil_div_u32(d.n, tile_keys), nc = ceil_div_u32(d.n, kSegChunk);
+        for (uint32_t i = threadIdx.x; i < nt; i += blockDim.x) tile_seg[d.tile0 + i] = li;
+        for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) chunk_seg[d.chunk0 + i] = li;
+    }
 }
 
 // Per-segment digit counts of `passes` digits: seg_counts[li][q][d].  One
@@ -97,26 +97,27 @@ __global__ void __launch_bounds__(512) k_seg_counts(const KeyT* __restrict__ key
     if (zero_words > used_words) zero_words = used_words;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + tid; i < zero_words; i += (size_t)gridDim.x * blockDim.x)
         zero_ptr[i] = 0u;
-    const uint32_t c = blockIdx.x;
-    if (c >= hdr->total_chunks) return;
     dg.init();
-    const uint32_t li = chunk_seg[c];
-    const SegDesc d = large[li];
-    const uint32_t lo = (c - d.chunk0) * kSegChunk;
-    const uint32_t hi = min(d.n, lo + kSegChunk);
     const int ncnt = passes * (int)bins;
-    for (int i = tid; i < ncnt; i += blockDim.x) s_cnt[i] = 0;
-    __syncthreads();
-    const KeyT* kp = keys + d.start;
-    const KeyT klo = (KeyT)d.key_lo;
-    for (uint32_t i = lo + tid; i < hi; i += blockDim.x) {
-        const KeyT x = (KeyT)(__ldcs(kp + i) - klo);
-        for (int q = 0; q < passes; ++q) atomicAdd(&s_cnt[q * bins + dg(x, q)], 1u);
+    for (uint32_t c = blockIdx.x; c < hdr->total_chunks; c += gridDim.x) {
+        const uint32_t li = chunk_seg[c];
+        const SegDesc d = large[li];
+        const uint32_t lo = (c - d.chunk0) * kSegChunk;
+        const uint32_t hi = min(d.n, lo + kSegChunk);
+        __syncthreads();
+        for (int i = tid; i < ncnt; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        const KeyT* kp = keys + d.start;
+        const KeyT klo = (KeyT)d.key_lo;
+        for (uint32_t i = lo + tid; i < hi; i += blockDim.x) {
+            const KeyT x = (KeyT)(__ldcs(kp + i) - klo);
+            for (int q = 0; q < passes; ++q) atomicAdd(&s_cnt[q * bins + dg(x, q)], 1u);
+        }
+        __syncthreads();
+        uint32_t* out = seg_counts + (size_t)li * ncnt;
+        for (int i = tid; i < ncnt; i += blockDim.x)
+            if (s_cnt[i]) atomicAdd(&out[i], s_cnt[i]);
     }
-    __syncthreads();
-    uint32_t* out = seg_counts + (size_t)li * ncnt;
-    for (int i = tid; i < ncnt; i += blockDim.x)
-        if (s_cnt[i]) atomicAdd(&out[i], s_cnt[i]);
 }
 
 // Exclusive prefix of every (segment, pass) row of bins counts, in place.
@@ -125,12 +126,14 @@ static __global__ void __launch_bounds__(256) k_seg_scan(uint32_t* rows, const S
                                                   uint32_t bins, int use_next) {
     extern __shared__ uint32_t s_row[];  // [bins] + scan scratch
     const uint32_t nrows = (use_next ? hdr->num_next : hdr->num_large) * (uint32_t)passes;
-    if (blockIdx.x >= nrows) return;
-    uint32_t* row = rows + (size_t)blockIdx.x * bins;
-    for (uint32_t d = threadIdx.x; d < bins; d += 256) s_row[d] = row[d];
-    __syncthreads();
-    block_exclusive_scan_smem<256>(s_row, (int)bins, s_row + bins);
-    for (uint32_t d = threadIdx.x; d < bins; d += 256) row[d] = s_row[d];
+    for (uint32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        uint32_t* row = rows + (size_t)r * bins;
+        __syncthreads();
+        for (uint32_t d = threadIdx.x; d < bins; d += 256) s_row[d] = row[d];
+        __syncthreads();
+        block_exclusive_scan_smem<256>(s_row, (int)bins, s_row + bins);
+        for (uint32_t d = threadIdx.x; d < bins; d += 256) row[d] = s_row[d];
+    }
 }
 
 // Parameters of a segmented scatter pass.
@@ -156,32 +159,35 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep_seg(SegPassParams<Digi
     DigitOp op = p.op;
     op.init();
     const int tid = threadIdx.x;
-    for (uint32_t i = tid; i < (uint32_t)(BLOCK / 32) * bins; i += BLOCK) sm.tab[i] = 0ull;
-    if (tid == 0) s_tile = atomicAdd(p.tile_ctr, 1u);
-    __syncthreads();
-    const uint32_t g = s_tile;
-    if (g >= sp.hdr->total_tiles) return;  // uniform across the block
-    if (p.status_next)
-        for (uint32_t d = tid; d < bins; d += BLOCK) p.status_next[(size_t)g * bins + d] = 0u;
-    const uint32_t li = sp.tile_seg[g];
-    const SegDesc seg = sp.segs[li];
-    const uint32_t base = (g - seg.tile0) * (uint32_t)kTile;
-    TileCtx<KeyT> c;
-    c.kin = static_cast<const KeyT*>(p.keys_in) + seg.start + base;
-    c.vin = VALS ? p.vals_in + seg.start + base : nullptr;
-    c.kout = static_cast<KeyT*>(p.keys_out) + seg.start;
-    c.vout = VALS ? p.vals_out + seg.start : nullptr;
-    c.digit_base = sp.seg_base + ((size_t)li * sp.passes + sp.pass) * bins;
-    c.tile = g;
-    c.first_tile = seg.tile0;
-    c.tile_n = min((uint32_t)kTile, seg.n - base);
-    c.seg_n = seg.n;
-    c.key_lo = (KeyT)seg.key_lo;
-    const bool publish = (int)g != p.stall_tile;
-    if (c.tile_n == (uint32_t)kTile)
-        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, true>(p, op, sm, c, bins, publish);
-    else
-        onesweep_tile<KeyT, VALS, BLOCK, ITEMS, false>(p, op, sm, c, bins, publish);
+    while (true) {
+        for (uint32_t i = tid; i < (uint32_t)(BLOCK / 32) * bins; i += BLOCK) sm.tab[i] = 0ull;
+        if (tid == 0) s_tile = atomicAdd(p.tile_ctr, 1u);
+        __syncthreads();
+        const uint32_t g = s_tile;
+        if (g >= sp.hdr->total_tiles) return;  // uniform across the block
+        if (p.status_next)
+            for (uint32_t d = tid; d < bins; d += BLOCK) p.status_next[(size_t)g * bins + d] = 0u;
+        const uint32_t li = sp.tile_seg[g];
+        const SegDesc seg = sp.segs[li];
+        const uint32_t base = (g - seg.tile0) * (uint32_t)kTile;
+        TileCtx<KeyT> c;
+        c.kin = static_cast<const KeyT*>(p.keys_in) + seg.start + base;
+        c.vin = VALS ? p.vals_in + seg.start + base : nullptr;
+        c.kout = static_cast<KeyT*>(p.keys_out) + seg.start;
+        c.vout = VALS ? p.vals_out + seg.start : nullptr;
+        c.digit_base = sp.seg_base + ((size_t)li * sp.passes + sp.pass) * bins;
+        c.tile = g;
+        c.first_tile = seg.tile0;
+        c.tile_n = min((uint32_t)kTile, seg.n - base);
+        c.seg_n = seg.n;
+        c.key_lo = (KeyT)seg.key_lo;
+        const bool publish = (int)g != p.stall_tile;
+        if (c.tile_n == (uint32_t)kTile)
+            onesweep_tile<KeyT, VALS, BLOCK, ITEMS, true>(p, op, sm, c, bins, publish);
+        else
+            onesweep_tile<KeyT, VALS, BLOCK, ITEMS, false>(p, op, sm, c, bins, publish);
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -220,14 +226,19 @@ __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, K
     __syncthreads();
     const uint32_t tab = smem_addr(s_tab + (size_t)warp * 256);
     const uint32_t lt = lanemask_lt(), lanebit = 1u << lane, gt = ~(lt | lanebit);
-    const uint32_t wofs = (uint32_t)warp * (ITEMS * 32) + lane;
+    // each warp owns a contiguous run of `used` items of 32 keys, just enough
+    // to cover the m keys of the segment
+    const uint32_t used = (m + BLOCK - 1) / BLOCK;
+    const uint32_t wofs = (uint32_t)warp * (used * 32) + lane;
     uint32_t dr[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t idx = wofs + i * 32;
-        const bool ok = idx < m;
-        const uint32_t d = ok ? dfun(ka[idx]) : 0u;
-        dr[i] = (d << 16) | warp_rank<false>(tab, d, ok, lanebit, lt, gt);
+        if ((uint32_t)i < used) {
+            const uint32_t idx = wofs + i * 32;
+            const bool ok = idx < m;
+            const uint32_t d = ok ? dfun(ka[idx]) : 0u;
+            dr[i] = (d << 16) | warp_rank<false>(tab, d, ok, lanebit, lt, gt);
+        }
     }
     __syncthreads();
     for (uint32_t d = tid; d < 256; d += BLOCK) {
@@ -253,7 +264,7 @@ __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, K
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const uint32_t idx = wofs + i * 32;
-        if (idx < m) {
+        if ((uint32_t)i < used && idx < m) {
             const uint32_t pos = ld_shared_u32(tab + 8u * (dr[i] >> 16)) + (dr[i] & 0xffffu);
             if (pos < m) {
                 kb[pos] = ka[idx];
@@ -275,13 +286,10 @@ struct LocalParams {
 };
 
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename BucketFn>
-__global__ void __launch_bounds__(BLOCK) k_local_sort(LocalParams lp, BucketFn bfn) {
+__global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketFn bfn) {
     constexpr int kCap = BLOCK * ITEMS;
     constexpr int kWarps = BLOCK / 32;
     extern __shared__ __align__(16) unsigned char smem[];
-    if (blockIdx.x >= *lp.count) return;
-    const SegDesc seg = lp.segs[blockIdx.x];
-    const uint32_t m = seg.n;
     unsigned long long* s_tab = reinterpret_cast<unsigned long long*>(smem);
     KeyT* kbuf[2];
     kbuf[0] = reinterpret_cast<KeyT*>(s_tab + kWarps * 256);
@@ -294,67 +302,74 @@ __global__ void __launch_bounds__(BLOCK) k_local_sort(LocalParams lp, BucketFn b
     uint32_t* s_scan = s_cnt + 256;
     uint32_t* s_flag = s_scan + kWarps + 1;
 
-    const KeyT* kin = static_cast<const KeyT*>(lp.keys_in) + seg.start;
-    for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
-        kbuf[0][i] = kin[i];
-        if (VALS) vbuf[0][i] = lp.vals_in[seg.start + i];
-    }
-    const KeyT klo = (KeyT)seg.key_lo;
-    int cur = 0;
-    bool by_keys = true;
-    if (bfn.active()) {
-        bfn.init();
-        const uint64_t b_lo = bfn.first_bucket(seg), span = bfn.bucket_span(seg);
-        if (threadIdx.x == 0) *s_flag = 0u;
+    if (bfn.active()) bfn.init();
+    const uint32_t nseg = *lp.count;
+    for (uint32_t si = blockIdx.x; si < nseg; si += gridDim.x) {
+        const SegDesc seg = lp.segs[si];
+        const uint32_t m = seg.n;
         __syncthreads();
-        if (span <= 256) {
-            local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[0], vbuf[0], kbuf[1], vbuf[1], m, s_tab, s_start, s_cnt, s_scan,
-                                                 [&](KeyT k) { return (uint32_t)(bfn.bucket(k) - b_lo); });
-            cur = 1;
-            for (uint32_t d = threadIdx.x; d < 256; d += BLOCK)
-                if (s_cnt[d] > kInsertionMax) *s_flag = 1u;
+        const KeyT* kin = static_cast<const KeyT*>(lp.keys_in) + seg.start;
+        for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
+            kbuf[0][i] = kin[i];
+            if (VALS) vbuf[0][i] = lp.vals_in[seg.start + i];
+        }
+        const KeyT klo = (KeyT)seg.key_lo;
+        int cur = 0;
+        bool by_keys = true;
+        if (bfn.active()) {
+            const uint64_t b_lo = bfn.first_bucket(seg), span = bfn.bucket_span(seg);
+            if (threadIdx.x == 0) *s_flag = 0u;
             __syncthreads();
-            if (*s_flag == 0u) {
-                by_keys = false;
-                // Algorithm 1 on every bucket: thread d sorts bucket d in place
-                for (uint32_t d = threadIdx.x; d < 256; d += BLOCK) {
-                    KeyT* A = kbuf[1] + s_start[d];
-                    uint32_t* V = vbuf[1] + (VALS ? s_start[d] : 0);
-                    const uint32_t len = s_cnt[d];
-                    for (uint32_t j = 1; j < len; ++j) {
-                        const KeyT key = A[j];
-                        uint32_t val = 0;
-                        if (VALS) val = V[j];
-                        uint32_t i = j;
-                        while (i > 0 && A[i - 1] > key) {
-                            A[i] = A[i - 1];
-                            if (VALS) V[i] = V[i - 1];
-                            --i;
+            if (span <= 256) {
+                local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[0], vbuf[0], kbuf[1], vbuf[1], m, s_tab, s_start, s_cnt, s_scan,
+                                                     [&](KeyT k) { return (uint32_t)(bfn.bucket(k) - b_lo); });
+                cur = 1;
+                for (uint32_t d = threadIdx.x; d < 256; d += BLOCK)
+                    if (s_cnt[d] > kInsertionMax) *s_flag = 1u;
+                __syncthreads();
+                if (*s_flag == 0u) {
+                    by_keys = false;
+                    // Algorithm 1 on every bucket: thread d sorts bucket d in place
+                    for (uint32_t d = threadIdx.x; d < 256; d += BLOCK) {
+                        KeyT* A = kbuf[1] + s_start[d];
+                        uint32_t* V = vbuf[1] + (VALS ? s_start[d] : 0);
+                        const uint32_t len = s_cnt[d];
+                        for (uint32_t j = 1; j < len; ++j) {
+                            const KeyT key = A[j];
+                            uint32_t val = 0;
+                            if (VALS) val = V[j];
+                            uint32_t i = j;
+                            while (i > 0 && A[i - 1] > key) {
+                                A[i] = A[i - 1];
+                                if (VALS) V[i] = V[i - 1];
+                                --i;
+                            }
+                            A[i] = key;
+                            if (VALS) V[i] = val;
                         }
-                        A[i] = key;
-                        if (VALS) V[i] = val;
                     }
+                    __syncthreads();
                 }
+            } else {
                 __syncthreads();
             }
         } else {
             __syncthreads();
         }
-    } else {
-        __syncthreads();
-    }
-    if (by_keys) {
-        for (uint32_t shift = 0; shift < seg.bits; shift += 8) {
-            local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1], m, s_tab, s_start,
-                                                 s_cnt, s_scan,
-                                                 [&](KeyT k) { return (uint32_t)((KeyT)(k - klo) >> shift) & 255u; });
-            cur ^= 1;
+        if (by_keys) {
+            for (uint32_t shift = 0; shift < seg.bits; shift += 8) {
+                local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1], m, s_tab, s_start,
+                                                     s_cnt, s_scan,
+                                                     [&](KeyT k) { return (uint32_t)((KeyT)(k - klo) >> shift) & 255u; });
+                cur ^= 1;
+            }
         }
-    }
-    KeyT* kout = static_cast<KeyT*>(lp.keys_out) + seg.start;
-    for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
-        kout[i] = kbuf[cur][i];
-        if (VALS) lp.vals_out[seg.start + i] = vbuf[cur][i];
+        KeyT* kout = static_cast<KeyT*>(lp.keys_out) + seg.start;
+        for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
+            kout[i] = kbuf[cur][i];
+            if (VALS) lp.vals_out[seg.start + i] = vbuf[cur][i];
+        }
+        __syncthreads();
     }
 }
 

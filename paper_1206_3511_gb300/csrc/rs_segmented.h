@@ -2,6 +2,8 @@
 // shared with the bucket sort.
 #pragma once
 
+#include <algorithm>
+
 #include "rs_radix.h"
 #include "rs_segmented.cuh"
 
@@ -45,8 +47,10 @@ cudaError_t launch_seg_pass(const SegPassParams<DigitOp>& sp, size_t grid, cudaS
                                         (int)Shape::smem_bytes(kMaxDigitBits));
     });
     if (attr_err != cudaSuccess) return attr_err;
+    const size_t smem = Shape::smem_bytes(sp.base.digit_bits);
+    grid = std::min<size_t>(grid, (size_t)resident_grid(kern, S::kBlock, smem));
     KernelScope scope("onesweep_seg_pass", s);
-    kern<<<(unsigned)grid, S::kBlock, Shape::smem_bytes(sp.base.digit_bits), s>>>(sp);
+    kern<<<(unsigned)(grid ? grid : 1), S::kBlock, smem, s>>>(sp);
     return cudaGetLastError();
 }
 
@@ -62,9 +66,10 @@ cudaError_t launch_seg_counts(const KeyT* keys, const SegDesc* segs, const SegPl
                                         (int)max_count_smem_bytes());
     });
     if (attr_err != cudaSuccess) return attr_err;
+    const size_t grid = std::min<size_t>(max_chunks, (size_t)device_sm_count() * 4);
     KernelScope scope("seg_counts", s);
-    kern<<<(unsigned)max_chunks, 512, (size_t)passes * bins * 4, s>>>(keys, segs, hdr, chunk_seg, dg, passes, bins,
-                                                                     rows, zero_ptr, zero_words);
+    kern<<<(unsigned)(grid ? grid : 1), 512, (size_t)passes * bins * 4, s>>>(keys, segs, hdr, chunk_seg, dg, passes,
+                                                                            bins, rows, zero_ptr, zero_words);
     return cudaGetLastError();
 }
 
