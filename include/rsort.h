@@ -213,6 +213,74 @@ RS_API rs_status rs_sort_segmented_u64(const uint64_t* keys_in, uint64_t* keys_o
                                        size_t n_total, int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Sort server (continuous batching).  Requests arrive at any time from any
+ * host thread; a dispatcher thread admits them, oldest first, while the
+ * memory they need fits under budget_bytes, and keeps up to num_streams
+ * launches in flight on separate streams so their work overlaps on the GPU.
+ * Waiting radix requests of at most batch_max_keys keys with the same key
+ * type, value presence and key_bits are packed, up to max_batch at a time,
+ * into one segmented sort (their keys are gathered into the pool, sorted per
+ * segment and copied back); other requests run as single sorts.  Each
+ * request's output is exactly what rs_sort_* / bs_sort_* would produce for
+ * it alone.
+ *
+ * pool/pool_bytes: caller-owned DEVICE memory (256-byte aligned) from which
+ * the server takes workspaces and batch staging; the server never allocates
+ * device memory.  budget_bytes (0 = pool_bytes): admission budget over every
+ * admitted request's own inputs and outputs, its workspace and any staging.
+ * A request that can never fit is refused at submit with RS_ERR_BUDGET.
+ * Request buffers must stay valid and untouched until the request is done.
+ * The server uses the CUDA device that is current at rs_server_create.
+ */
+typedef struct rs_server rs_server;
+typedef struct rs_server_config {
+    void* pool;
+    size_t pool_bytes;
+    size_t budget_bytes;
+    int num_streams;        /* 1 .. 64 */
+    int max_batch;          /* requests per batched launch, >= 1 (1 = no batching) */
+    size_t batch_max_keys;  /* largest request that may be batched (0 = 262144) */
+} rs_server_config;
+typedef struct rs_request {
+    int algo;       /* RS_ALGO_RADIX or RS_ALGO_BUCKET */
+    int key_bytes;  /* 4 or 8 */
+    const void* keys_in;
+    void* keys_out;
+    const uint32_t* vals_in; /* NULL for keys only */
+    uint32_t* vals_out;
+    size_t n;
+    int key_bits;           /* radix: as rs_sort_*; ignored for bucket */
+    uint64_t min_key, max_key; /* bucket: as bs_sort_* (min > max: computed) */
+    size_t num_buckets;     /* bucket: as bs_sort_* */
+} rs_request;
+typedef struct rs_result {
+    rs_status status;   /* RS_ERR_NOT_READY while queued or running */
+    double t_arrive_ms; /* host steady-clock times: submit, launch, completion seen */
+    double t_start_ms;
+    double t_done_ms;
+} rs_result;
+typedef struct rs_server_stats {
+    uint64_t submitted, completed, rejected, queued;
+    size_t in_use_bytes, max_in_use_bytes, budget_bytes;
+    uint64_t batches, batched_requests;
+} rs_server_stats;
+
+RS_API rs_status rs_server_create(const rs_server_config* cfg, rs_server** out);
+/* Queue a request; *ticket identifies it.  RS_ERR_BUDGET: it can never fit;
+ * RS_ERR_SHUTDOWN: the server is being destroyed. */
+RS_API rs_status rs_server_submit(rs_server* s, const rs_request* req, uint64_t* ticket);
+/* Status of a request without waiting (RS_ERR_NOT_READY while not done). */
+RS_API rs_status rs_server_poll(rs_server* s, uint64_t ticket, rs_result* out);
+/* Wait up to timeout_ms (< 0: forever) for a request; its status, or
+ * RS_ERR_NOT_READY on timeout. */
+RS_API rs_status rs_server_wait(rs_server* s, uint64_t ticket, int timeout_ms);
+RS_API rs_status rs_server_get_stats(rs_server* s, rs_server_stats* out);
+/* Stop accepting requests; finish (cancel_pending = 0) or cancel (nonzero:
+ * queued requests end with RS_ERR_SHUTDOWN) the queue, wait for launches in
+ * flight, release streams and the dispatcher.  The pool is not freed. */
+RS_API rs_status rs_server_destroy(rs_server* s, int cancel_pending);
+
+/* ---------------------------------------------------------------------------
  * Sorting without a caller-provided workspace.  The paper has no counterpart:
  * this exists for callers that cannot allocate device memory (code running
  * where cudaMalloc is not allowed or not available, or that cannot own an

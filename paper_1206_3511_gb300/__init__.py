@@ -14,7 +14,8 @@ bits are sorted as unsigned).  Values are 32-bit (uint32 or int32).
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (bs_sort_u32, bs_sort_u64, rs_segmented_workspace_bytes, rs_sort_segmented_u32, rs_sort_segmented_u64,
+from ._lib import (RsRequest, RsResult, RsServerConfig, RsServerStats, rs_server_create, rs_server_destroy,
+                   rs_server_get_stats, rs_server_poll, rs_server_submit, rs_server_wait, bs_sort_u32, bs_sort_u64, rs_segmented_workspace_bytes, rs_sort_segmented_u32, rs_sort_segmented_u64,
                    RS_ALGO_BUCKET, RS_ALGO_RADIX, STATUS, RsConfig, load, rs_config_count, rs_config_get,
                    rs_counting_pass_u32, rs_counting_pass_u64, rs_default_config, rs_digit_counts_u32,
                    rs_digit_counts_u64, rs_get_status, rs_launch_count, rs_profile_enable, rs_profile_read,
@@ -29,7 +30,9 @@ __all__ = [
     "rs_config_count", "rs_config_get", "RsConfig", "RS_ALGO_RADIX", "RS_ALGO_BUCKET", "STATUS",
     "rs_profile_enable", "rs_profile_read", "rs_launch_count", "rs_sort_u32_noalloc",
     "rs_segmented_workspace_bytes", "rs_sort_segmented_u32", "rs_sort_segmented_u64", "segmented_sort",
-    "bs_sort_u32", "bs_sort_u64", "bucket_sort",
+    "bs_sort_u32", "bs_sort_u64", "bucket_sort", "Server", "RsRequest", "RsResult", "RsServerConfig",
+    "RsServerStats", "rs_server_create", "rs_server_destroy", "rs_server_get_stats", "rs_server_poll",
+    "rs_server_submit", "rs_server_wait",
 ]
 
 
@@ -176,3 +179,55 @@ def bucket_sort(keys, values=None, min_key=None, max_key=None, num_buckets: int 
     fn = bs_sort_u32 if kb == 4 else bs_sort_u64
     check(fn(keys, out, values, out_values, n, min_key, max_key, num_buckets, ws, ws.numel(), stream), "bs_sort")
     return out, out_values
+
+
+class Server:
+    """Sort server over the C ABI (rs_server_*): requests are sorted
+    asynchronously with admission under a memory budget and continuous
+    batching.  The device pool is a torch uint8 buffer kept alive here."""
+
+    def __init__(self, pool_bytes: int, budget_bytes: int = 0, num_streams: int = 4, max_batch: int = 64,
+                 batch_max_keys: int = 0, device=None):
+        self.pool = workspace(pool_bytes, device)
+        cfg = RsServerConfig(self.pool.data_ptr(), self.pool.numel(), budget_bytes, num_streams, max_batch,
+                             batch_max_keys)
+        rc, self.handle = rs_server_create(cfg)
+        check(rc, "rs_server_create")
+        self._keep = {}
+
+    def submit(self, keys_in, keys_out, vals_in=None, vals_out=None, algo: int = RS_ALGO_RADIX, key_bits: int = 0,
+               min_key: int = 1, max_key: int = 0, num_buckets: int = 0) -> int:
+        """Queue one sort; returns its ticket.  The tensors must stay alive
+        and untouched until the request is done (kept referenced here)."""
+        req = RsRequest(algo, key_bytes_of(keys_in), keys_in.data_ptr(), keys_out.data_ptr(),
+                        vals_in.data_ptr() if vals_in is not None else None,
+                        vals_out.data_ptr() if vals_out is not None else None, keys_in.numel(), key_bits,
+                        min_key, max_key, num_buckets)
+        rc, ticket = rs_server_submit(self.handle, req)
+        check(rc, "rs_server_submit")
+        self._keep[ticket] = (keys_in, keys_out, vals_in, vals_out)
+        return ticket
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> int:
+        rc = rs_server_wait(self.handle, ticket, timeout_ms)
+        if rc != 7:  # done (RS_ERR_NOT_READY means still running)
+            self._keep.pop(ticket, None)
+        return rc
+
+    def result(self, ticket: int):
+        return rs_server_poll(self.handle, ticket)
+
+    def stats(self):
+        return rs_server_get_stats(self.handle)
+
+    def close(self, cancel_pending: bool = False) -> None:
+        if self.handle:
+            rs_server_destroy(self.handle, cancel_pending)
+            self.handle = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

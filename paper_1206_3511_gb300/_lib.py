@@ -36,6 +36,28 @@ class RsKernelStat(_c.Structure):
     _fields_ = [("name", _c.c_char * 32), ("launches", _c.c_uint64), ("total_ms", _c.c_double)]
 
 
+class RsServerConfig(_c.Structure):
+    _fields_ = [("pool", _c.c_void_p), ("pool_bytes", _c.c_size_t), ("budget_bytes", _c.c_size_t),
+                ("num_streams", _c.c_int), ("max_batch", _c.c_int), ("batch_max_keys", _c.c_size_t)]
+
+
+class RsRequest(_c.Structure):
+    _fields_ = [("algo", _c.c_int), ("key_bytes", _c.c_int), ("keys_in", _c.c_void_p), ("keys_out", _c.c_void_p),
+                ("vals_in", _c.c_void_p), ("vals_out", _c.c_void_p), ("n", _c.c_size_t), ("key_bits", _c.c_int),
+                ("min_key", _c.c_uint64), ("max_key", _c.c_uint64), ("num_buckets", _c.c_size_t)]
+
+
+class RsResult(_c.Structure):
+    _fields_ = [("status", _c.c_int), ("t_arrive_ms", _c.c_double), ("t_start_ms", _c.c_double),
+                ("t_done_ms", _c.c_double)]
+
+
+class RsServerStats(_c.Structure):
+    _fields_ = [("submitted", _c.c_uint64), ("completed", _c.c_uint64), ("rejected", _c.c_uint64),
+                ("queued", _c.c_uint64), ("in_use_bytes", _c.c_size_t), ("max_in_use_bytes", _c.c_size_t),
+                ("budget_bytes", _c.c_size_t), ("batches", _c.c_uint64), ("batched_requests", _c.c_uint64)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES: dict[str, tuple] = {
     "rs_status_string": (_c.c_char_p, [_I]),
@@ -58,6 +80,12 @@ SIGNATURES: dict[str, tuple] = {
     "rs_segmented_workspace_bytes": (_SZ, [_I, _I, _SZ, _SZ, _I]),
     "rs_sort_segmented_u32": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P]),
     "rs_sort_segmented_u64": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P]),
+    "rs_server_create": (_I, [_c.POINTER(RsServerConfig), _c.POINTER(_c.c_void_p)]),
+    "rs_server_submit": (_I, [_P, _c.POINTER(RsRequest), _c.POINTER(_c.c_uint64)]),
+    "rs_server_poll": (_I, [_P, _c.c_uint64, _c.POINTER(RsResult)]),
+    "rs_server_wait": (_I, [_P, _c.c_uint64, _I]),
+    "rs_server_get_stats": (_I, [_P, _c.POINTER(RsServerStats)]),
+    "rs_server_destroy": (_I, [_P, _I]),
     "rs_sort_u32_noalloc": (_I, [_P, _P, _P, _P, _SZ, _I, _P]),
     "rs_get_status": (_I, [_P, _P]),
     "rs_set_debug": (None, [_U32, _I]),
@@ -233,6 +261,43 @@ def rs_sort_segmented_u64(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, n
                           stream=None) -> int:
     return _call("rs_sort_segmented_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out),
                  ptr(d_seg_offsets), nseg, n_total, key_bits, ptr(ws), ws_bytes, stream_handle(stream))
+
+
+def rs_server_create(cfg: RsServerConfig):
+    """Returns (status, server handle)."""
+    h = _c.c_void_p()
+    rc = _call("rs_server_create", _c.byref(cfg), _c.byref(h))
+    return rc, h.value
+
+
+def rs_server_submit(server, req: RsRequest):
+    """Returns (status, ticket)."""
+    t = _c.c_uint64()
+    rc = _call("rs_server_submit", server, _c.byref(req), _c.byref(t))
+    return rc, t.value
+
+
+def rs_server_poll(server, ticket):
+    """Returns (status, RsResult)."""
+    r = RsResult()
+    rc = _call("rs_server_poll", server, ticket, _c.byref(r))
+    return rc, r
+
+
+def rs_server_wait(server, ticket, timeout_ms=-1) -> int:
+    return _call("rs_server_wait", server, ticket, timeout_ms)
+
+
+def rs_server_get_stats(server) -> RsServerStats:
+    st = RsServerStats()
+    rc = _call("rs_server_get_stats", server, _c.byref(st))
+    if rc:
+        raise RuntimeError(STATUS.get(rc, rc))
+    return st
+
+
+def rs_server_destroy(server, cancel_pending=False) -> int:
+    return _call("rs_server_destroy", server, int(bool(cancel_pending)))
 
 
 RS_NOALLOC_MAX_KEYS = 1 << 20

@@ -1,0 +1,155 @@
+"""The sort server: every request's result in the mix equals the result of
+sorting it alone (zero tolerance), admission never exceeds the budget, small
+requests are batched, requests that can never fit are refused, and shutdown
+cancels what is still queued."""
+import threading
+
+import numpy as np
+import pytest
+
+import synth
+from tests._util import assert_same, from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix(seed=0, count=60):
+    """Sizes log-uniform in [1000, 2000000], 70% u32 keys only, 30% u64 keys
+    with index values, radix and bucket requests."""
+    sizes = synth.log_uniform_sizes(count, 1000, 2_000_000, seed=seed, dist_id=31)
+    kinds = synth.uniform_below(count, 10, seed, 32)
+    algos = synth.uniform_below(count, 2, seed, 33)
+    reqs = []
+    for i, (n, k, a) in enumerate(zip(sizes.tolist(), kinds.tolist(), algos.tolist())):
+        if k < 7:
+            keys = synth.keys_u32(n, i % 7, seed=100 + i)
+            vals = None
+        else:
+            keys = synth.keys_u64(n, 64, seed=100 + i)
+            vals = synth.index_values(n)
+        reqs.append((keys, vals, 1 if a else 0))
+    return reqs
+
+
+def _submit_all(rs, srv, reqs):
+    """Stage every request on the device first, then submit them back to back
+    (requests that arrive while others run are what gets batched)."""
+    import torch
+
+    staged = []
+    for keys, vals, algo in reqs:
+        kd = to_dev(keys)
+        vd = to_dev(vals) if vals is not None else None
+        ko = torch.empty_like(kd)
+        vo = torch.empty_like(vd) if vd is not None else None
+        staged.append((kd, ko, vd, vo, algo))
+    torch.cuda.synchronize()
+    handles = []
+    for kd, ko, vd, vo, algo in staged:
+        t = srv.submit(kd, ko, vd, vo, algo=algo)
+        handles.append((t, ko, vo))
+    return handles
+
+
+def test_results_in_the_mix_equal_results_alone(rs, oracle):
+    reqs = _mix(0, 60)
+    with rs.Server(pool_bytes=6 << 30, num_streams=4, max_batch=16, batch_max_keys=1 << 18) as srv:
+        handles = _submit_all(rs, srv, reqs)
+        for (t, ko, vo), (keys, vals, algo) in zip(handles, reqs):
+            assert srv.wait(t, 60_000) == 0
+            gk = from_dev(ko, keys.dtype)
+            if vals is None:
+                assert_same(gk, oracle.radix_sort(keys), f"ticket {t}")
+            else:
+                wk, wv = oracle.radix_sort(keys, vals)
+                assert_same(gk, wk, f"ticket {t} keys")
+                assert_same(from_dev(vo, np.uint32), wv, f"ticket {t} values")
+        st = srv.stats()
+        assert st.completed == len(reqs) and st.rejected == 0
+        assert st.batches >= 1 and st.batched_requests >= 2
+        assert st.max_in_use_bytes <= st.budget_bytes
+
+
+def test_budget_is_never_exceeded_and_everything_completes(rs):
+    import torch
+
+    budget = 300 << 20
+    with rs.Server(pool_bytes=1 << 30, budget_bytes=budget, num_streams=4, max_batch=8) as srv:
+        tickets = []
+        outs = []
+        for i in range(24):
+            n = 3_000_000 if i % 3 == 0 else 100_000
+            kd = to_dev(synth.u32(n, 60 + i, 0))
+            ko = torch.empty_like(kd)
+            tickets.append(srv.submit(kd, ko))
+            outs.append((kd, ko))
+        for t in tickets:
+            assert srv.wait(t, 60_000) == 0
+        st = srv.stats()
+        assert st.completed == 24
+        assert 0 < st.max_in_use_bytes <= budget
+        for kd, ko in outs:
+            a = ko.cpu().numpy().view(np.uint32)
+            assert np.all(a[1:] >= a[:-1])
+
+
+def test_submissions_from_many_threads(rs, oracle):
+    import torch
+
+    with rs.Server(pool_bytes=2 << 30, num_streams=3, max_batch=32) as srv:
+        results = {}
+        lock = threading.Lock()
+
+        def worker(w):
+            for j in range(10):
+                keys = synth.u32(5000 + 977 * j + w, 70 + w * 10 + j, 0)
+                kd = to_dev(keys)
+                ko = torch.empty_like(kd)
+                t = srv.submit(kd, ko)
+                with lock:
+                    results[t] = (keys, ko, kd)
+
+        threads = [threading.Thread(target=worker, args=(w,)) for w in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        for t, (keys, ko, _) in results.items():
+            assert srv.wait(t, 60_000) == 0
+            assert_same(from_dev(ko, np.uint32), np.sort(keys), f"thread ticket {t}")
+
+
+def test_request_that_can_never_fit_is_refused(rs):
+    import torch
+
+    with rs.Server(pool_bytes=64 << 20, num_streams=2, max_batch=4) as srv:
+        kd = torch.zeros(20_000_000, dtype=torch.int32, device="cuda")
+        ko = torch.empty_like(kd)
+        with pytest.raises(rs.SortError) as e:
+            srv.submit(kd, ko)
+        assert e.value.code == 4  # RS_ERR_BUDGET
+        assert srv.stats().rejected == 1
+
+
+def test_shutdown_cancels_queued_requests(rs):
+    """With one stream and a budget that admits one request at a time, a
+    cancelling shutdown returns without sorting the queue."""
+    import time
+
+    import torch
+
+    keys = to_dev(synth.u32(8_000_000, 90, 0))
+    outs = [torch.empty_like(keys) for _ in range(40)]
+    torch.cuda.synchronize()
+    srv = rs.Server(pool_bytes=512 << 20, budget_bytes=200 << 20, num_streams=1, max_batch=1)
+    for ko in outs:
+        srv.submit(keys, ko)
+    st = srv.stats()
+    assert st.submitted == 40 and st.queued >= 30
+    t0 = time.perf_counter()
+    assert rs.rs_server_destroy(srv.handle, True) == 0
+    elapsed = time.perf_counter() - t0
+    srv.handle = None
+    torch.cuda.synchronize()
+    # 40 sorts of 8M keys one after another take far longer than this
+    assert elapsed < 0.5, elapsed
