@@ -213,6 +213,50 @@ RS_API rs_status rs_sort_segmented_u64(const uint64_t* keys_in, uint64_t* keys_o
                                        size_t n_total, int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Plans: one sort call with fixed buffers and sizes, captured once into a
+ * CUDA graph and replayed by rs_plan_launch with a single host launch (the
+ * segmented sort of many arrays then costs one launch per call).  The
+ * planned call is rs_sort_* (RS_PLAN_RADIX), bs_sort_* (RS_PLAN_BUCKET) or
+ * rs_sort_segmented_* (RS_PLAN_SEGMENTED, n = n_total) with the arguments in
+ * the descriptor; argument errors are returned by rs_plan_create.
+ * autotune (radix only): every compiled kernel shape whose workspace fits
+ * ws_bytes is timed on the plan's buffers and the fastest is kept (all
+ * shapes give identical bits); results are cached per GPU, key width,
+ * values, key_bits and floor(log2 n) for the life of the process.
+ * rs_plan_create runs the planned sort at least once (more when tuning) on
+ * the plan's buffers and waits for it.  The buffers must stay valid for the
+ * life of the plan; a plan must not be launched concurrently with itself.
+ */
+#define RS_PLAN_RADIX 0
+#define RS_PLAN_BUCKET 1
+#define RS_PLAN_SEGMENTED 2
+typedef struct rs_plan rs_plan;
+typedef struct rs_plan_desc {
+    int algo;
+    int key_bytes;
+    const void* keys_in;
+    void* keys_out;
+    const uint32_t* vals_in;
+    uint32_t* vals_out;
+    size_t n;
+    int key_bits;
+    uint64_t min_key, max_key; /* bucket */
+    size_t num_buckets;        /* bucket */
+    const uint64_t* d_seg_offsets; /* segmented */
+    size_t nseg;                   /* segmented */
+    void* ws;
+    size_t ws_bytes;
+    int autotune;
+} rs_plan_desc;
+RS_API rs_status rs_plan_create(const rs_plan_desc* desc, rs_plan** out);
+RS_API rs_status rs_plan_launch(rs_plan* plan, rs_stream_t stream);
+/* The kernel shape in use (radix plans; zeros otherwise), the number of
+ * kernel nodes in the graph, and the tuned time per sort in ms (-1 if not
+ * tuned in this call). */
+RS_API rs_status rs_plan_info(const rs_plan* plan, rs_config* cfg, size_t* kernel_nodes, float* tuned_ms);
+RS_API void rs_plan_destroy(rs_plan* plan);
+
+/* ---------------------------------------------------------------------------
  * Sort server (continuous batching).  Requests arrive at any time from any
  * host thread; a dispatcher thread admits them, oldest first, while the
  * memory they need fits under budget_bytes, and keeps up to num_streams

@@ -14,7 +14,8 @@ bits are sorted as unsigned).  Values are 32-bit (uint32 or int32).
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (RsRequest, RsResult, RsServerConfig, RsServerStats, rs_server_create, rs_server_destroy,
+from ._lib import (RS_PLAN_BUCKET, RS_PLAN_RADIX, RS_PLAN_SEGMENTED, RsPlanDesc, rs_plan_create, rs_plan_destroy,
+                   rs_plan_info, rs_plan_launch, RsRequest, RsResult, RsServerConfig, RsServerStats, rs_server_create, rs_server_destroy,
                    rs_server_get_stats, rs_server_poll, rs_server_submit, rs_server_wait, bs_sort_u32, bs_sort_u64, rs_segmented_workspace_bytes, rs_sort_segmented_u32, rs_sort_segmented_u64,
                    RS_ALGO_BUCKET, RS_ALGO_RADIX, STATUS, RsConfig, load, rs_config_count, rs_config_get,
                    rs_counting_pass_u32, rs_counting_pass_u64, rs_default_config, rs_digit_counts_u32,
@@ -30,7 +31,8 @@ __all__ = [
     "rs_config_count", "rs_config_get", "RsConfig", "RS_ALGO_RADIX", "RS_ALGO_BUCKET", "STATUS",
     "rs_profile_enable", "rs_profile_read", "rs_launch_count", "rs_sort_u32_noalloc",
     "rs_segmented_workspace_bytes", "rs_sort_segmented_u32", "rs_sort_segmented_u64", "segmented_sort",
-    "bs_sort_u32", "bs_sort_u64", "bucket_sort", "Server", "RsRequest", "RsResult", "RsServerConfig",
+    "bs_sort_u32", "bs_sort_u64", "bucket_sort", "Server", "Plan", "RsPlanDesc", "rs_plan_create",
+    "rs_plan_destroy", "rs_plan_info", "rs_plan_launch", "RS_PLAN_RADIX", "RS_PLAN_BUCKET", "RS_PLAN_SEGMENTED", "RsRequest", "RsResult", "RsServerConfig",
     "RsServerStats", "rs_server_create", "rs_server_destroy", "rs_server_get_stats", "rs_server_poll",
     "rs_server_submit", "rs_server_wait",
 ]
@@ -231,3 +233,56 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Plan:
+    """A sort captured into a CUDA graph (rs_plan_*).  algo: RS_PLAN_RADIX,
+    RS_PLAN_BUCKET or RS_PLAN_SEGMENTED.  The tensors are kept referenced for
+    the life of the plan; the constructor runs the sort (several times when
+    autotuning) and waits for it."""
+
+    def __init__(self, algo, keys_in, keys_out, vals_in=None, vals_out=None, key_bits: int = 0, min_key: int = 1,
+                 max_key: int = 0, num_buckets: int = 0, seg_offsets=None, autotune: bool = False, ws=None):
+        kb = key_bytes_of(keys_in)
+        n = keys_in.numel()
+        has_v = vals_in is not None
+        nseg = seg_offsets.numel() - 1 if seg_offsets is not None else 0
+        if ws is None:
+            in_place = keys_out.data_ptr() == keys_in.data_ptr()
+            if algo == RS_PLAN_SEGMENTED:
+                nbytes = rs_segmented_workspace_bytes(kb, has_v, n, max(nseg, 1), key_bits)
+            elif algo == RS_PLAN_BUCKET:
+                nbytes = rs_workspace_bytes(RS_ALGO_BUCKET, kb, has_v, n, 0, num_buckets, in_place)
+            else:
+                nbytes = rs_workspace_bytes(RS_ALGO_RADIX, kb, has_v, n, key_bits, 0, in_place)
+                if autotune:  # room for the shapes with wider digits too
+                    for i in range(rs_config_count(kb, has_v)):
+                        nbytes = max(nbytes, rs_workspace_bytes_cfg(kb, has_v, n, key_bits, rs_config_get(kb, has_v, i)))
+            ws = workspace(nbytes, keys_in.device)
+        self._keep = (keys_in, keys_out, vals_in, vals_out, seg_offsets, ws)
+        desc = RsPlanDesc(algo, kb, keys_in.data_ptr(), keys_out.data_ptr(),
+                          vals_in.data_ptr() if has_v else None, vals_out.data_ptr() if has_v else None, n, key_bits,
+                          min_key, max_key, num_buckets, seg_offsets.data_ptr() if seg_offsets is not None else None,
+                          nseg, ws.data_ptr(), ws.numel(), int(bool(autotune)))
+        rc, self.handle = rs_plan_create(desc)
+        check(rc, "rs_plan_create")
+        self.ws = ws
+
+    def launch(self, stream=None) -> None:
+        check(rs_plan_launch(self.handle, stream), "rs_plan_launch")
+
+    def info(self):
+        rc, cfg, nodes, ms = rs_plan_info(self.handle)
+        check(rc, "rs_plan_info")
+        return cfg.as_tuple(), nodes, ms
+
+    def close(self) -> None:
+        if self.handle:
+            rs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -58,6 +58,14 @@ class RsServerStats(_c.Structure):
                 ("budget_bytes", _c.c_size_t), ("batches", _c.c_uint64), ("batched_requests", _c.c_uint64)]
 
 
+class RsPlanDesc(_c.Structure):
+    _fields_ = [("algo", _c.c_int), ("key_bytes", _c.c_int), ("keys_in", _c.c_void_p), ("keys_out", _c.c_void_p),
+                ("vals_in", _c.c_void_p), ("vals_out", _c.c_void_p), ("n", _c.c_size_t), ("key_bits", _c.c_int),
+                ("min_key", _c.c_uint64), ("max_key", _c.c_uint64), ("num_buckets", _c.c_size_t),
+                ("d_seg_offsets", _c.c_void_p), ("nseg", _c.c_size_t), ("ws", _c.c_void_p),
+                ("ws_bytes", _c.c_size_t), ("autotune", _c.c_int)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES: dict[str, tuple] = {
     "rs_status_string": (_c.c_char_p, [_I]),
@@ -80,6 +88,10 @@ SIGNATURES: dict[str, tuple] = {
     "rs_segmented_workspace_bytes": (_SZ, [_I, _I, _SZ, _SZ, _I]),
     "rs_sort_segmented_u32": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P]),
     "rs_sort_segmented_u64": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P]),
+    "rs_plan_create": (_I, [_c.POINTER(RsPlanDesc), _c.POINTER(_c.c_void_p)]),
+    "rs_plan_launch": (_I, [_P, _P]),
+    "rs_plan_info": (_I, [_P, _c.POINTER(RsConfig), _c.POINTER(_c.c_size_t), _c.POINTER(_c.c_float)]),
+    "rs_plan_destroy": (None, [_P]),
     "rs_server_create": (_I, [_c.POINTER(RsServerConfig), _c.POINTER(_c.c_void_p)]),
     "rs_server_submit": (_I, [_P, _c.POINTER(RsRequest), _c.POINTER(_c.c_uint64)]),
     "rs_server_poll": (_I, [_P, _c.c_uint64, _c.POINTER(RsResult)]),
@@ -261,6 +273,33 @@ def rs_sort_segmented_u64(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, n
                           stream=None) -> int:
     return _call("rs_sort_segmented_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out),
                  ptr(d_seg_offsets), nseg, n_total, key_bits, ptr(ws), ws_bytes, stream_handle(stream))
+
+
+RS_PLAN_RADIX, RS_PLAN_BUCKET, RS_PLAN_SEGMENTED = 0, 1, 2
+
+
+def rs_plan_create(desc: RsPlanDesc):
+    """Returns (status, plan handle)."""
+    h = _c.c_void_p()
+    rc = _call("rs_plan_create", _c.byref(desc), _c.byref(h))
+    return rc, h.value
+
+
+def rs_plan_launch(plan, stream=None) -> int:
+    return _call("rs_plan_launch", plan, stream_handle(stream))
+
+
+def rs_plan_info(plan):
+    """Returns (status, RsConfig, kernel nodes, tuned ms)."""
+    cfg = RsConfig()
+    nodes = _c.c_size_t()
+    ms = _c.c_float()
+    rc = _call("rs_plan_info", plan, _c.byref(cfg), _c.byref(nodes), _c.byref(ms))
+    return rc, cfg, nodes.value, ms.value
+
+
+def rs_plan_destroy(plan) -> None:
+    _call("rs_plan_destroy", plan)
 
 
 def rs_server_create(cfg: RsServerConfig):

@@ -51,6 +51,8 @@ cudaEvent_t take_event() {
 KernelScope::KernelScope(const char* name, cudaStream_t stream) : slot_(-1), stream_(stream) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_profile.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     cudaEvent_t a = take_event(), b = take_event();
     if (!a || !b) return;

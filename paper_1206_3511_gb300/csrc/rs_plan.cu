@@ -1,0 +1,215 @@
+// rs_plan.cu -- plans: one sort call with fixed buffers and sizes, captured
+// once into a CUDA graph and replayed with one host launch.  For radix sorts
+// the plan can first autotune the kernel shape (digit width, threads per
+// block, keys per thread) by timing every compiled shape that fits the
+// workspace; every shape gives bit-identical output, so tuning changes only
+// the speed.  Tuning results are cached per (GPU, key width, values, key
+// bits, log2 n).
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "rs_segmented.h"
+
+namespace rs {
+
+rs_status radix_sort_impl(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                          uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
+                          cudaStream_t stream, const rs_config* cfg);
+
+namespace {
+
+rs_status enqueue_plan(const rs_plan_desc& d, const rs_config* cfg, cudaStream_t s) {
+    switch (d.algo) {
+        case RS_PLAN_RADIX:
+            return radix_sort_impl(d.key_bytes, d.keys_in, d.keys_out, d.vals_in, d.vals_out, d.n, d.key_bits, d.ws,
+                                   d.ws_bytes, s, cfg);
+        case RS_PLAN_BUCKET:
+            return d.key_bytes == 4
+                       ? bs_sort_u32(static_cast<const uint32_t*>(d.keys_in), static_cast<uint32_t*>(d.keys_out),
+                                     d.vals_in, d.vals_out, d.n, (uint32_t)d.min_key, (uint32_t)d.max_key,
+                                     d.num_buckets, d.ws, d.ws_bytes, s)
+                       : bs_sort_u64(static_cast<const uint64_t*>(d.keys_in), static_cast<uint64_t*>(d.keys_out),
+                                     d.vals_in, d.vals_out, d.n, d.min_key, d.max_key, d.num_buckets, d.ws,
+                                     d.ws_bytes, s);
+        case RS_PLAN_SEGMENTED:
+            return d.key_bytes == 4
+                       ? rs_sort_segmented_u32(static_cast<const uint32_t*>(d.keys_in),
+                                               static_cast<uint32_t*>(d.keys_out), d.vals_in, d.vals_out,
+                                               d.d_seg_offsets, d.nseg, d.n, d.key_bits, d.ws, d.ws_bytes, s)
+                       : rs_sort_segmented_u64(static_cast<const uint64_t*>(d.keys_in),
+                                               static_cast<uint64_t*>(d.keys_out), d.vals_in, d.vals_out,
+                                               d.d_seg_offsets, d.nseg, d.n, d.key_bits, d.ws, d.ws_bytes, s);
+    }
+    return RS_ERR_INVALID_ARG;
+}
+
+using TuneKey = std::tuple<std::string, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, rs_config> g_tune_cache;
+
+TuneKey tune_key(const rs_plan_desc& d) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    const int kbits = d.key_bits ? d.key_bits : 8 * d.key_bytes;
+    return TuneKey(std::string(prop.name), d.key_bytes, d.vals_in != nullptr, kbits,
+                   d.n ? (int)std::floor(std::log2((double)d.n)) : 0);
+}
+
+// Time one shape: mean of `reps` runs after one warm-up run.
+float time_config(const rs_plan_desc& d, const rs_config& cfg, cudaStream_t s, cudaEvent_t a, cudaEvent_t b,
+                  int reps) {
+    if (enqueue_plan(d, &cfg, s) != RS_OK) return -1.f;
+    cudaEventRecord(a, s);
+    for (int r = 0; r < reps; ++r)
+        if (enqueue_plan(d, &cfg, s) != RS_OK) return -1.f;
+    cudaEventRecord(b, s);
+    if (cudaEventSynchronize(b) != cudaSuccess) return -1.f;
+    if (rs_get_status(d.ws, s) != RS_OK) return -1.f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms / reps;
+}
+
+rs_status autotune(const rs_plan_desc& d, cudaStream_t s, rs_config* best, float* best_ms) {
+    const TuneKey key = tune_key(d);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *best = it->second;
+            *best_ms = -1.f;
+            return RS_OK;
+        }
+    }
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return RS_ERR_CUDA;
+    const int kbits = d.key_bits ? d.key_bits : 8 * d.key_bytes;
+    const int count = rs_config_count(d.key_bytes, d.vals_in != nullptr);
+    float found = -1.f;
+    for (int i = 0; i < count; ++i) {
+        rs_config c{};
+        if (rs_config_get(d.key_bytes, d.vals_in != nullptr, i, &c) != RS_OK) continue;
+        const size_t need = rs_workspace_bytes_cfg(d.key_bytes, d.vals_in != nullptr, d.n, kbits, &c);
+        if (need == 0 || need > d.ws_bytes) continue;
+        const float ms = time_config(d, c, s, a, b, 3);
+        if (ms > 0.f && (found < 0.f || ms < found)) {
+            found = ms;
+            *best = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (found < 0.f) return rs_default_config(d.key_bytes, d.vals_in != nullptr, d.n, best);
+    *best_ms = found;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = *best;
+    return RS_OK;
+}
+
+}  // namespace
+
+}  // namespace rs
+
+using namespace rs;
+
+struct rs_plan {
+    rs_plan_desc desc;
+    rs_config cfg;
+    bool has_cfg;
+    float tuned_ms;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    size_t kernel_nodes;
+};
+
+extern "C" {
+
+rs_status rs_plan_create(const rs_plan_desc* desc, rs_plan** out) {
+    if (!desc || !out) return RS_ERR_INVALID_ARG;
+    const rs_plan_desc& d = *desc;
+    if (d.algo != RS_PLAN_RADIX && d.algo != RS_PLAN_BUCKET && d.algo != RS_PLAN_SEGMENTED) return RS_ERR_INVALID_ARG;
+    if (d.key_bytes != 4 && d.key_bytes != 8) return RS_ERR_INVALID_ARG;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return RS_ERR_CUDA;
+    rs_plan* p = new rs_plan();
+    p->desc = d;
+    p->has_cfg = false;
+    p->tuned_ms = -1.f;
+    rs_status st = RS_OK;
+    if (d.algo == RS_PLAN_RADIX) {
+        if (d.autotune)
+            st = autotune(d, s, &p->cfg, &p->tuned_ms);
+        else
+            st = rs_default_config(d.key_bytes, d.vals_in != nullptr, d.n, &p->cfg);
+        p->has_cfg = st == RS_OK;
+    }
+    if (st == RS_OK) {
+        // a dry enqueue outside capture checks the arguments and sets kernel attributes
+        st = enqueue_plan(d, p->has_cfg ? &p->cfg : nullptr, s);
+        if (st == RS_OK && cudaStreamSynchronize(s) != cudaSuccess) st = RS_ERR_CUDA;
+    }
+    if (st == RS_OK) {
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            st = RS_ERR_CUDA;
+        } else {
+            st = enqueue_plan(d, p->has_cfg ? &p->cfg : nullptr, s);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (st == RS_OK && e != cudaSuccess) st = RS_ERR_CUDA;
+            p->graph = g;
+            if (st == RS_OK && cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) st = RS_ERR_CUDA;
+        }
+    }
+    if (st == RS_OK) {
+        size_t nn = 0;
+        cudaGraphGetNodes(p->graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(p->graph, nodes.data(), &nn);
+        for (cudaGraphNode_t node : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(node, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++p->kernel_nodes;
+        }
+    }
+    cudaStreamDestroy(s);
+    if (st != RS_OK) {
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return RS_OK;
+}
+
+rs_status rs_plan_launch(rs_plan* plan, rs_stream_t stream) {
+    if (!plan || !plan->exec) return RS_ERR_INVALID_ARG;
+    return cudaGraphLaunch(plan->exec, stream) == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
+rs_status rs_plan_info(const rs_plan* plan, rs_config* cfg, size_t* kernel_nodes, float* tuned_ms) {
+    if (!plan) return RS_ERR_INVALID_ARG;
+    if (cfg) {
+        if (plan->has_cfg)
+            *cfg = plan->cfg;
+        else
+            *cfg = rs_config{0, 0, 0};
+    }
+    if (kernel_nodes) *kernel_nodes = plan->kernel_nodes;
+    if (tuned_ms) *tuned_ms = plan->tuned_ms;
+    return RS_OK;
+}
+
+void rs_plan_destroy(rs_plan* plan) {
+    if (!plan) return;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    delete plan;
+}
+
+}  // extern "C"
