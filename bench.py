@@ -56,6 +56,18 @@ WORKLOADS["bucket_u32_1m"] = ("bucket", 4, False, 1_000_000, 31, 10,
                               "bucket sort, 1M uint32 keys uniform [0,2^31), 62,500 buckets over [0,2^31-1]")
 WORKLOADS["radix_u32_1m"] = ("radix", 4, False, 1_000_000, 32, 10,
                              "LSD radix sort, 1M uint32 keys uniform [0,2^31), 8-bit digits, 4 passes")
+# n = number of arrays (batched) or requests per arrival rate (served)
+WORKLOADS["batched_u32_20k"] = ("batched", 4, False, 20_000, 32, 0,
+                                "segmented sort of 20,000 uint32 arrays, sizes log-uniform in [256, 2,000,000] "
+                                "(seed 0), uniform keys, one CUDA-graph launch; vs one rs_sort_u32 call per array")
+WORKLOADS["served_mix"] = ("served", 4, False, 1_000, 32, None,
+                           "sort server: Poisson arrivals at 1k-50k req/s, sizes log-uniform in [1e3, 5e7] keys, "
+                           "70% uint32 keys-only / 30% uint64 keys + uint32 values, distributions 0-6, 80 GB budget; "
+                           "vs a FIFO of one sort per request on one stream")
+BATCH_LO, BATCH_HI = 256, 2_000_000
+SERVED_LO, SERVED_HI = 1_000, 50_000_000
+SERVED_RATES = (1_000, 2_000, 5_000, 10_000, 20_000, 35_000, 50_000)
+SERVED_BUDGET = 80 * 10**9
 
 # kernels whose algorithmic bytes per launch are 2 n (w + v) (one read and one
 # write of every key) and n w (one read)
@@ -72,6 +84,9 @@ def parse_args():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="radix_u32_100m")
     ap.add_argument("--n", type=int, default=0, help="override the key count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rates", default="", help="served: comma-separated arrival rates per second")
+    ap.add_argument("--no-bucket-sweep", dest="bucket_sweep", action="store_false",
+                    help="served: skip the second sweep with half the requests bucket sorts")
     return ap.parse_args()
 
 
@@ -435,10 +450,538 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------------------ batched (segmented) workload
+def _roofline_from_stats(kstats, steps, step_bytes_of, hbm_peak, peak_src, traffic=None):
+    """Roofline of the kernel with the most device time: its algorithmic
+    bytes per step (step_bytes_of(name, launches per step)) over its time per
+    step."""
+    if not kstats:
+        return None
+    top = max(kstats, key=lambda k: kstats[k][1])
+    nl, tot = kstats[top]
+    per_step = nl / steps
+    step_bytes = step_bytes_of(top, per_step)
+    achieved = step_bytes / (tot / steps / 1e3) / 1e9
+    return {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": f"{peak_src} copy bandwidth",
+            "algorithmic_bytes_per_launch": step_bytes / per_step, "avg_launch_ms": tot / nl, "launches": nl}
+
+
+def _pct(xs, q):
+    import numpy as np
+
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def batched_inputs(count, rank, dev):
+    import numpy as np
+
+    import synth
+
+    sizes = synth.log_uniform_sizes(count, BATCH_LO, BATCH_HI, seed=0)
+    off = synth.segment_offsets(sizes)
+    n_total = int(off[-1])
+    keys = synth.u32_torch(n_total, seed=rank, dist_id=0, device=dev)
+    return sizes, off, keys
+
+
+def run_batched(args):
+    import numpy as np
+    import torch
+
+    import paper_1206_3511_gb300 as rs
+
+    world, rank, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    rs.load()
+    count = args.n or WORKLOADS["batched_u32_20k"][3]
+    sizes, off, d_keys = batched_inputs(count, rank, dev)
+    n_total = int(off[-1])
+    d_out = torch.empty_like(d_keys)
+    d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+    stream = torch.cuda.current_stream()
+    plan = rs.Plan(rs.RS_PLAN_SEGMENTED, d_keys, d_out, seg_offsets=d_off)
+    _, graph_kernels, _ = plan.info()
+
+    sampler = ClockSampler(dev)
+    sampler.start()
+    for _ in range(max(3, args.warmup)):
+        plan.launch(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.launch(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    status = rs.get_status(plan.ws)
+    if status:
+        raise rs.SortError(status, "device status after the timed steps")
+
+    # per-kernel times: graph replays record no events, so the same sort runs
+    # as eager calls with event profiling
+    prof_steps = 3
+    seg_ws = plan.ws
+    rs.rs_profile_enable(True)
+    launches0 = rs.rs_launch_count()
+    for _ in range(prof_steps):
+        rs.check(rs.rs_sort_segmented_u32(d_keys, d_out, None, None, d_off, count, n_total, 32, seg_ws,
+                                          seg_ws.numel(), stream), "segmented")
+    torch.cuda.synchronize()
+    launches_per_step = (rs.rs_launch_count() - launches0) / prof_steps
+    rs.rs_profile_enable(False)
+    kstats = rs.rs_profile_read()
+
+    # spot check: a few arrays against a host sort (the tests hold the oracle checks)
+    for i in (0, count // 2, count - 1):
+        a, b = int(off[i]), int(off[i + 1])
+        got = d_out[a:b].cpu().numpy().view(np.uint32)
+        want = np.sort(d_keys[a:b].cpu().numpy().view(np.uint32), kind="stable")
+        assert np.array_equal(got, want), f"batched output wrong in array {i}"
+
+    # one rs_sort_u32 call per array (the plain path), same stream, one workspace
+    big = int(sizes.max())
+    ws_plain = rs.workspace(rs.rs_workspace_bytes(rs.RS_ALGO_RADIX, 4, False, big, 32, 0, 0), d_keys.device)
+    kp, op = d_keys.data_ptr(), d_out.data_ptr()
+    offs = [int(x) for x in off]
+
+    def plain_step(events=None):
+        for i in range(count):
+            a, b = offs[i], offs[i + 1]
+            rc = rs.rs_sort_u32(kp + 4 * a, op + 4 * a, None, None, b - a, 32, ws_plain, ws_plain.numel(), stream)
+            if rc:
+                raise rs.SortError(rc, "plain sort")
+            if events is not None:
+                events[i].record(stream)
+
+    plain_step()
+    torch.cuda.synchronize()
+    plain_steps = max(1, min(args.steps, 3))
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(plain_steps):
+        plain_step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1) / plain_steps
+    # completion latency of every array when all are handed over at once:
+    # plain = the event after its own sort; batched = the end of the graph
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(count)]
+    s0 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    plain_step(evs)
+    torch.cuda.synchronize()
+    plain_lat = [s0.elapsed_time(e) for e in evs]
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    plan.launch(stream)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    batched_lat = g0.elapsed_time(g1)
+
+    # end to end: pinned host keys -> device -> graph -> host
+    h_keys = torch.empty(n_total, dtype=torch.int32, pin_memory=True)
+    h_keys.copy_(d_keys)
+    h_out = torch.empty_like(h_keys, pin_memory=True)
+    e2e_steps = max(3, min(args.steps, 5))
+    d_keys.copy_(h_keys, non_blocking=True)
+    plan.launch(stream)
+    h_out.copy_(d_out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        d_keys.copy_(h_keys, non_blocking=True)
+        plan.launch(stream)
+        h_out.copy_(d_out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+
+    if world > 1:
+        t = torch.tensor([ms, e2e_ms, plain_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e_ms, plain_ms = float(t[0]), float(t[1]), float(t[2])
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    value = world * n_total * args.steps / (ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+    n_large = int(sizes[sizes > 4096].sum())
+    n_small = n_total - n_large
+
+    def step_bytes_of(name, per_step):
+        if name == "onesweep_seg_pass":
+            return 2 * n_large * 4 * per_step
+        if name == "local_sort":
+            return 2 * n_small * 4
+        return n_large * 4 * per_step
+
+    roofline = _roofline_from_stats(kstats, prof_steps, step_bytes_of, hbm_peak, peak_src)
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = _batched_cpu_sample(sizes, off, d_keys)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["batched_u32_20k"][6], "arrays": count, "n_total": n_total,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (%d MB keys vs 129 MB L2), no flush" % (n_total * 4 // 2**20)},
+        "clocks": clocks, "gpu_launches": graph_kernels * args.steps, "graph_kernel_nodes": graph_kernels,
+        "eager_launches_per_step": launches_per_step,
+        "roofline": roofline,
+        "batched": {"ms_per_step": ms / args.steps, "p50_ms": batched_lat, "p99_ms": batched_lat,
+                    "host_launches_per_step": 1},
+        "plain": {"value": n_total / (plain_ms / 1e3) / 1e9, "unit": "Gkeys/s", "ms_per_step": plain_ms,
+                  "p50_ms": _pct(plain_lat, 50), "p99_ms": _pct(plain_lat, 99), "host_calls_per_step": count,
+                  "steps": plain_steps},
+        "latency_note": "completion time of each array after all arrays are handed over at once",
+        "kernels": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kstats.items()},
+        "e2e": {"value": n_total * e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": "Gkeys/s",
+                "h2d_bytes_per_step": n_total * 4, "d2h_bytes_per_step": n_total * 4},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _batched_cpu_sample(sizes, off, d_keys=None, budget_keys=150_000_000):
+    """The oracle's segmented sort of the first arrays of the batch, up to
+    about budget_keys keys: (Gkeys/s, ...)."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    oracle.build()
+    m = int(np.searchsorted(np.cumsum(sizes), budget_keys)) + 1
+    m = min(m, sizes.size)
+    sub = synth.segment_offsets(sizes[:m])
+    n = int(sub[-1])
+    if d_keys is not None:
+        keys = d_keys[:n].cpu().numpy().view(np.uint32)
+    else:
+        keys = synth.u32(n, 0, 0)
+    t0 = time.perf_counter()
+    oracle.segmented_radix_sort(keys, sub, None, 32)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle", "sample_keys": n,
+            "sample": f"oracle segmented sort of the first {m} arrays of the batch ({n} keys, {dt:.1f} s), "
+                      f"single thread of {os.cpu_count()} host cores"}
+
+
+# ------------------------------------------------------------------ served workload
+def served_bytes(n, kind):
+    """Algorithmic HBM bytes of one radix request: one read to count, then
+    per pass a read and a write of keys (and values)."""
+    if kind == 0:
+        return n * 4 + 4 * 2 * n * 4
+    return n * 8 + 8 * 2 * n * 12
+
+
+def run_served(args):
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import paper_1206_3511_gb300 as rs
+    import synth
+    from paper_1206_3511_gb300 import _lib
+
+    world, rank, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    rs.load()
+    count = args.n or WORKLOADS["served_mix"][3]
+    rates = SERVED_RATES if not args.rates else tuple(int(r) for r in args.rates.split(","))
+    sizes, kinds, dists = synth.served_mix(count, SERVED_LO, SERVED_HI, seed=rank)
+    big = int(sizes.max())
+    # resident inputs: one array per (kind, distribution); request i reads a prefix
+    src_k, src_v = {}, None
+    for d in sorted(set(dists.tolist())):
+        if np.any((dists == d) & (kinds == 0)):
+            src_k[(0, d)] = torch.from_numpy(synth.keys_u32(big, d, seed=rank).view(np.int32)).to(dev)
+        if np.any((dists == d) & (kinds == 1)):
+            src_k[(1, d)] = torch.from_numpy(synth.keys_u64_shaped(big, d, seed=rank).view(np.int64)).to(dev)
+    if np.any(kinds == 1):
+        src_v = torch.arange(big, dtype=torch.int32, device=dev)
+    # output ring: request i writes slot i % M and waits for request i - M first
+    M = 48
+    ring_k = [torch.empty(big * 8, dtype=torch.uint8, device=dev) for _ in range(M)]
+    ring_v = [torch.empty(big * 4, dtype=torch.uint8, device=dev) for _ in range(M)]
+    def build_requests(bucket_share):
+        """One request per draw; a share of them (drawn) use the bucket sort
+        with the distribution's declared bounds and n/16 buckets."""
+        use_bucket = synth.unit_doubles(count, rank, 45) < bucket_share
+        reqs, nbytes = [], 0
+        for i in range(count):
+            n, kd, d = int(sizes[i]), int(kinds[i]), int(dists[i])
+            slot = i % M
+            lo, hi = synth.DECLARED_BOUNDS[d]
+            kb = 4 if kd == 0 else 8
+            if kd == 1:
+                lo, hi = lo << 32, (hi << 32) | 0xFFFFFFFF
+            kin, kout = src_k[(kd, d)].data_ptr(), ring_k[slot].data_ptr()
+            vin = src_v.data_ptr() if kd == 1 else None
+            vout = ring_v[slot].data_ptr() if kd == 1 else None
+            if use_bucket[i]:
+                reqs.append(_lib.RsRequest(rs.RS_ALGO_BUCKET, kb, kin, kout, vin, vout, n, 0, lo, hi, 0))
+                w = kb + (4 if kd == 1 else 0)
+                nbytes += n * kb + 4 * n * w
+            else:
+                reqs.append(_lib.RsRequest(rs.RS_ALGO_RADIX, kb, kin, kout, vin, vout, n, 8 * kb, 1, 0, 0))
+                nbytes += served_bytes(n, kd)
+        return reqs, nbytes, int(use_bucket.sum())
+
+    total_keys = int(sizes.sum())
+    reqs, total_bytes, _ = build_requests(0.0)
+
+    def run_mode(rate, num_streams, max_batch, seed):
+        srv = rs.Server(SERVED_BUDGET, SERVED_BUDGET, num_streams=num_streams, max_batch=max_batch, device=dev)
+        arr = synth.poisson_arrivals(count, rate, seed=seed) * 1e3  # ms
+        tickets = [0] * count
+        lag = []
+        t0 = time.monotonic() * 1e3 + 2.0
+        for i in range(count):
+            if i >= M:
+                srv.wait(tickets[i - M])
+            target = t0 + arr[i]
+            while time.monotonic() * 1e3 < target:
+                pass
+            lag.append(time.monotonic() * 1e3 - target)
+            rc, tickets[i] = _lib.rs_server_submit(srv.handle, reqs[i])
+            if rc:
+                raise rs.SortError(rc, "submit")
+        lat, done = [], []
+        for i in range(count):
+            rc = srv.wait(tickets[i])
+            if rc:
+                raise rs.SortError(rc, f"request {i}")
+            _, r = srv.result(tickets[i])
+            done.append(r.t_done_ms)
+            lat.append(r.t_done_ms - (t0 + arr[i]))
+        st = srv.stats()
+        srv.close()
+        span_ms = max(done) - t0
+        return {"p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "max_ms": max(lat),
+                "gkeys_s": total_keys / (span_ms / 1e3) / 1e9, "span_ms": span_ms,
+                "offered_gkeys_s": total_keys / (arr[-1] / 1e3) / 1e9,
+                "submit_lag_p99_ms": _pct(lag, 99), "submitted": int(st.submitted),
+                "admitted": int(st.submitted - st.rejected), "rejected": int(st.rejected),
+                "completed": int(st.completed), "batches": int(st.batches),
+                "batched_requests": int(st.batched_requests), "max_in_use_gb": st.max_in_use_bytes / 1e9}
+
+    def knee(rows, mode):
+        """The highest rate whose p99 stays within 4x the p99 at the lowest rate."""
+        base = rows[0][mode]["p99_ms"]
+        ok = [r["rate_per_s"] for r in rows if r[mode]["p99_ms"] <= 4 * base]
+        return max(ok) if ok else None
+
+    # warm-up: every request once through the server
+    for _ in range(max(1, min(args.warmup, 2))):
+        run_mode(1e6, 4, 64, seed=99)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    launches0 = rs.rs_launch_count()
+    sweep = []
+    for j, rate in enumerate(rates):
+        srv_res = run_mode(rate, 4, 64, seed=j)
+        fifo_res = run_mode(rate, 1, 1, seed=j)
+        sweep.append({"rate_per_s": rate, "server": srv_res, "fifo": fifo_res})
+    radix_reqs, radix_bytes = reqs, total_bytes
+    sweep_bucket = []
+    if args.bucket_sweep:
+        reqs, bucket_bytes, n_bucket = build_requests(0.5)
+        for j, rate in enumerate(rates):
+            sweep_bucket.append({"rate_per_s": rate, "server": run_mode(rate, 4, 64, seed=j),
+                                 "fifo": run_mode(rate, 1, 1, seed=j)})
+        reqs = radix_reqs
+    launches = rs.rs_launch_count() - launches0
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+
+    # spot check: the last small requests of the last run, against a host sort
+    checked = 0
+    for i in range(count - 1, max(-1, count - M - 1), -1):
+        n, kd, d = int(sizes[i]), int(kinds[i]), int(dists[i])
+        if n > 2_000_000:
+            continue
+        if kd == 0:
+            inp = src_k[(0, d)][:n].cpu().numpy().view(np.uint32)
+            got = ring_k[i % M][: 4 * n].cpu().numpy().view(np.uint32)
+            assert np.array_equal(got, np.sort(inp, kind="stable")), f"served request {i} wrong"
+        else:
+            inp = src_k[(1, d)][:n].cpu().numpy().view(np.uint64)
+            order = np.argsort(inp, kind="stable")
+            got_k = ring_k[i % M][: 8 * n].cpu().numpy().view(np.uint64)
+            got_v = ring_v[i % M][: 4 * n].cpu().numpy().view(np.uint32)
+            assert np.array_equal(got_k, inp[order]) and np.array_equal(got_v, order.astype(np.uint32)), \
+                f"served request {i} wrong"
+        checked += 1
+        if checked == 4:
+            break
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    peak_src = "measured" if peaks.get("hbm_gbs") else "fallback"
+    top = sweep[-1]["server"]
+    achieved = radix_bytes / (top["span_ms"] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": top["gkeys_s"], "unit": "Gkeys/s", "n_gpus": world,
+        "steps": len(rates), "warmup": args.warmup, "ms_per_step": top["span_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32+u64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["served_mix"][6], "requests_per_rate": count, "keys_per_run": total_keys,
+                   "rates_per_s": list(rates), "budget_bytes": SERVED_BUDGET,
+                   "server": "4 streams, batches of up to 64 requests of <= 262,144 keys",
+                   "fifo": "same server with 1 stream and no batching",
+                   "l2": "inputs resident in HBM (%.1f GB per run) larger than L2, no flush" % (total_bytes / 1e9)},
+        "value_note": "server throughput at the highest arrival rate (keys / (last completion - first arrival))",
+        "clocks": clocks, "gpu_launches": launches,
+        "roofline": {"kernel": "all kernels of the served mix", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                     "peak_source": f"{peak_src} copy bandwidth",
+                     "algorithmic_bytes_per_run": radix_bytes},
+        "sweep": sweep, "knee_per_s": {"server": knee(sweep, "server"), "fifo": knee(sweep, "fifo")},
+        "sweep_half_bucket": sweep_bucket,
+        "knee_half_bucket_per_s": ({"server": knee(sweep_bucket, "server"), "fifo": knee(sweep_bucket, "fifo")}
+                                   if sweep_bucket else None),
+        "e2e": {"value": top["gkeys_s"], "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "host-submitted requests, completion seen on the host; keys resident on the device"},
+        "cpu_baseline": None if args.no_cpu_baseline else _served_cpu_sample(sizes, kinds, dists),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _served_cpu_sample(sizes, kinds, dists, budget_keys=100_000_000):
+    """The oracle's radix sorts of the first requests of the mix, one after
+    another, up to about budget_keys keys."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    oracle.build()
+    done, t = 0, 0.0
+    for i in range(sizes.size):
+        n, kd, d = int(sizes[i]), int(kinds[i]), int(dists[i])
+        if done and done + n > budget_keys:
+            continue
+        if kd == 0:
+            keys, vals, kb = synth.keys_u32(n, d, seed=0), None, 32
+        else:
+            keys, vals, kb = synth.keys_u64_shaped(n, d, seed=0), synth.index_values(n), 64
+        t0 = time.perf_counter()
+        oracle.radix_sort(keys, vals, kb, 8)
+        t += time.perf_counter() - t0
+        done += n
+        if done >= budget_keys:
+            break
+    return {"value": done / t / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle", "sample_keys": done,
+            "sample": f"oracle radix sorts of {done} keys of the request mix, one after another ({t:.1f} s), "
+                      f"single thread of {os.cpu_count()} host cores"}
+
+
+def run_reference_batched(args):
+    _, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    import synth
+
+    count = args.n or WORKLOADS["batched_u32_20k"][3]
+    sizes = synth.log_uniform_sizes(count, BATCH_LO, BATCH_HI, seed=0)
+    total_steps = max(1, args.warmup + args.steps)
+    budget = max(5_000_000, 60 * 50_000_000 // total_steps)
+    rates = []
+    cpu = None
+    for i in range(total_steps):
+        cpu = _batched_cpu_sample(sizes, None, None, budget)
+        if i >= args.warmup:
+            rates.append(cpu["value"])
+    value = statistics.median(rates)
+    cpu["value"] = value
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": cpu["sample_keys"] / value / 1e6,
+        "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["batched_u32_20k"][6], "arrays": count, "parallelism": "none (1 CPU thread)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_reference_served(args):
+    _, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    import synth
+
+    count = args.n or WORKLOADS["served_mix"][3]
+    sizes, kinds, dists = synth.served_mix(count, SERVED_LO, SERVED_HI, seed=0)
+    total_steps = max(1, args.warmup + args.steps)
+    budget = max(5_000_000, 60 * 40_000_000 // total_steps)
+    rates, cpu = [], None
+    for i in range(total_steps):
+        cpu = _served_cpu_sample(sizes, kinds, dists, budget)
+        if i >= args.warmup:
+            rates.append(cpu["value"])
+    value = statistics.median(rates)
+    cpu["value"] = value
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": cpu["sample_keys"] / value / 1e6,
+        "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32+u64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["served_mix"][6], "parallelism": "none (1 CPU thread)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def main():
     args = parse_args()
+    kind = WORKLOADS[args.workload][0]
     if args.impl == "reference":
-        run_reference(args)
+        if kind == "batched":
+            run_reference_batched(args)
+        elif kind == "served":
+            run_reference_served(args)
+        else:
+            run_reference(args)
+    elif kind == "batched":
+        run_batched(args)
+    elif kind == "served":
+        run_served(args)
     else:
         run_ours(args)
 

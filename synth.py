@@ -71,6 +71,53 @@ def u64(n: int, seed: int, dist_id: int = 0, stream: int = 0, start: int = 0) ->
     return out
 
 
+def _signed(v: int) -> int:
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def u64_torch_range(a: int, b: int, seed: int, dist_id: int = 0, stream: int = 0, device="cpu"):
+    """Draws a .. b-1 of u64() (counters a+1 .. b) as an int64 torch tensor
+    on `device`, same bits: for inputs too large to build on the host.
+    int64 multiplication wraps modulo 2^64 like uint64; right shifts are
+    made logical by masking."""
+    import torch
+
+    base = _signed(int(stream_base(seed, dist_id, stream)))
+    g, m1, m2 = _signed(int(GAMMA)), _signed(int(_M1)), _signed(int(_M2))
+
+    def srl(z, k):
+        return (z >> k) & ((1 << (64 - k)) - 1)
+
+    z = torch.arange(a + 1, b + 1, dtype=torch.int64, device=device)
+    z.mul_(g).add_(base)
+    z = (z ^ srl(z, 30)) * m1
+    z = (z ^ srl(z, 27)) * m2
+    return z ^ srl(z, 31)
+
+
+def u64_torch(n: int, seed: int, dist_id: int = 0, stream: int = 0, device="cpu", chunk: int = 1 << 27):
+    """u64() as an int64 torch tensor on `device` (same bits)."""
+    import torch
+
+    out = torch.empty(n, dtype=torch.int64, device=device)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        out[a:b] = u64_torch_range(a, b, seed, dist_id, stream, device)
+    return out
+
+
+def u32_torch(n: int, seed: int, dist_id: int = 0, stream: int = 0, device="cpu", chunk: int = 1 << 27):
+    """u32() as an int32 torch tensor on `device` (same bits): the high
+    halves, taken with an arithmetic shift so that the int32 cast is exact."""
+    import torch
+
+    out = torch.empty(n, dtype=torch.int32, device=device)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        out[a:b] = (u64_torch_range(a, b, seed, dist_id, stream, device) >> 32).to(torch.int32)
+    return out
+
+
 def u32(n: int, seed: int, dist_id: int = 0, stream: int = 0) -> np.ndarray:
     """n 32-bit draws: the high halves of the 64-bit draws."""
     return (u64(n, seed, dist_id, stream) >> np.uint64(32)).astype(np.uint32)
@@ -185,6 +232,35 @@ def log_uniform_sizes(count: int, lo: int, hi: int, seed: int = 0, dist_id: int 
     u = (d >> np.uint64(11)).astype(np.float64) * (1.0 / 2**53)
     s = np.floor(np.exp(math.log(lo) + u * (math.log(hi) - math.log(lo)))).astype(np.int64)
     return np.clip(s, lo, hi)
+
+
+def unit_doubles(n: int, seed: int, dist_id: int, stream: int = 0) -> np.ndarray:
+    """n doubles uniform in [0, 1) from the top 53 bits of the draws."""
+    return (u64(n, seed, dist_id, stream) >> np.uint64(11)).astype(np.float64) * (1.0 / 2**53)
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = 0, dist_id: int = 40) -> np.ndarray:
+    """Arrival times in seconds of a Poisson process of `rate` per second:
+    cumulative sums of exponential gaps -ln(1 - u) / rate."""
+    u = unit_doubles(count, seed, dist_id)
+    return np.cumsum(-np.log1p(-u) / rate)
+
+
+def served_mix(count: int, lo: int, hi: int, seed: int = 0):
+    """Request mix of the served workload: (sizes log-uniform in [lo, hi],
+    kind 0 = uint32 keys only (70%) or 1 = uint64 keys + uint32 values (30%),
+    distribution id 0-6)."""
+    sizes = log_uniform_sizes(count, lo, hi, seed=seed, dist_id=41)
+    kind = (unit_doubles(count, seed, 42) >= 0.7).astype(np.int64)
+    dist = uniform_below(count, 7, seed, 43).astype(np.int64)
+    return sizes, kind, dist
+
+
+def keys_u64_shaped(n: int, dist: int, seed: int = 0) -> np.ndarray:
+    """uint64 keys with the shape of u32 distribution `dist` in their high
+    half and uniform low halves: (keys_u32(n, dist) << 32) | draws."""
+    hi = keys_u32(n, dist, seed).astype(np.uint64) << np.uint64(32)
+    return hi | u32(n, seed, 44, dist).astype(np.uint64)
 
 
 def segment_offsets(sizes) -> np.ndarray:

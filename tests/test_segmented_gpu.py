@@ -96,3 +96,55 @@ def test_bad_offsets_are_reported(rs):
     out = torch.empty_like(keys)
     assert rs.rs_sort_segmented_u32(keys, out, None, None, off, 3, 100, 32, ws, ws.numel()) == 0
     assert rs.get_status(ws) == 1  # RS_ERR_INVALID_ARG recorded on the device
+
+
+def _u32_as_i64(t):
+    return t.to(__import__("torch").int64) & 0xFFFFFFFF
+
+
+@pytest.mark.slow
+def test_full_batched_workload_sampled_against_oracle(rs, oracle):
+    """The batched workload at full size, in the launch configuration the
+    benchmark times (a segmented-sort plan replayed from a CUDA graph):
+    20,000 uint32 arrays with sizes log-uniform in [256, 2,000,000], about
+    4.5e9 keys, so offsets pass 2^32.  Sampled arrays (including the last,
+    past 2^32) are compared with the oracle; every array is checked on the
+    device to be nondecreasing with its key sum and sum of squares (mod
+    2^64) unchanged."""
+    import torch
+
+    sizes = synth.log_uniform_sizes(20_000, 256, 2_000_000, seed=0)
+    off = synth.segment_offsets(sizes)
+    n = int(off[-1])
+    assert n > 2**32
+    kd = synth.u32_torch(n, seed=0, dist_id=0, device="cuda")
+    od = torch.from_numpy(off.view(np.int64)).cuda()
+    out = torch.empty_like(kd)
+    plan = rs.Plan(rs.RS_PLAN_SEGMENTED, kd, out, seg_offsets=od)
+    out.zero_()
+    plan.launch()
+    torch.cuda.synchronize()
+    assert rs.get_status(plan.ws) == 0
+    for i in [0, 1, 777, 5000, 10_000, 15_000, 19_998, 19_999, int(np.argmax(sizes)), int(np.argmin(sizes))]:
+        a, b = int(off[i]), int(off[i + 1])
+        keys = kd[a:b].cpu().numpy().view(np.uint32)
+        assert_same(out[a:b].cpu().numpy().view(np.uint32), oracle.radix_sort(keys, None, 32), f"array {i}")
+    # properties of every array, in chunks of whole arrays
+    starts = torch.from_numpy(off[:-1].view(np.int64)).cuda()
+    i0 = 0
+    while i0 < sizes.size:
+        i1 = int(np.searchsorted(off, off[i0] + (1 << 28), side="right")) - 1
+        i1 = max(i1, i0 + 1)
+        a, b = int(off[i0]), int(off[i1])
+        x, y = _u32_as_i64(kd[a:b]), _u32_as_i64(out[a:b])
+        step_ok = y[1:] >= y[:-1]
+        step_ok[(starts[i0 + 1:i1] - a - 1)] = True  # array boundaries
+        assert bool(step_ok.all()), f"arrays {i0}..{i1} not sorted"
+        seg = torch.repeat_interleave(torch.arange(i1 - i0, device="cuda"),
+                                      torch.from_numpy(sizes[i0:i1]).cuda())
+        for f in (lambda v: v, lambda v: v * v):
+            sx = torch.zeros(i1 - i0, dtype=torch.int64, device="cuda").index_add_(0, seg, f(x))
+            sy = torch.zeros(i1 - i0, dtype=torch.int64, device="cuda").index_add_(0, seg, f(y))
+            assert torch.equal(sx, sy), f"arrays {i0}..{i1}: multiset changed"
+        i0 = i1
+    plan.close()
