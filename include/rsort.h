@@ -140,6 +140,27 @@ RS_API rs_status rs_sort_u64_ex(const uint64_t* keys_in, uint64_t* keys_out, con
                          uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
                          rs_stream_t stream, const rs_config* cfg);
 
+/* Typed keys: the radix sort of rs_sort_u32/u64 over another order.  The
+ * paper sorts non-negative `int` keys (Sec. 3.1); this call extends it to
+ * signed integers, IEEE-754 floats and descending order by sorting the keys'
+ * order-preserving unsigned images: a signed key flips its sign bit; a float
+ * flips its sign bit when non-negative and all bits when negative, so floats
+ * follow the standard's totalOrder (-NaN < -inf < ... < -0 < +0 < ... < +inf
+ * < +NaN, NaNs by payload); descending complements the image.  The images
+ * are formed as the keys are loaded and undone as they are stored: the output
+ * holds the original key bits.  Stable in every mode (equal keys keep input
+ * order, also when descending).
+ * key_kind: RS_KEY_UINT, RS_KEY_INT or RS_KEY_FLOAT; key_bytes 4 or 8;
+ * every bit is significant (no key_bits).  Workspace: rs_workspace_bytes(
+ * RS_ALGO_RADIX, key_bytes, has_values, n, 0, 0, in_place).  Layout, aliasing
+ * and errors as rs_sort_u32/u64. */
+#define RS_KEY_UINT 0
+#define RS_KEY_INT 1
+#define RS_KEY_FLOAT 2
+RS_API rs_status rs_sort_typed(int key_kind, int key_bytes, int descending, const void* keys_in, void* keys_out,
+                               const uint32_t* vals_in, uint32_t* vals_out, size_t n, void* ws, size_t ws_bytes,
+                               rs_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Bucket sort, Sec. 2.3 Algorithm 2: every key goes to bucket
  *     b(k) = floor((k - min_key) * num_buckets / (max_key - min_key + 1))

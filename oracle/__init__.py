@@ -56,6 +56,7 @@ def _load():
             lib.oracle_bucket_counts_u64.argtypes = [P64, sz, u64, u64, u64, P64]
             lib.oracle_bucket_sort_u64.argtypes = [P64, P32, sz, u64, u64, u64, P64, P32]
             lib.oracle_minmax_u64.argtypes = [P64, sz, P64, P64]
+            lib.oracle_sort_typed_u64.argtypes = [P64, P32, sz, i, i, i, P64, P32]
             _lib = lib
     return _lib
 
@@ -203,3 +204,29 @@ def segmented_radix_sort(keys, offsets, vals=None, key_bits: int | None = None, 
         else:
             out[a:b] = radix_sort(keys[a:b], None, key_bits, digit_bits)
     return (out, outv) if vals is not None else out
+
+
+KIND_UINT, KIND_INT, KIND_FLOAT = 0, 1, 2
+_KIND_OF = {np.dtype(np.uint32): 0, np.dtype(np.uint64): 0, np.dtype(np.int32): 1, np.dtype(np.int64): 1,
+            np.dtype(np.float32): 2, np.dtype(np.float64): 2}
+_BITS_OF = {4: np.uint32, 8: np.uint64}
+
+
+def sort_typed(keys, vals=None, kind: int | None = None, descending: bool = False):
+    """Stable sort of typed keys (unsigned, signed, IEEE float by totalOrder),
+    ascending or descending.  keys: a numpy array of a 4- or 8-byte dtype;
+    kind None takes it from the dtype.  Returns keys (same dtype) or
+    (keys, values)."""
+    keys = np.ascontiguousarray(keys)
+    if keys.dtype.itemsize not in (4, 8):
+        raise TypeError("keys must be 4 or 8 bytes wide")
+    if kind is None:
+        kind = _KIND_OF[keys.dtype]
+    bits = keys.view(_BITS_OF[keys.dtype.itemsize]).astype(np.uint64)
+    v = _vals(vals, bits.size)
+    out = np.empty(bits.size, np.uint64)
+    vout = np.empty(bits.size, np.uint32) if v is not None else None
+    _check(_load().oracle_sort_typed_u64(_p64(bits), _p32(v), bits.size, keys.dtype.itemsize, kind,
+                                         int(bool(descending)), _p64(out), _p32(vout)))
+    res = out.astype(_BITS_OF[keys.dtype.itemsize]).view(keys.dtype)
+    return res if v is None else (res, vout)

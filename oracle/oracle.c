@@ -299,3 +299,98 @@ int oracle_minmax_u64(const uint64_t* keys, size_t n, uint64_t* min_key, uint64_
     *max_key = hi;
     return ORACLE_OK;
 }
+
+/* ---------------------------------------------------------------------------
+ * Typed keys (beyond the paper, which sorts non-negative ints, Sec. 3.1).
+ * The order of each key kind is written out as a comparison of the keys'
+ * bits, width = 8 * key_bytes:
+ *   kind 0, unsigned: the order of the unsigned integers;
+ *   kind 1, signed (two's complement): a key with the sign bit set is below
+ *           every key without it; keys of one sign compare as unsigned bits;
+ *   kind 2, IEEE-754 binary float, totalOrder (IEEE 754-2008, 5.10): the bits
+ *           are sign and magnitude; every key with the sign bit set is below
+ *           every key without it; among non-negative keys the larger
+ *           magnitude is larger, among negative keys the larger magnitude is
+ *           smaller (so -0 < +0, and NaNs sit beyond the infinities, ordered
+ *           by payload);
+ *   descending: the reverse of that order.
+ * The sort is a stable merge sort: equal keys keep their input order in both
+ * directions.
+ */
+static int typed_less(uint64_t a, uint64_t b, int width, int kind)
+{
+    if (kind == 0)
+        return a < b;
+    const uint64_t sign = 1ull << (width - 1);
+    const int sa = (a & sign) != 0, sb = (b & sign) != 0;
+    if (sa != sb)
+        return sa;  /* the negative one is smaller */
+    if (kind == 1)
+        return a < b;
+    const uint64_t ma = a & ~sign, mb = b & ~sign;
+    return sa ? (ma > mb) : (ma < mb);
+}
+
+static int typed_before(uint64_t a, uint64_t b, int width, int kind, int descending)
+{
+    return descending ? typed_less(b, a, width, kind) : typed_less(a, b, width, kind);
+}
+
+/* Merge sort of the index range [lo, hi) of idx by the keys; tmp is scratch.
+ * The right element is taken only when it is strictly before the left one. */
+static void merge_sort_idx(const uint64_t* keys, size_t* idx, size_t* tmp, size_t lo, size_t hi, int width,
+                           int kind, int descending)
+{
+    if (hi - lo < 2)
+        return;
+    const size_t mid = lo + (hi - lo) / 2;
+    merge_sort_idx(keys, idx, tmp, lo, mid, width, kind, descending);
+    merge_sort_idx(keys, idx, tmp, mid, hi, width, kind, descending);
+    size_t i = lo, j = mid, o = lo;
+    while (i < mid && j < hi) {
+        if (typed_before(keys[idx[j]], keys[idx[i]], width, kind, descending))
+            tmp[o++] = idx[j++];
+        else
+            tmp[o++] = idx[i++];
+    }
+    while (i < mid)
+        tmp[o++] = idx[i++];
+    while (j < hi)
+        tmp[o++] = idx[j++];
+    memcpy(idx + lo, tmp + lo, (hi - lo) * sizeof(size_t));
+}
+
+int oracle_sort_typed_u64(const uint64_t* keys, const uint32_t* vals, size_t n, int key_bytes, int kind,
+                          int descending, uint64_t* out, uint32_t* out_vals)
+{
+    if ((key_bytes != 4 && key_bytes != 8) || kind < 0 || kind > 2 || (n && (!keys || !out)))
+        return ORACLE_EARG;
+    if ((vals == NULL) != (out_vals == NULL))
+        return ORACLE_EARG;
+    const int width = 8 * key_bytes;
+    if (width < 64) {
+        for (size_t i = 0; i < n; ++i)
+            if (keys[i] >> width)
+                return ORACLE_EARG;
+    }
+    if (n == 0)
+        return ORACLE_OK;
+    size_t* idx = (size_t*)malloc(n * sizeof(size_t));
+    size_t* tmp = (size_t*)malloc(n * sizeof(size_t));
+    if (!idx || !tmp) {
+        free(idx);
+        free(tmp);
+        return ORACLE_ENOMEM;
+    }
+    for (size_t i = 0; i < n; ++i)
+        idx[i] = i;
+    merge_sort_idx(keys, idx, tmp, 0, n, width, kind, descending);
+    for (size_t i = 0; i < n; ++i) {
+        out[i] = keys[idx[i]];
+        if (vals)
+            out_vals[i] = vals[idx[i]];
+    }
+    free(idx);
+    free(tmp);
+    return ORACLE_OK;
+}

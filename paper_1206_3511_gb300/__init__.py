@@ -14,7 +14,7 @@ bits are sorted as unsigned).  Values are 32-bit (uint32 or int32).
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (RS_PLAN_BUCKET, RS_PLAN_RADIX, RS_PLAN_SEGMENTED, RsPlanDesc, rs_plan_create, rs_plan_destroy,
+from ._lib import (RS_KEY_FLOAT, RS_KEY_INT, RS_KEY_UINT, rs_sort_typed, RS_PLAN_BUCKET, RS_PLAN_RADIX, RS_PLAN_SEGMENTED, RsPlanDesc, rs_plan_create, rs_plan_destroy,
                    rs_plan_info, rs_plan_launch, RsRequest, RsResult, RsServerConfig, RsServerStats, rs_server_create, rs_server_destroy,
                    rs_server_get_stats, rs_server_poll, rs_server_submit, rs_server_wait, bs_sort_u32, bs_sort_u64, rs_segmented_workspace_bytes, rs_sort_segmented_u32, rs_sort_segmented_u64,
                    RS_ALGO_BUCKET, RS_ALGO_RADIX, STATUS, RsConfig, load, rs_config_count, rs_config_get,
@@ -31,7 +31,8 @@ __all__ = [
     "rs_config_count", "rs_config_get", "RsConfig", "RS_ALGO_RADIX", "RS_ALGO_BUCKET", "STATUS",
     "rs_profile_enable", "rs_profile_read", "rs_launch_count", "rs_sort_u32_noalloc",
     "rs_segmented_workspace_bytes", "rs_sort_segmented_u32", "rs_sort_segmented_u64", "segmented_sort",
-    "bs_sort_u32", "bs_sort_u64", "bucket_sort", "Server", "Plan", "RsPlanDesc", "rs_plan_create",
+    "bs_sort_u32", "bs_sort_u64", "bucket_sort", "Server", "Plan", "sort_typed", "rs_sort_typed", "RS_KEY_UINT",
+    "RS_KEY_INT", "RS_KEY_FLOAT", "RsPlanDesc", "rs_plan_create",
     "rs_plan_destroy", "rs_plan_info", "rs_plan_launch", "RS_PLAN_RADIX", "RS_PLAN_BUCKET", "RS_PLAN_SEGMENTED", "RsRequest", "RsResult", "RsServerConfig",
     "RsServerStats", "rs_server_create", "rs_server_destroy", "rs_server_get_stats", "rs_server_poll",
     "rs_server_submit", "rs_server_wait",
@@ -130,6 +131,38 @@ def digit_counts(keys, key_bits: int = 0, digit_bits: int = 8, ws=None, stream=N
     fn = rs_digit_counts_u32 if kb == 4 else rs_digit_counts_u64
     check(fn(keys, keys.numel(), key_bits, digit_bits, counts, ws, ws.numel(), stream), "rs_digit_counts")
     return counts.view(P, 1 << digit_bits).to(torch.int64)
+
+
+_TYPED = {"int32": (1, 4), "int64": (1, 8), "float32": (2, 4), "float64": (2, 8)}
+
+
+def sort_typed(keys, values=None, kind=None, descending: bool = False, out=None, out_values=None, ws=None,
+               stream=None):
+    """Stable radix sort of signed or floating-point keys, ascending or
+    descending (rs_sort_typed).  kind: RS_KEY_UINT / RS_KEY_INT / RS_KEY_FLOAT,
+    or None to take it from the tensor dtype (int32/int64 signed, float32/
+    float64 float).  Floats are ordered by IEEE-754 totalOrder.  Returns
+    (keys, values or None)."""
+    import torch
+
+    _check_tensor(keys, "keys")
+    name = str(keys.dtype).replace("torch.", "")
+    if kind is None:
+        if name not in _TYPED:
+            raise ValueError(f"no key kind for dtype {keys.dtype}")
+        kind = _TYPED[name][0]
+    kb = keys.element_size()
+    if kb not in (4, 8):
+        raise ValueError("keys must be 4 or 8 bytes wide")
+    n = keys.numel()
+    out = torch.empty_like(keys) if out is None else out
+    if values is not None and out_values is None:
+        out_values = torch.empty_like(values)
+    if ws is None:
+        ws = workspace(rs_workspace_bytes(RS_ALGO_RADIX, kb, values is not None, n, 0, 0, out is keys), keys.device)
+    check(rs_sort_typed(kind, kb, descending, keys, out, values, out_values, n, ws, ws.numel(), stream),
+          "rs_sort_typed")
+    return out, out_values
 
 
 def get_status(ws, stream=None) -> int:

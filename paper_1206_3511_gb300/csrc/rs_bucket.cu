@@ -570,11 +570,11 @@ static rs_status bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const uint32
     }
     // b5: sort each bucket of the shared-memory partitions (Algorithm 1 per bucket)
     rs_status st = enqueue_local_sorts(sizeof(KeyT), VALS, tmp_k, tmp_v, keys_out, vals_out, leaf1,
-                                       &h_leaf1->num_small, bins1, bp, stream);
+                                       &h_leaf1->num_small, bins1, bp, nullptr, stream);
     if (st != RS_OK) return st;
     if (I.level2) {
         st = enqueue_local_sorts(sizeof(KeyT), VALS, keys_out, vals_out, keys_out, vals_out, leaf2,
-                                 &h_next->num_small, I.max_leaf2, bp, stream);
+                                 &h_next->num_small, I.max_leaf2, bp, nullptr, stream);
         if (st != RS_OK) return st;
     }
     // overflow partitions: radix on the key bits their buckets span

@@ -91,6 +91,36 @@ __device__ __forceinline__ void set_device_error(WsHeader* h, uint32_t code, uin
     if (atomicCAS(&h->status, 0u, code) == 0u) h->error_detail = detail;
 }
 
+// Order-preserving bijection from a key type to unsigned integers of the same
+// width: a signed key flips its sign bit; an IEEE-754 float flips its sign bit
+// when it is non-negative and every bit when it is negative (the unsigned
+// order of the result is the standard's totalOrder: -NaN < -inf < ... < -0 <
+// +0 < ... < +inf < +NaN); a descending sort complements the result.  Radix
+// digits are taken from to_ordered(key); the sorted keys are written back
+// through from_ordered.
+enum KeyKind : int { kKindUnsigned = 0, kKindSigned = 1, kKindFloat = 2 };
+
+struct KeyXform {
+    int kind;
+    int descending;
+    __host__ __device__ __forceinline__ bool active() const { return kind != kKindUnsigned || descending; }
+    template <typename KeyT>
+    __host__ __device__ __forceinline__ KeyT to_ordered(KeyT k) const {
+        constexpr KeyT top = (KeyT)1 << (8 * sizeof(KeyT) - 1);
+        if (kind == kKindSigned) k ^= top;
+        else if (kind == kKindFloat) k ^= (k & top) ? (KeyT)~(KeyT)0 : top;
+        return descending ? (KeyT)~k : k;
+    }
+    template <typename KeyT>
+    __host__ __device__ __forceinline__ KeyT from_ordered(KeyT y) const {
+        constexpr KeyT top = (KeyT)1 << (8 * sizeof(KeyT) - 1);
+        if (descending) y = (KeyT)~y;
+        if (kind == kKindSigned) y ^= top;
+        else if (kind == kKindFloat) y ^= (y & top) ? top : (KeyT)~(KeyT)0;
+        return y;
+    }
+};
+
 template <typename KeyT>
 __device__ __forceinline__ uint32_t digit_of(KeyT k, int shift, uint32_t mask) {
     return (uint32_t)(k >> shift) & mask;

@@ -51,6 +51,23 @@ struct RadixDigits {
     }
 };
 
+// RadixDigits of the ordered image of typed keys (signed, float, descending):
+// every key is mapped by to_ordered before its digits are taken; all 2^w
+// images are valid, so there is no range check.
+struct OrderedRadixDigits {
+    RadixDigits base;
+    KeyXform xf;
+    __device__ __forceinline__ void init() {}
+    template <typename KeyT>
+    __device__ __forceinline__ uint32_t operator()(KeyT x, int q) const {
+        return base(xf.to_ordered(x), q);
+    }
+    template <typename KeyT>
+    __device__ __forceinline__ bool in_range(KeyT) const {
+        return true;
+    }
+};
+
 struct CountParams {
     const void* keys;
     size_t n;
@@ -175,6 +192,8 @@ struct PassParams {
     WsHeader* hdr;
     uint32_t spin_limit;
     int stall_tile;              // test hook: this tile never publishes (-1 = off)
+    KeyXform xf;                 // typed keys: map loaded keys to their ordered image (xf_in) and
+    int xf_in, xf_out;           // stored keys back (xf_out); both 0 for unsigned keys
 };
 
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS>
@@ -305,6 +324,24 @@ struct TileCtx {
     KeyT key_lo;                 // subtracted from every key before its digit is taken
 };
 
+// The last step of a tile: every staged key (and value) to its place.
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, bool FULL, bool XF, typename DigitOp>
+__device__ __forceinline__ void scatter_staged(const PassParams<DigitOp>& p, const DigitOp& op,
+                                               const PassSmem<KeyT>& sm, const TileCtx<KeyT>& c) {
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t idx = j * BLOCK + threadIdx.x;
+        if (FULL || idx < c.tile_n) {
+            const KeyT key = sm.keys[idx];
+            const uint32_t pos = sm.delta[op((KeyT)(key - c.key_lo))] + idx;
+            if (pos < c.seg_n) {
+                c.kout[pos] = XF ? p.xf.from_ordered(key) : key;
+                if (VALS) c.vout[pos] = sm.vals[idx];
+            }
+        }
+    }
+}
+
 // The body of the pass for one tile; FULL tiles skip every bounds check.
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS, bool FULL, typename DigitOp>
 __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, const DigitOp& op,
@@ -326,6 +363,10 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
         const bool ok = FULL || idx < c.tile_n;
         k[i] = ok ? c.kin[idx] : c.key_lo;
         if (VALS) v[i] = ok ? c.vin[idx] : 0u;
+    }
+    if (p.xf_in) {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) k[i] = p.xf.to_ordered(k[i]);
     }
 
     // rank every key inside its warp; keep (digit << 16 | rank) per item
@@ -390,19 +431,13 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     }
     __syncthreads();
 
-    // write runs of equal digits to their places in the segment
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) {
-        const uint32_t idx = j * BLOCK + tid;
-        if (FULL || idx < c.tile_n) {
-            const KeyT key = sm.keys[idx];
-            const uint32_t pos = sm.delta[op((KeyT)(key - c.key_lo))] + idx;
-            if (pos < c.seg_n) {
-                c.kout[pos] = key;
-                if (VALS) c.vout[pos] = sm.vals[idx];
-            }
-        }
-    }
+    // write runs of equal digits to their places in the segment (typed keys
+    // are mapped back in a separate copy of the loop, so that plain sorts
+    // pay nothing for them)
+    if (p.xf_out)
+        scatter_staged<KeyT, VALS, BLOCK, ITEMS, FULL, true>(p, op, sm, c);
+    else
+        scatter_staged<KeyT, VALS, BLOCK, ITEMS, FULL, false>(p, op, sm, c);
 }
 
 // Persistent: every block claims tiles from the pass's counter until none is

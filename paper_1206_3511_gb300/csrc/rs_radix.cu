@@ -6,6 +6,7 @@
 
 #include "rs_onesweep.cuh"
 #include "rs_radix.h"
+#include "rs_segmented.h"
 
 namespace rs {
 
@@ -166,9 +167,17 @@ rs_status enqueue_digit_counts(int key_bytes, const void* keys, size_t n, int sh
 rs_status radix_sort_impl(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
                           uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
                           cudaStream_t stream, const rs_config* cfg) {
+    return radix_sort_xf(key_bytes, keys_in, keys_out, vals_in, vals_out, n, key_bits, ws, ws_bytes, stream, cfg,
+                         KeyXform{});
+}
+
+rs_status radix_sort_xf(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                        uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes, cudaStream_t stream,
+                        const rs_config* cfg, const KeyXform& xf) {
     const int width = 8 * key_bytes;
     if (key_bits == 0) key_bits = width;
     if (key_bits < 1 || key_bits > width) return RS_ERR_INVALID_ARG;
+    if (xf.active() && key_bits != width) return RS_ERR_INVALID_ARG;  // typed keys use every bit
     if ((vals_in == nullptr) != (vals_out == nullptr)) return RS_ERR_INVALID_ARG;
     if (n > RS_MAX_KEYS) return RS_ERR_INVALID_ARG;
     const bool vals = vals_in != nullptr;
@@ -202,6 +211,11 @@ rs_status radix_sort_impl(int key_bytes, const void* keys_in, void* keys_out, co
 
     // zero the per-call part of the header and the counts
     RS_CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(WsHeader), stream));
+    // a small array without a requested kernel shape is sorted whole by one
+    // block in shared memory: one launch instead of a count and P passes
+    if (!cfg && n <= kLocalCap)
+        return enqueue_local_one(key_bytes, vals, keys_in, vals_in, keys_out, vals_out, (uint32_t)n, key_bits, hdr,
+                                 xf, stream);
     RS_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)L.passes * L.bins * 4, stream));
 
     const int P = L.passes;
@@ -220,9 +234,17 @@ rs_status radix_sort_impl(int key_bytes, const void* keys_in, void* keys_out, co
         }
     }
     const size_t status_words = (size_t)L.tiles * L.bins;
-    st = enqueue_digit_counts(key_bytes, src_k, n, 0, D, P, key_bits, counts, scan, status[0], status_words, hdr,
-                              stream);
-    if (st != RS_OK) return st;
+    if (xf.active()) {
+        CountParams cp{src_k, n, P, L.bins, counts, scan, status[0], status_words, hdr};
+        const OrderedRadixDigits dg{RadixDigits{0, D, L.bins - 1u, key_bits}, xf};
+        const cudaError_t e = key_bytes == 4 ? launch_counts<uint32_t>(cp, dg, count_grid(n), stream)
+                                             : launch_counts<uint64_t>(cp, dg, count_grid(n), stream);
+        if (e != cudaSuccess) return RS_ERR_CUDA;
+    } else {
+        st = enqueue_digit_counts(key_bytes, src_k, n, 0, D, P, key_bits, counts, scan, status[0], status_words, hdr,
+                                  stream);
+        if (st != RS_OK) return st;
+    }
 
     PassParams<RadixDigit> pp{};
     pp.n = (uint32_t)n;
@@ -244,6 +266,9 @@ rs_status radix_sort_impl(int key_bytes, const void* keys_in, void* keys_out, co
         pp.status = status[p & 1];
         pp.status_next = (p + 1 < P) ? status[(p + 1) & 1] : nullptr;
         pp.tile_ctr = &hdr->tile_ctr[p];
+        pp.xf = xf;
+        pp.xf_in = xf.active() && p == 0;
+        pp.xf_out = xf.active() && p == P - 1;
         cudaError_t e = var->launch(pp, stream);
         if (e != cudaSuccess) return RS_ERR_CUDA;
         src_k = dst_k;
@@ -335,6 +360,16 @@ rs_status rs_sort_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_
 rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
                       size_t n, int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream) {
     return radix_sort_impl(8, keys_in, keys_out, vals_in, vals_out, n, key_bits, ws, ws_bytes, stream, nullptr);
+}
+
+rs_status rs_sort_typed(int key_kind, int key_bytes, int descending, const void* keys_in, void* keys_out,
+                        const uint32_t* vals_in, uint32_t* vals_out, size_t n, void* ws, size_t ws_bytes,
+                        rs_stream_t stream) {
+    if (key_kind != RS_KEY_UINT && key_kind != RS_KEY_INT && key_kind != RS_KEY_FLOAT) return RS_ERR_INVALID_ARG;
+    if (key_bytes != 4 && key_bytes != 8) return RS_ERR_INVALID_ARG;
+    const KeyXform xf{key_kind == RS_KEY_INT ? kKindSigned : key_kind == RS_KEY_FLOAT ? kKindFloat : kKindUnsigned,
+                      descending ? 1 : 0};
+    return radix_sort_xf(key_bytes, keys_in, keys_out, vals_in, vals_out, n, 0, ws, ws_bytes, stream, nullptr, xf);
 }
 
 rs_status rs_sort_u32_ex(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in, uint32_t* vals_out,

@@ -42,6 +42,11 @@ const Variant* default_variant(int key_bytes, bool vals);
 rs_status radix_sort_impl(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
                           uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
                           cudaStream_t stream, const rs_config* cfg);
+// The same for typed keys: digits come from xf.to_ordered(key) (pass 0 maps
+// the keys as it loads them, the last pass maps them back as it stores).
+rs_status radix_sort_xf(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                        uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes, cudaStream_t stream,
+                        const rs_config* cfg, const KeyXform& xf);
 
 // Grid of the digit-count kernel for n keys.
 size_t count_grid(size_t n);

@@ -163,8 +163,8 @@ rs_status enqueue_large_passes(int key_bytes, bool vals, const void* src_k, cons
 
 rs_status enqueue_local_sorts(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,
                               uint32_t* out_v, const SegDesc* segs, const uint32_t* count, size_t max_count,
-                              const void* bucket, cudaStream_t stream) {
-    LocalParams lp{src_k, out_k, src_v, out_v, segs, count, bucket};
+                              const void* bucket, WsHeader* range_hdr, cudaStream_t stream) {
+    LocalParams lp{src_k, out_k, src_v, out_v, segs, count, bucket, SegDesc{}, range_hdr, KeyXform{}};
     const size_t grid = max_count ? max_count : 1;
     cudaError_t e;
     if (bucket) {
@@ -184,6 +184,22 @@ rs_status enqueue_local_sorts(int key_bytes, bool vals, const void* src_k, const
             e = vals ? launch_local<uint64_t, true>(lp, f, grid, stream)
                      : launch_local<uint64_t, false>(lp, f, grid, stream);
     }
+    return e == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
+rs_status enqueue_local_one(int key_bytes, bool vals, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                            uint32_t* vals_out, uint32_t n, int key_bits, WsHeader* hdr, const KeyXform& xf,
+                            cudaStream_t stream) {
+    SegDesc one{};
+    one.n = n;
+    one.bits = (uint32_t)key_bits;
+    LocalParams lp{keys_in, keys_out, vals_in, vals_out, nullptr, nullptr, nullptr, one, hdr, xf};
+    NoBucket f;
+    cudaError_t e;
+    if (key_bytes == 4)
+        e = vals ? launch_local<uint32_t, true>(lp, f, 1, stream) : launch_local<uint32_t, false>(lp, f, 1, stream);
+    else
+        e = vals ? launch_local<uint64_t, true>(lp, f, 1, stream) : launch_local<uint64_t, false>(lp, f, 1, stream);
     return e == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
 
@@ -239,7 +255,7 @@ static rs_status segmented_impl(int key_bytes, const void* keys_in, void* keys_o
     // small segments: one block each, straight from the input (a block reads
     // its whole segment before writing, so in place is fine)
     return enqueue_local_sorts(key_bytes, vals, keys_in, vals_in, keys_out, vals_out, B.small, &B.hdr->num_small,
-                               nseg, nullptr, stream);
+                               nseg, nullptr, B.ws_hdr, stream);
 }
 
 }  // namespace rs

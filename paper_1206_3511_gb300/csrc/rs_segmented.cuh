@@ -281,8 +281,11 @@ struct LocalParams {
     const uint32_t* vals_in;
     uint32_t* vals_out;
     const SegDesc* segs;
-    const uint32_t* count;  // number of segments in segs
+    const uint32_t* count;  // number of segments in segs; null: sort the single segment `one`
     const void* bucket;     // BucketParams (bucket mode) or null
+    SegDesc one;            // the segment when count is null
+    WsHeader* hdr;          // non-null: keys >= 2^bits (relative to key_lo) are reported here
+    KeyXform xf;            // typed keys: sorted by their ordered image (plain sorts only)
 };
 
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename BucketFn>
@@ -303,17 +306,22 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
     uint32_t* s_flag = s_scan + kWarps + 1;
 
     if (bfn.active()) bfn.init();
-    const uint32_t nseg = *lp.count;
+    const uint32_t nseg = lp.count ? *lp.count : 1u;
     for (uint32_t si = blockIdx.x; si < nseg; si += gridDim.x) {
-        const SegDesc seg = lp.segs[si];
+        const SegDesc seg = lp.count ? lp.segs[si] : lp.one;
         const uint32_t m = seg.n;
+        const KeyT klo = (KeyT)seg.key_lo;
         __syncthreads();
         const KeyT* kin = static_cast<const KeyT*>(lp.keys_in) + seg.start;
+        bool bad = false;
+        const bool xf = lp.xf.active();
         for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
-            kbuf[0][i] = kin[i];
+            const KeyT k = xf ? lp.xf.to_ordered(kin[i]) : kin[i];
+            kbuf[0][i] = k;
             if (VALS) vbuf[0][i] = lp.vals_in[seg.start + i];
+            bad |= seg.bits < 8 * sizeof(KeyT) && ((KeyT)(k - klo) >> seg.bits) != 0;
         }
-        const KeyT klo = (KeyT)seg.key_lo;
+        if (bad && lp.hdr) set_device_error(lp.hdr, RS_ERR_KEY_RANGE, si);
         int cur = 0;
         bool by_keys = true;
         if (bfn.active()) {
@@ -366,7 +374,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
         }
         KeyT* kout = static_cast<KeyT*>(lp.keys_out) + seg.start;
         for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
-            kout[i] = kbuf[cur][i];
+            kout[i] = xf ? lp.xf.from_ordered(kbuf[cur][i]) : kbuf[cur][i];
             if (VALS) lp.vals_out[seg.start + i] = vbuf[cur][i];
         }
         __syncthreads();

@@ -251,3 +251,73 @@ def test_segmented_oracle_matches_per_segment_sort(oracle):
         a, b = int(off[s]), int(off[s + 1])
         rk, rv = _stable_ref(keys[a:b], vals[a:b])
         assert np.array_equal(ok[a:b], rk) and np.array_equal(ov[a:b], rv)
+
+
+# ---------------------------------------------------------------- typed keys
+def test_typed_signed_matches_numpy_stable_sort(oracle):
+    rng = np.random.default_rng(5)
+    for dt, lo, hi in [(np.int32, -2**31, 2**31), (np.int64, -2**63, 2**63 - 1)]:
+        x = rng.integers(lo, hi, 20_000, dtype=dt)
+        x[:6] = [np.iinfo(dt).min, np.iinfo(dt).max, -1, 0, 1, np.iinfo(dt).min]
+        x[100:200] = x[300:400]  # duplicates
+        order = np.argsort(x, kind="stable")
+        k, v = oracle.sort_typed(x, np.arange(x.size, dtype=np.uint32))
+        assert np.array_equal(k, x[order]) and np.array_equal(v, order.astype(np.uint32))
+
+
+def test_typed_float_matches_numpy_without_nan_and_negative_zero(oracle):
+    rng = np.random.default_rng(6)
+    for dt in (np.float32, np.float64):
+        x = (rng.standard_normal(20_000) * 10.0 ** rng.integers(-30, 30, 20_000)).astype(dt)
+        x[:4] = [np.inf, -np.inf, np.finfo(dt).tiny, -np.finfo(dt).max]
+        x[1000:1100] = x[2000:2100]
+        x[x == 0] = 1  # numpy treats -0 and +0 as equal; totalOrder does not
+        order = np.argsort(x, kind="stable")
+        k, v = oracle.sort_typed(x, np.arange(x.size, dtype=np.uint32))
+        assert np.array_equal(k.view(np.uint8), x[order].view(np.uint8))
+        assert np.array_equal(v, order.astype(np.uint32))
+
+
+def test_typed_float_total_order_of_special_values(oracle):
+    """IEEE 754-2008 totalOrder: -NaN < -inf < -1 < -denormal < -0 < +0 <
+    +denormal < 1 < +inf < +NaN."""
+    for dt, ut in ((np.float32, np.uint32), (np.float64, np.uint64)):
+        qnan = np.array([np.nan], dt).view(ut)[0]
+        sign = ut(1) << ut(8 * np.dtype(dt).itemsize - 1)
+        want_bits = [qnan | sign] + [np.array([v], dt).view(ut)[0] for v in
+                                     (-np.inf, -1.0, -np.finfo(dt).smallest_subnormal, -0.0, 0.0,
+                                      np.finfo(dt).smallest_subnormal, 1.0, np.inf)] + [qnan]
+        want = np.array(want_bits, ut)
+        perm = np.array([9, 3, 0, 7, 5, 1, 8, 2, 6, 4])
+        got = oracle.sort_typed(want[perm].view(dt)).view(ut)
+        assert np.array_equal(got, want)
+
+
+def test_typed_descending_is_the_stable_reverse_order(oracle):
+    rng = np.random.default_rng(7)
+    x = rng.integers(-50, 50, 5000, dtype=np.int32)
+    k, v = oracle.sort_typed(x, np.arange(x.size, dtype=np.uint32), descending=True)
+    order = sorted(range(x.size), key=lambda i: (-int(x[i]), i))
+    assert np.array_equal(v, np.array(order, np.uint32)) and np.array_equal(k, x[order])
+    f = rng.standard_normal(3000).astype(np.float64)
+    f[::7] = f[3]
+    kf, vf = oracle.sort_typed(f, np.arange(f.size, dtype=np.uint32), descending=True)
+    order = sorted(range(f.size), key=lambda i: (-float(f[i]), i))
+    assert np.array_equal(vf, np.array(order, np.uint32))
+
+
+def test_typed_tiny_exhaustive_against_sorted(oracle):
+    alphabet = np.array([-2, -1, 0, 3], np.int32)
+    import itertools
+    for n in range(0, 5):
+        for combo in itertools.product(range(4), repeat=n):
+            x = alphabet[list(combo)] if n else np.zeros(0, np.int32)
+            for desc in (False, True):
+                k, v = oracle.sort_typed(x, np.arange(n, dtype=np.uint32), descending=desc)
+                order = sorted(range(n), key=lambda i: ((-1 if desc else 1) * int(x[i]), i))
+                assert list(v) == order
+
+
+def test_typed_unsigned_equals_radix(oracle):
+    x = synth.u32(10_000, 8, 0)
+    assert np.array_equal(oracle.sort_typed(x), oracle.radix_sort(x, None, 32))

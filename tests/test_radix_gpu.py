@@ -44,7 +44,8 @@ def test_small_config_1m_uniform_31bit(rs, oracle):
     _check(rs, oracle, keys, None, 31, what="1M uniform key_bits=31")
 
 
-TILE_SIZES = [0, 1, 2, 3, 31, 33, 3839, 3840, 3841, 2 * 3840 + 7, 65537, (1 << 20) + 3]
+# around the single-block limit (4096 keys) and the u32 scatter tile (4608 keys)
+TILE_SIZES = [0, 1, 2, 3, 31, 33, 3840, 4095, 4096, 4097, 4607, 4608, 4609, 2 * 4608 + 7, 65537, (1 << 20) + 3]
 
 
 @pytest.mark.parametrize("n", TILE_SIZES)
@@ -54,7 +55,7 @@ def test_sizes_u32(rs, oracle, n):
     _check(rs, oracle, keys, synth.index_values(n), what=f"u32 kv n={n}")
 
 
-@pytest.mark.parametrize("n", [0, 1, 5, 3071, 3072, 3073, 2560 * 3 + 1, 100_003])
+@pytest.mark.parametrize("n", [0, 1, 5, 3071, 4096, 4097, 6143, 6144, 6145, 2560 * 3 + 1, 100_003])
 def test_sizes_u64(rs, oracle, n):
     keys = synth.keys_u64(n, 64, seed=n)
     _check(rs, oracle, keys, None, what=f"u64 n={n}")
@@ -175,6 +176,49 @@ def test_key_above_key_bits_is_reported(rs):
     keys[777] = 5
     kd = to_dev(keys)
     assert rs.rs_sort_u32(kd, out, None, None, keys.size, 12, ws, ws.numel()) == 0
+    assert rs.get_status(ws) == 0
+    assert np.array_equal(from_dev(out, np.uint32), np.sort(keys))
+
+
+@pytest.mark.parametrize("kb,with_values", [(4, False), (4, True), (8, False), (8, True)])
+def test_small_array_is_one_block_sort(rs, oracle, kb, with_values):
+    """Arrays of at most 4096 keys are sorted by one shared-memory block: one
+    kernel launch, the same bits as the oracle, in place too."""
+    import torch
+
+    n = 4000
+    keys = synth.u32(n, 61, 0) if kb == 4 else synth.keys_u64(n, 64, seed=61)
+    vals = synth.index_values(n) if with_values else None
+    kd = to_dev(keys)
+    vd = to_dev(vals) if with_values else None
+    torch.cuda.synchronize()
+    before = rs.rs_launch_count()
+    ok, ov = rs.sort(kd, vd)
+    torch.cuda.synchronize()
+    assert rs.rs_launch_count() - before == 1
+    if with_values:
+        wk, wv = oracle.radix_sort(keys, vals, 8 * kb)
+        assert_same(from_dev(ov, np.uint32), wv, "small values")
+    else:
+        wk = oracle.radix_sort(keys, None, 8 * kb)
+    assert_same(from_dev(ok, keys.dtype), wk, "small keys")
+    ok2, ov2 = rs.sort(kd, vd, out=kd, out_values=vd)
+    torch.cuda.synchronize()
+    assert_same(from_dev(kd, keys.dtype), wk, "small in place")
+
+
+def test_small_key_above_key_bits_is_reported(rs):
+    import torch
+
+    keys = synth.u32(1000, 62, 0) >> np.uint32(20)  # 12-bit keys
+    keys[500] = 1 << 12
+    kd = to_dev(keys)
+    ws = rs.workspace(rs.rs_workspace_bytes(0, 4, 0, keys.size, 12, 0, 0))
+    out = torch.empty_like(kd)
+    assert rs.rs_sort_u32(kd, out, None, None, keys.size, 12, ws, ws.numel()) == 0
+    assert rs.get_status(ws) == 3  # RS_ERR_KEY_RANGE
+    keys[500] = 7
+    assert rs.rs_sort_u32(to_dev(keys), out, None, None, keys.size, 12, ws, ws.numel()) == 0
     assert rs.get_status(ws) == 0
     assert np.array_equal(from_dev(out, np.uint32), np.sort(keys))
 

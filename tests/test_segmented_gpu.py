@@ -98,6 +98,21 @@ def test_bad_offsets_are_reported(rs):
     assert rs.get_status(ws) == 1  # RS_ERR_INVALID_ARG recorded on the device
 
 
+def test_key_above_key_bits_in_a_small_segment_is_reported(rs):
+    import torch
+
+    sizes = [100, 20_000, 300]
+    n = sum(sizes)
+    keys = synth.u32(n, 47, 0) >> np.uint32(20)  # 12-bit keys
+    keys[20_150] = 1 << 12  # inside the last (shared-memory) segment
+    kd = to_dev(keys)
+    off = to_dev(synth.segment_offsets(sizes))
+    ws = rs.workspace(rs.rs_segmented_workspace_bytes(4, 0, n, 3, 12))
+    out = torch.empty_like(kd)
+    assert rs.rs_sort_segmented_u32(kd, out, None, None, off, 3, n, 12, ws, ws.numel()) == 0
+    assert rs.get_status(ws) == 3  # RS_ERR_KEY_RANGE
+
+
 def _u32_as_i64(t):
     return t.to(__import__("torch").int64) & 0xFFFFFFFF
 
