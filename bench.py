@@ -42,7 +42,8 @@ WORKLOADS = {
     "radix_u64kv_100m": ("radix", 8, True, 100_000_000, 64, None,
                          "LSD radix sort, 100M uint64 keys uniform [0,2^64) + uint32 index values, 8 passes"),
     "radix_u64_40bit_50m": ("radix", 8, False, 50_000_000, 40, None,
-                            "LSD radix sort, 50M uint64 keys uniform [0,2^40), key_bits=40, 5 passes"),
+                            "LSD radix sort, 50M uint64 keys uniform [0,2^40), key_bits=40, autotuned digit width "
+                            "and kernel shape"),
 }
 # the seven 100M-key u32 distributions, radix (key_bits 32) and bucket (declared bounds, n/16 buckets)
 for _d in range(7):
@@ -56,6 +57,19 @@ WORKLOADS["bucket_u32_1m"] = ("bucket", 4, False, 1_000_000, 31, 10,
                               "bucket sort, 1M uint32 keys uniform [0,2^31), 62,500 buckets over [0,2^31-1]")
 WORKLOADS["radix_u32_1m"] = ("radix", 4, False, 1_000_000, 32, 10,
                              "LSD radix sort, 1M uint32 keys uniform [0,2^31), 8-bit digits, 4 passes")
+WORKLOADS["paper_cases"] = ("paper", 4, False, 100_000_000, 0, None,
+                            "the paper's six input cases (Sec. 3.1) at n = 10^6, 10^7, 10^8: radix sort with key_bits "
+                            "= bit length of M - 1 and bucket sort with bounds [0, M - 1] and n/16 buckets")
+# the paper's Table 1: seconds on a laptop (Intel i5), sequential C++, per case: radix at n = 10^6, 10^7, 10^8, then
+# bucket at the same sizes (context only)
+PAPER_TABLE1_S = {
+    1: (1.78, 17.66, 176.84, 0.74, 5.84, 45.92),
+    2: (1.88, 18.93, 174.85, 0.61, 4.14, 26.83),
+    3: (1.86, 17.69, 178.68, 0.61, 4.12, 28.27),
+    4: (1.05, 11.10, 105.31, 0.31, 3.00, 31.54),
+    5: (2.45, 24.56, 246.28, 0.78, 8.54, 97.43),
+    6: (1.77, 17.66, 176.65, 0.61, 5.18, 41.06),
+}
 # n = number of arrays (batched) or requests per arrival rate (served)
 WORKLOADS["batched_u32_20k"] = ("batched", 4, False, 20_000, 32, 0,
                                 "segmented sort of 20,000 uint32 arrays, sizes log-uniform in [256, 2,000,000] "
@@ -68,6 +82,9 @@ BATCH_LO, BATCH_HI = 256, 2_000_000
 SERVED_LO, SERVED_HI = 1_000, 50_000_000
 SERVED_RATES = (1_000, 2_000, 5_000, 10_000, 20_000, 35_000, 50_000)
 SERVED_BUDGET = 80 * 10**9
+
+# radix workloads whose kernel shape and digit width come from the autotuner
+AUTOTUNED = ("radix_u64_40bit_50m",)
 
 # kernels whose algorithmic bytes per launch are 2 n (w + v) (one read and one
 # write of every key) and n w (one read)
@@ -84,6 +101,8 @@ def parse_args():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="radix_u32_100m")
     ap.add_argument("--n", type=int, default=0, help="override the key count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="radix: pick the kernel shape with the autotuner")
+    ap.add_argument("--no-context", action="store_true", help="skip the torch.sort context timing")
     ap.add_argument("--rates", default="", help="served: comma-separated arrival rates per second")
     ap.add_argument("--no-bucket-sweep", dest="bucket_sweep", action="store_false",
                     help="served: skip the second sweep with half the requests bucket sorts")
@@ -158,7 +177,7 @@ def measured_peaks() -> dict:
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("rs_onesweep.cuh", "rs_radix.cu", "rs_common.cuh"):
+    for f in ("rs_onesweep.cuh", "rs_radix.cu", "rs_common.cuh", "rs_segmented.cuh", "rs_segmented.cu", "rs_segmented.h"):
         with open(os.path.join(ROOT, "paper_1206_3511_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -292,6 +311,7 @@ def run_ours(args):
     d_out = torch.empty_like(d_keys)
     d_outv = torch.empty_like(d_vals) if has_v else None
     stream = torch.cuda.current_stream()
+    tuned = None
     if algo == "bucket":
         lo, hi = bucket_bounds(wl)
         nb = max(1, n // 16)
@@ -301,11 +321,19 @@ def run_ours(args):
         def call(ws):
             return bfn(d_keys, d_out, d_vals, d_outv, n, lo, hi, nb, ws, ws.numel(), stream)
     else:
-        nbytes = rs.rs_workspace_bytes(rs.RS_ALGO_RADIX, kb, has_v, n, key_bits, 0, 0)
-        rfn = rs.rs_sort_u32 if kb == 4 else rs.rs_sort_u64
+        if args.autotune or wl in AUTOTUNED:
+            # the plan's autotuner picks the kernel shape and digit width; the
+            # timed calls then use that shape (eager, so kernels are timed)
+            plan = rs.Plan(rs.RS_PLAN_RADIX, d_keys, d_out, d_vals, d_outv, key_bits=key_bits, autotune=True)
+            tuned, _, tuned_ms = plan.info()
+            plan.close()
+            nbytes = rs.rs_workspace_bytes_cfg(kb, has_v, n, key_bits, tuned)
+        else:
+            nbytes = rs.rs_workspace_bytes(rs.RS_ALGO_RADIX, kb, has_v, n, key_bits, 0, 0)
+        rfn = rs.rs_sort_u32_ex if kb == 4 else rs.rs_sort_u64_ex
 
         def call(ws):
-            return rfn(d_keys, d_out, d_vals, d_outv, n, key_bits, ws, ws.numel(), stream)
+            return rfn(d_keys, d_out, d_vals, d_outv, n, key_bits, ws, ws.numel(), stream, tuned)
     ws = rs.workspace(nbytes, d_keys.device)
 
     def step():
@@ -416,13 +444,34 @@ def run_ours(args):
         # read+write to sort the buckets
         whole_bytes = n * kb + 4 * n * w
     else:
-        passes = -(-key_bits // 8)
+        digit_bits = tuned[0] if tuned else 8
+        passes = -(-key_bits // digit_bits)
         whole_bytes = n * kb + passes * 2 * n * w
     step_s = ms / args.steps / 1e3
     whole = {"algorithmic_bytes_per_step": whole_bytes,
              "achieved_gbs": whole_bytes / step_s / 1e9,
              "frac_of_peak": whole_bytes / step_s / 1e9 / hbm_peak,
              "kernels": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kstats.items()}}
+
+    # context: a library sort (torch.sort, stable, keys only) of the same
+    # keys on the same GPU, read as signed integers of the same width
+    lib = None
+    if not args.no_context:
+        t_in = d_keys.clone()
+        for _ in range(2):
+            torch.sort(t_in, stable=True)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        c0.record(stream)
+        for _ in range(reps):
+            torch.sort(t_in, stable=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        lib_ms = c0.elapsed_time(c1) / reps
+        lib = {"torch.sort": {"value": n / (lib_ms / 1e3) / 1e9, "unit": "Gkeys/s", "ms_per_sort": lib_ms,
+                              "note": "stable torch.sort of the keys as signed integers, keys only, same GPU"}}
+        del t_in
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -440,10 +489,12 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": _dtype(wl), "data": "synthetic",
         "config": {"workload": desc, "n": n, "key_bits": key_bits, "parallelism": f"replicas x{world}",
+                   "kernel_shape": ({"digit_bits": tuned[0], "block_threads": tuned[1], "items_per_thread": tuned[2],
+                                     "chosen_by": "autotuner"} if algo == "radix" and tuned else None),
                    "l2": "inputs larger than L2 (%d MB keys vs 129 MB L2), no flush" % (n * kb // 2**20)},
         "clocks": clocks, "gpu_launches": launches, "roofline": roofline, "whole_sort": whole,
         "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "cpu_baseline": cpu,
+        "cpu_baseline": cpu, "context": lib,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -638,6 +689,8 @@ def run_batched(args):
         return n_large * 4 * per_step
 
     roofline = _roofline_from_stats(kstats, prof_steps, step_bytes_of, hbm_peak, peak_src)
+    if roofline and roofline["kernel"] == "onesweep_seg_pass" and count == WORKLOADS["batched_u32_20k"][3]:
+        roofline["traffic"] = ncu_traffic("onesweep_seg_pass", "batched_u32_20k")
     cpu = None
     if not args.no_cpu_baseline:
         cpu = _batched_cpu_sample(sizes, off, d_keys)
@@ -693,6 +746,79 @@ def _batched_cpu_sample(sizes, off, d_keys=None, budget_keys=150_000_000):
                       f"single thread of {os.cpu_count()} host cores"}
 
 
+# ------------------------------------------------------------------ the paper's cases
+def run_paper_cases(args):
+    """The paper's Table 1 grid on the GPU: six input cases at three sizes,
+    radix and bucket sort, with the workspace each call needs (the analogue
+    of Table 2).  Keys are copied to the device before timing."""
+    import numpy as np
+    import torch
+
+    import paper_1206_3511_gb300 as rs
+    import synth
+
+    world, rank, local = _dist_env()
+    torch.cuda.set_device(local if world > 1 else 0)
+    rs.load()
+    sizes = (10**6, 10**7, 10**8) if not args.n else (args.n,)
+    steps = max(3, min(args.steps, 20))
+    stream = torch.cuda.current_stream()
+    rows = []
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    launches0 = rs.rs_launch_count()
+    for case, (desc, M) in synth.PAPER_CASES.items():
+        for si, n in enumerate(sizes):
+            keys = synth.paper_case_keys(n, case, seed=rank)
+            d_keys = torch.from_numpy(keys.view(np.int32)).cuda()
+            d_out = torch.empty_like(d_keys)
+            key_bits = max(1, int(M - 1).bit_length())
+            nb = max(1, n // 16)
+            ws_r = rs.rs_workspace_bytes(rs.RS_ALGO_RADIX, 4, False, n, key_bits, 0, 0)
+            ws_b = rs.rs_workspace_bytes(rs.RS_ALGO_BUCKET, 4, False, n, 0, nb, 0)
+            ws = rs.workspace(max(ws_r, ws_b), d_keys.device)
+            calls = {
+                "radix": lambda: rs.rs_sort_u32(d_keys, d_out, None, None, n, key_bits, ws, ws.numel(), stream),
+                "bucket": lambda: rs.bs_sort_u32(d_keys, d_out, None, None, n, 0, M - 1, nb, ws, ws.numel(), stream),
+            }
+            row = {"case": case, "input": desc, "n": n, "key_bits": key_bits, "num_buckets": nb,
+                   "workspace_mb": {"radix": ws_r / 2**20, "bucket": ws_b / 2**20}, "input_mb": n * 4 / 2**20}
+            want = np.sort(keys)
+            for algo, fn in calls.items():
+                for _ in range(max(3, args.warmup)):
+                    rs.check(fn(), algo)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(steps):
+                    rs.check(fn(), algo)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                if rs.get_status(ws):
+                    raise rs.SortError(rs.get_status(ws), algo)
+                assert np.array_equal(d_out.cpu().numpy().view(np.uint32), want), f"{algo} case {case} n={n}"
+                paper_s = PAPER_TABLE1_S[case][si + (3 if algo == "bucket" else 0)] if n in (10**6, 10**7, 10**8) else None
+                row[algo] = {"ms": ms, "gkeys_s": n / (ms / 1e3) / 1e9, "paper_laptop_s": paper_s}
+            rows.append(row)
+            del d_keys, d_out, ws
+    clocks = sampler.stop()
+    launches = rs.rs_launch_count() - launches0
+    if rank != 0:
+        return
+    top = [r for r in rows if r["case"] == 1 and r["n"] == max(sizes)][0]
+    print(json.dumps({
+        "metric": METRIC, "value": top["radix"]["gkeys_s"], "unit": "Gkeys/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": top["radix"]["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["paper_cases"][6], "sizes": list(sizes),
+                   "l2": "every size is timed as is; 10^6 and 10^7 fit in L2 (context rows)"},
+        "value_note": "radix sort of case 1 at the largest size", "clocks": clocks, "gpu_launches": launches,
+        "roofline": None, "cases": rows,
+        "paper_note": "paper_laptop_s: the paper's Table 1 (sequential C++, Intel i5 laptop), context only",
+        "e2e": None, "cpu_baseline": None}), flush=True)
+
+
 # ------------------------------------------------------------------ served workload
 def served_bytes(n, kind):
     """Algorithmic HBM bytes of one radix request: one read to count, then
@@ -735,10 +861,22 @@ def run_served(args):
             src_k[(1, d)] = torch.from_numpy(synth.keys_u64_shaped(big, d, seed=rank).view(np.int64)).to(dev)
     if np.any(kinds == 1):
         src_v = torch.arange(big, dtype=torch.int32, device=dev)
-    # output ring: request i writes slot i % M and waits for request i - M first
-    M = 48
-    ring_k = [torch.empty(big * 8, dtype=torch.uint8, device=dev) for _ in range(M)]
-    ring_v = [torch.empty(big * 4, dtype=torch.uint8, device=dev) for _ in range(M)]
+    # outputs: a circular arena; request i's keys (and values) go at the head,
+    # and before a region is reused the requests that held it are waited for
+    ARENA = 60 * 10**9
+    arena = torch.empty(ARENA, dtype=torch.uint8, device=dev)
+    abase = arena.data_ptr()
+    out_off, out_end, lap = [], [], []
+    head, cur_lap = 0, 0
+    for i in range(count):
+        nb_out = int(sizes[i]) * (4 if kinds[i] == 0 else 12)
+        nb_out = (nb_out + 255) // 256 * 256
+        if head + nb_out > ARENA:
+            head, cur_lap = 0, cur_lap + 1
+        out_off.append(head)
+        out_end.append(head + nb_out)
+        lap.append(cur_lap)
+        head += nb_out
     def build_requests(bucket_share):
         """One request per draw; a share of them (drawn) use the bucket sort
         with the distribution's declared bounds and n/16 buckets."""
@@ -746,14 +884,13 @@ def run_served(args):
         reqs, nbytes = [], 0
         for i in range(count):
             n, kd, d = int(sizes[i]), int(kinds[i]), int(dists[i])
-            slot = i % M
             lo, hi = synth.DECLARED_BOUNDS[d]
             kb = 4 if kd == 0 else 8
             if kd == 1:
                 lo, hi = lo << 32, (hi << 32) | 0xFFFFFFFF
-            kin, kout = src_k[(kd, d)].data_ptr(), ring_k[slot].data_ptr()
+            kin, kout = src_k[(kd, d)].data_ptr(), abase + out_off[i]
             vin = src_v.data_ptr() if kd == 1 else None
-            vout = ring_v[slot].data_ptr() if kd == 1 else None
+            vout = abase + out_off[i] + 8 * n if kd == 1 else None
             if use_bucket[i]:
                 reqs.append(_lib.RsRequest(rs.RS_ALGO_BUCKET, kb, kin, kout, vin, vout, n, 0, lo, hi, 0))
                 w = kb + (4 if kd == 1 else 0)
@@ -771,10 +908,16 @@ def run_served(args):
         arr = synth.poisson_arrivals(count, rate, seed=seed) * 1e3  # ms
         tickets = [0] * count
         lag = []
+        oldest = 0  # requests below this index no longer hold arena space
         t0 = time.monotonic() * 1e3 + 2.0
         for i in range(count):
-            if i >= M:
-                srv.wait(tickets[i - M])
+            # wait for the earlier requests whose output region this one
+            # reuses: every request two laps back, and those of the previous
+            # lap that start before this region ends
+            while oldest < i and (lap[oldest] < lap[i] - 1 or
+                                  (lap[oldest] == lap[i] - 1 and out_off[oldest] < out_end[i])):
+                srv.wait(tickets[oldest])
+                oldest += 1
             target = t0 + arr[i]
             while time.monotonic() * 1e3 < target:
                 pass
@@ -831,21 +974,23 @@ def run_served(args):
     clocks = sampler.stop()
     torch.cuda.synchronize()
 
-    # spot check: the last small requests of the last run, against a host sort
+    # spot check: the last small requests of the last run (their output
+    # regions are not reused after them), against a host sort
     checked = 0
-    for i in range(count - 1, max(-1, count - M - 1), -1):
+    for i in range(count - 1, -1, -1):
         n, kd, d = int(sizes[i]), int(kinds[i]), int(dists[i])
-        if n > 2_000_000:
+        if n > 2_000_000 or any(out_off[j] < out_end[i] and out_off[i] < out_end[j] for j in range(i + 1, count)):
             continue
+        o = out_off[i]
         if kd == 0:
             inp = src_k[(0, d)][:n].cpu().numpy().view(np.uint32)
-            got = ring_k[i % M][: 4 * n].cpu().numpy().view(np.uint32)
+            got = arena[o: o + 4 * n].cpu().numpy().view(np.uint32)
             assert np.array_equal(got, np.sort(inp, kind="stable")), f"served request {i} wrong"
         else:
             inp = src_k[(1, d)][:n].cpu().numpy().view(np.uint64)
             order = np.argsort(inp, kind="stable")
-            got_k = ring_k[i % M][: 8 * n].cpu().numpy().view(np.uint64)
-            got_v = ring_v[i % M][: 4 * n].cpu().numpy().view(np.uint32)
+            got_k = arena[o: o + 8 * n].cpu().numpy().view(np.uint64)
+            got_v = arena[o + 8 * n: o + 12 * n].cpu().numpy().view(np.uint32)
             assert np.array_equal(got_k, inp[order]) and np.array_equal(got_v, order.astype(np.uint32)), \
                 f"served request {i} wrong"
         checked += 1
@@ -976,8 +1121,13 @@ def main():
             run_reference_batched(args)
         elif kind == "served":
             run_reference_served(args)
+        elif kind == "paper":
+            print(json.dumps({"impl": "reference", "unavailable": "the paper-case grid is a report; its oracle "
+                              "timings are the per-workload reference runs"}), flush=True)
         else:
             run_reference(args)
+    elif kind == "paper":
+        run_paper_cases(args)
     elif kind == "batched":
         run_batched(args)
     elif kind == "served":

@@ -213,6 +213,34 @@ def gaussian_u32(n: int, seed: int = 0) -> np.ndarray:
     return out
 
 
+# The paper's six input cases (Sec. 3.1): (description, M); keys lie in [0, M).
+PAPER_CASES = {
+    1: ("uniform, M = 10^6", 10**6),
+    2: ("sorted, M = 10^6", 10**6),
+    3: ("95% sorted, M = 10^6", 10**6),
+    4: ("small range, M = 10^4", 10**4),
+    5: ("large range, M = 10^8", 10**8),
+    6: ("n/3 equal to one value, M = 10^6", 10**6),
+}
+
+
+def paper_case_keys(n: int, case: int, seed: int = 0) -> np.ndarray:
+    """n uint32 keys shaped like the paper's input case (Sec. 3.1)."""
+    if case == 1:
+        return uniform_below(n, 10**6, seed, 61)
+    if case == 2:
+        return _sorted_spread(n, seed, 62, 10**6)
+    if case == 3:
+        return keys_u32(n, 7, seed)
+    if case == 4:
+        return uniform_below(n, 10**4, seed, 64)
+    if case == 5:
+        return keys_u32(n, 9, seed)
+    if case == 6:
+        return keys_u32(n, 8, seed)
+    raise ValueError(f"no paper case {case}")
+
+
 def keys_u64(n: int, key_bits: int = 64, seed: int = 0, dist_id: int = 20) -> np.ndarray:
     """n uint64 keys uniform over [0, 2^key_bits)."""
     d = u64(n, seed, dist_id)
