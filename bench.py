@@ -117,6 +117,25 @@ def _dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(values, device=None) -> list[float]:
+    """Each value's maximum over all ranks (the job's time is its slowest
+    rank's); the values themselves on a single process."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_rate(units_per_rank: float, world: int, ms: float, scale: float = 1e9) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time
+    (weak scaling: each rank sorts its own inputs)."""
+    return world * units_per_rank / (ms / 1e3) / scale
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons while running."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -399,17 +418,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
 
-    if world > 1:
-        t = torch.tensor([ms, e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], device=dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
-    value = world * n * args.steps / (ms / 1e3) / 1e9
-    e2e_value = world * n * e2e_steps / (e2e_ms / 1e3) / 1e9
+    value = job_rate(n * args.steps, world, ms)
+    e2e_value = job_rate(n * e2e_steps, world, e2e_ms)
     h2d = n * kb + (n * 4 if has_v else 0)
     d2h = n * kb
 
@@ -664,16 +680,13 @@ def run_batched(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
 
-    if world > 1:
-        t = torch.tensor([ms, e2e_ms, plain_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_ms, plain_ms = float(t[0]), float(t[1]), float(t[2])
+    ms, e2e_ms, plain_ms = max_over_ranks([ms, e2e_ms, plain_ms], device=dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
-    value = world * n_total * args.steps / (ms / 1e3) / 1e9
+    value = job_rate(n_total * args.steps, world, ms)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm_peak else "fallback"
@@ -711,7 +724,7 @@ def run_batched(args):
                   "steps": plain_steps},
         "latency_note": "completion time of each array after all arrays are handed over at once",
         "kernels": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kstats.items()},
-        "e2e": {"value": n_total * e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": "Gkeys/s",
+        "e2e": {"value": job_rate(n_total * e2e_steps, world, e2e_ms), "unit": "Gkeys/s",
                 "h2d_bytes_per_step": n_total * 4, "d2h_bytes_per_step": n_total * 4},
         "cpu_baseline": cpu,
     }
@@ -973,6 +986,9 @@ def run_served(args):
     launches = rs.rs_launch_count() - launches0
     clocks = sampler.stop()
     torch.cuda.synchronize()
+    # replicas: every rank serves its own copy of the mix; the job's time at
+    # the top rate is the slowest rank's
+    top_span = max_over_ranks([sweep[-1]["server"]["span_ms"]], device=dev)[0]
 
     # spot check: the last small requests of the last run (their output
     # regions are not reused after them), against a host sort
@@ -1002,9 +1018,9 @@ def run_served(args):
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     peak_src = "measured" if peaks.get("hbm_gbs") else "fallback"
     top = sweep[-1]["server"]
-    achieved = radix_bytes / (top["span_ms"] / 1e3) / 1e9
+    achieved = job_rate(radix_bytes, world, top_span)
     line = {
-        "metric": METRIC, "value": top["gkeys_s"], "unit": "Gkeys/s", "n_gpus": world,
+        "metric": METRIC, "value": job_rate(total_keys, world, top_span), "unit": "Gkeys/s", "n_gpus": world,
         "steps": len(rates), "warmup": args.warmup, "ms_per_step": top["span_ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32+u64", "data": "synthetic",
         "config": {"workload": WORKLOADS["served_mix"][6], "requests_per_rate": count, "keys_per_run": total_keys,
@@ -1022,7 +1038,8 @@ def run_served(args):
         "sweep_half_bucket": sweep_bucket,
         "knee_half_bucket_per_s": ({"server": knee(sweep_bucket, "server"), "fifo": knee(sweep_bucket, "fifo")}
                                    if sweep_bucket else None),
-        "e2e": {"value": top["gkeys_s"], "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+        "e2e": {"value": job_rate(total_keys, world, top_span), "unit": "Gkeys/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0,
                 "note": "host-submitted requests, completion seen on the host; keys resident on the device"},
         "cpu_baseline": None if args.no_cpu_baseline else _served_cpu_sample(sizes, kinds, dists),
     }

@@ -282,7 +282,7 @@ cudaError_t launch_plain_bucket_pass(const PassParams<BucketDigit>& p, cudaStrea
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
         attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)Shape::smem_bytes(8));
+                                        (int)max_fitting_pass_smem<Shape>());
     });
     if (attr_err != cudaSuccess) return attr_err;
     const size_t smem = Shape::smem_bytes(p.digit_bits);

@@ -343,7 +343,9 @@ __device__ __forceinline__ void scatter_staged(const PassParams<DigitOp>& p, con
 }
 
 // The body of the pass for one tile; FULL tiles skip every bounds check.
-template <typename KeyT, bool VALS, int BLOCK, int ITEMS, bool FULL, typename DigitOp>
+// XF: compiled with the typed-key mapping (p.xf_in / p.xf_out are honoured);
+// plain kernels are compiled without it and carry none of its code.
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, bool FULL, typename DigitOp, bool XF = false>
 __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, const DigitOp& op,
                                               const PassSmem<KeyT>& sm, const TileCtx<KeyT>& c, uint32_t bins,
                                               bool publish) {
@@ -364,7 +366,7 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
         k[i] = ok ? c.kin[idx] : c.key_lo;
         if (VALS) v[i] = ok ? c.vin[idx] : 0u;
     }
-    if (p.xf_in) {
+    if (XF && p.xf_in) {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) k[i] = p.xf.to_ordered(k[i]);
     }
@@ -432,9 +434,8 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     __syncthreads();
 
     // write runs of equal digits to their places in the segment (typed keys
-    // are mapped back in a separate copy of the loop, so that plain sorts
-    // pay nothing for them)
-    if (p.xf_out)
+    // are mapped back in a separate copy of the loop)
+    if (XF && p.xf_out)
         scatter_staged<KeyT, VALS, BLOCK, ITEMS, FULL, true>(p, op, sm, c);
     else
         scatter_staged<KeyT, VALS, BLOCK, ITEMS, FULL, false>(p, op, sm, c);
@@ -443,7 +444,7 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
 // Persistent: every block claims tiles from the pass's counter until none is
 // left.  A block holds one tile at a time and only waits on tiles claimed
 // earlier, whose blocks are running, so the waits always end.
-template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB, typename DigitOp>
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB, typename DigitOp, bool XF = false>
 __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p) {
     constexpr int kTile = BLOCK * ITEMS;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -475,9 +476,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p)
         c.key_lo = 0;
         const bool publish = (int)tile != p.stall_tile;
         if (c.tile_n == (uint32_t)kTile)
-            onesweep_tile<KeyT, VALS, BLOCK, ITEMS, true>(p, op, sm, c, bins, publish);
+            onesweep_tile<KeyT, VALS, BLOCK, ITEMS, true, DigitOp, XF>(p, op, sm, c, bins, publish);
         else
-            onesweep_tile<KeyT, VALS, BLOCK, ITEMS, false>(p, op, sm, c, bins, publish);
+            onesweep_tile<KeyT, VALS, BLOCK, ITEMS, false, DigitOp, XF>(p, op, sm, c, bins, publish);
         __syncthreads();
     }
 }

@@ -12,17 +12,15 @@ namespace rs {
 
 namespace {
 
-template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB>
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB, bool XF = false>
 cudaError_t launch_pass(const PassParams<RadixDigit>& p, cudaStream_t s) {
     using Shape = OnesweepShape<KeyT, VALS, BLOCK, ITEMS>;
-    auto kern = k_onesweep<KeyT, VALS, BLOCK, ITEMS, MINB, RadixDigit>;
+    auto kern = k_onesweep<KeyT, VALS, BLOCK, ITEMS, MINB, RadixDigit, XF>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
-        size_t most = 0;
-        for (int D = kMinDigitBits; D <= kMaxDigitBits; ++D)
-            if (Shape::smem_bytes(D) <= kMaxSmemPerBlock && Shape::smem_bytes(D) > most) most = Shape::smem_bytes(D);
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)max_fitting_pass_smem<Shape>());
     });
     if (attr_err != cudaSuccess) return attr_err;
     const size_t smem = Shape::smem_bytes(p.digit_bits);
@@ -32,24 +30,37 @@ cudaError_t launch_pass(const PassParams<RadixDigit>& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB = 1024 / BLOCK>
+using PassLauncher = cudaError_t (*)(const PassParams<RadixDigit>&, cudaStream_t);
+
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB, bool TYPED>
+constexpr PassLauncher typed_launcher() {
+    if constexpr (TYPED)
+        return &launch_pass<KeyT, VALS, BLOCK, ITEMS, MINB, true>;
+    else
+        return nullptr;
+}
+
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB = 1024 / BLOCK, bool TYPED = false>
 constexpr Variant make_variant() {
     return Variant{(int)sizeof(KeyT), VALS, BLOCK, ITEMS, BLOCK * ITEMS,
-                   &launch_pass<KeyT, VALS, BLOCK, ITEMS, MINB>, &OnesweepShape<KeyT, VALS, BLOCK, ITEMS>::smem_bytes};
+                   &launch_pass<KeyT, VALS, BLOCK, ITEMS, MINB>,
+                   typed_launcher<KeyT, VALS, BLOCK, ITEMS, MINB, TYPED>(),
+                   &OnesweepShape<KeyT, VALS, BLOCK, ITEMS>::smem_bytes};
 }
 
 // Compiled kernel shapes.  The first entry of each (key width, values) group
-// is the default.
+// is the default (the fastest measured on GB300 at 100M keys); only the
+// defaults are also compiled for typed keys.
 const Variant kVariants[] = {
+    make_variant<uint32_t, false, 384, 16, 3, true>(),
     make_variant<uint32_t, false, 256, 18, 4>(),
     make_variant<uint32_t, false, 256, 15, 4>(),
-    make_variant<uint32_t, false, 384, 16, 3>(),
     make_variant<uint32_t, false, 512, 15, 2>(),
-    make_variant<uint32_t, true, 256, 12, 4>(),
+    make_variant<uint32_t, true, 256, 12, 4, true>(),
     make_variant<uint32_t, true, 256, 15, 3>(),
-    make_variant<uint64_t, false, 256, 12, 4>(),
+    make_variant<uint64_t, false, 256, 12, 4, true>(),
     make_variant<uint64_t, false, 256, 9, 4>(),
-    make_variant<uint64_t, true, 256, 10, 3>(),
+    make_variant<uint64_t, true, 256, 10, 3, true>(),
     make_variant<uint64_t, true, 256, 8, 4>(),
 };
 constexpr int kDefaultDigitBits = 8;
@@ -178,6 +189,7 @@ rs_status radix_sort_xf(int key_bytes, const void* keys_in, void* keys_out, cons
     if (key_bits == 0) key_bits = width;
     if (key_bits < 1 || key_bits > width) return RS_ERR_INVALID_ARG;
     if (xf.active() && key_bits != width) return RS_ERR_INVALID_ARG;  // typed keys use every bit
+    if (xf.active() && cfg) return RS_ERR_UNSUPPORTED;                 // typed kernels: default shapes only
     if ((vals_in == nullptr) != (vals_out == nullptr)) return RS_ERR_INVALID_ARG;
     if (n > RS_MAX_KEYS) return RS_ERR_INVALID_ARG;
     const bool vals = vals_in != nullptr;
@@ -269,7 +281,7 @@ rs_status radix_sort_xf(int key_bytes, const void* keys_in, void* keys_out, cons
         pp.xf = xf;
         pp.xf_in = xf.active() && p == 0;
         pp.xf_out = xf.active() && p == P - 1;
-        cudaError_t e = var->launch(pp, stream);
+        cudaError_t e = xf.active() ? var->launch_typed(pp, stream) : var->launch(pp, stream);
         if (e != cudaSuccess) return RS_ERR_CUDA;
         src_k = dst_k;
         src_v = dst_v;

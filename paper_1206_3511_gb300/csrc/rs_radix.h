@@ -16,11 +16,23 @@ struct Variant {
     int items;
     int tile_keys;
     cudaError_t (*launch)(const PassParams<RadixDigit>&, cudaStream_t);
+    cudaError_t (*launch_typed)(const PassParams<RadixDigit>&, cudaStream_t);  // typed keys; null if not compiled
     size_t (*smem_bytes)(int digit_bits);
 };
 
 // Shared memory a block may use on sm_103a (opt-in maximum).
 constexpr size_t kMaxSmemPerBlock = 227 * 1024;
+
+// The largest shared memory a scatter-pass shape needs over the digit widths
+// it can run (those whose tables fit in kMaxSmemPerBlock): the value to opt
+// the kernel in to.
+template <typename Shape>
+size_t max_fitting_pass_smem() {
+    size_t most = 0;
+    for (int D = kMinDigitBits; D <= kMaxDigitBits; ++D)
+        if (Shape::smem_bytes(D) <= kMaxSmemPerBlock && Shape::smem_bytes(D) > most) most = Shape::smem_bytes(D);
+    return most;
+}
 
 // Byte offsets of the regions of a radix-sort workspace.
 struct RadixLayout {

@@ -20,7 +20,7 @@ template <typename KeyT, bool VALS>
 struct SegShape;
 template <>
 struct SegShape<uint32_t, false> {
-    static constexpr int kBlock = 256, kItems = 18, kMinB = 4, kTile = kBlock * kItems;
+    static constexpr int kBlock = 384, kItems = 16, kMinB = 3, kTile = kBlock * kItems;
 };
 template <>
 struct SegShape<uint32_t, true> {
@@ -44,10 +44,11 @@ cudaError_t launch_seg_pass(const SegPassParams<DigitOp>& sp, size_t grid, cudaS
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
         attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)Shape::smem_bytes(kMaxDigitBits));
+                                        (int)max_fitting_pass_smem<Shape>());
     });
     if (attr_err != cudaSuccess) return attr_err;
     const size_t smem = Shape::smem_bytes(sp.base.digit_bits);
+    if (smem > max_fitting_pass_smem<Shape>()) return cudaErrorInvalidValue;
     grid = std::min<size_t>(grid, (size_t)resident_grid(kern, S::kBlock, smem));
     KernelScope scope("onesweep_seg_pass", s);
     kern<<<(unsigned)(grid ? grid : 1), S::kBlock, smem, s>>>(sp);

@@ -1,0 +1,71 @@
+"""The multi-process path of the benchmark on CPU (gloo, two ranks): the
+job's time is the slowest rank's, the job's rate counts every rank's keys,
+and every rank sorts its own seeded inputs (replicas, weak scaling)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+
+    try:
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+        env = bench._dist_env()
+        # rank r took (r + 1) ms for the sort and (10 - r) ms end to end
+        times = bench.max_over_ranks([rank + 1.0, 10.0 - rank])
+        keys, _ = bench.make_keys("radix_u32_1m", 1000, seed=env[1])
+        q.put((rank, env, times, keys.tolist()))
+        dist.barrier()
+        dist.destroy_process_group()
+    except Exception as e:  # reported to the parent
+        q.put((rank, "error", repr(e), None))
+
+
+def test_two_gloo_ranks_take_the_slowest_time_and_sort_their_own_inputs():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = {}
+    for _ in range(2):
+        rank, env, times, keys = q.get(timeout=120)
+        assert env != "error", times
+        out[rank] = (env, times, keys)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out[0][0] == (2, 0, 0) and out[1][0] == (2, 1, 1)
+    assert out[0][1] == [2.0, 10.0] and out[1][1] == [2.0, 10.0]  # max over ranks on every rank
+    assert out[0][2] != out[1][2]  # each rank's own seeded keys
+
+
+def test_job_rate_counts_every_rank():
+    import bench
+
+    # 2 ranks x 100M keys in 2 ms (the slowest rank) = 100 Gkeys/s for the job
+    assert bench.job_rate(100_000_000, 2, 2.0) == pytest.approx(100.0)
+    assert bench.job_rate(100_000_000, 1, 2.0) == pytest.approx(50.0)
+
+
+def test_single_process_max_is_identity():
+    import bench
+
+    assert bench.max_over_ranks([1.5, 2.5]) == [1.5, 2.5]
+    assert np.isfinite(bench.job_rate(1, 1, 1.0))

@@ -44,8 +44,10 @@ def test_small_config_1m_uniform_31bit(rs, oracle):
     _check(rs, oracle, keys, None, 31, what="1M uniform key_bits=31")
 
 
-# around the single-block limit (4096 keys) and the u32 scatter tile (4608 keys)
-TILE_SIZES = [0, 1, 2, 3, 31, 33, 3840, 4095, 4096, 4097, 4607, 4608, 4609, 2 * 4608 + 7, 65537, (1 << 20) + 3]
+# around the single-block limit (4096 keys) and the u32 scatter tiles (6144 keys
+# keys-only, 3072 with values; 4608 for the 256x18 shape)
+TILE_SIZES = [0, 1, 2, 3, 31, 33, 3840, 4095, 4096, 4097, 4607, 4608, 4609, 6143, 6144, 6145, 2 * 6144 + 7,
+              65537, (1 << 20) + 3]
 
 
 @pytest.mark.parametrize("n", TILE_SIZES)

@@ -36,7 +36,8 @@ def _check(rs, oracle, keys, sizes, vals=None, key_bits=0, in_place=False, what=
         assert_same(gv, wv, what + " values")
 
 
-EDGE_SIZES = [0, 1, 2, 3, 0, 255, 256, 4095, 4096, 4097, 4608, 4609, 9217, 70_001, 0, 1, 3072, 3073, 200_000]
+EDGE_SIZES = [0, 1, 2, 3, 0, 255, 256, 4095, 4096, 4097, 4608, 4609, 6143, 6144, 6145, 9217, 12289, 70_001, 0, 1,
+              3072, 3073, 200_000]
 
 
 @pytest.mark.parametrize("kb,with_values", [(4, False), (4, True), (8, False), (8, True)])
