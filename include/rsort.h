@@ -165,10 +165,11 @@ RS_API rs_status rs_sort_typed(int key_kind, int key_bytes, int descending, cons
  * Bucket sort, Sec. 2.3 Algorithm 2: every key goes to bucket
  *     b(k) = floor((k - min_key) * num_buckets / (max_key - min_key + 1))
  * (exact; the paper's n * A[i] / M with an inclusive key range), in input
- * order; every bucket is sorted (insertion sort, Sec. 2.2 Algorithm 1, for
- * buckets of up to 48 keys, a stable radix sort of the bucket's key range for
- * larger ones); the buckets are concatenated in bucket order.  The result is
- * the stable sort of the keys, identical to rs_sort_*.
+ * order; every bucket is sorted (buckets of up to 48 keys by a stable rank
+ * sort that makes insertion sort's comparisons, Sec. 2.2 Algorithm 1, for all
+ * keys at once; larger ones by a stable radix sort of the bucket's key
+ * range); the buckets are concatenated in bucket order.  The result is the
+ * stable sort of the keys, identical to rs_sort_*.
  * min_key > max_key: the bounds are the keys' own minimum and maximum,
  * computed on the device.  Otherwise every key must lie in [min_key,
  * max_key]; a key outside is reported as RS_ERR_KEY_RANGE by rs_get_status()
@@ -183,6 +184,21 @@ RS_API rs_status bs_sort_u32(const uint32_t* keys_in, uint32_t* keys_out, const 
 RS_API rs_status bs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
                              uint32_t* vals_out, size_t n, uint64_t min_key, uint64_t max_key, size_t num_buckets,
                              void* ws, size_t ws_bytes, rs_stream_t stream);
+
+/* The bucket counts of Algorithm 2's insert step: d_counts[b] = the number of
+ * keys with b(k) = b (the formula above), for b in [0, num_buckets).
+ * d_counts: DEVICE array of num_buckets uint32, overwritten.  Requires
+ * min_key <= max_key and 1 <= num_buckets <= 2^32; a key outside [min_key,
+ * max_key] is not counted and is reported as RS_ERR_KEY_RANGE by
+ * rs_get_status().  Workspace: at least 1024 bytes (any bucket-sort
+ * workspace will do).  One global atomic per key: a building block and a
+ * check of the bucket function, not a fast path. */
+RS_API rs_status bs_bucket_counts_u32(const uint32_t* keys, size_t n, uint32_t min_key, uint32_t max_key,
+                                      size_t num_buckets, uint32_t* d_counts, void* ws, size_t ws_bytes,
+                                      rs_stream_t stream);
+RS_API rs_status bs_bucket_counts_u64(const uint64_t* keys, size_t n, uint64_t min_key, uint64_t max_key,
+                                      size_t num_buckets, uint32_t* d_counts, void* ws, size_t ws_bytes,
+                                      rs_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Building blocks: one step of the radix path each.

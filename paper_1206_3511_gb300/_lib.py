@@ -89,6 +89,8 @@ SIGNATURES: dict[str, tuple] = {
     "rs_sort_segmented_u32": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P]),
     "rs_sort_segmented_u64": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P]),
     "rs_sort_typed": (_I, [_I, _I, _I, _P, _P, _P, _P, _SZ, _P, _SZ, _P]),
+    "bs_bucket_counts_u32": (_I, [_P, _SZ, _c.c_uint32, _c.c_uint32, _SZ, _P, _P, _SZ, _P]),
+    "bs_bucket_counts_u64": (_I, [_P, _SZ, _c.c_uint64, _c.c_uint64, _SZ, _P, _P, _SZ, _P]),
     "rs_plan_create": (_I, [_c.POINTER(RsPlanDesc), _c.POINTER(_c.c_void_p)]),
     "rs_plan_launch": (_I, [_P, _P]),
     "rs_plan_info": (_I, [_P, _c.POINTER(RsConfig), _c.POINTER(_c.c_size_t), _c.POINTER(_c.c_float)]),
@@ -274,6 +276,16 @@ def rs_sort_segmented_u64(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, n
                           stream=None) -> int:
     return _call("rs_sort_segmented_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out),
                  ptr(d_seg_offsets), nseg, n_total, key_bits, ptr(ws), ws_bytes, stream_handle(stream))
+
+
+def bs_bucket_counts_u32(keys, n, min_key, max_key, num_buckets, d_counts, ws, ws_bytes, stream=None) -> int:
+    return _call("bs_bucket_counts_u32", ptr(keys), n, min_key, max_key, num_buckets, ptr(d_counts), ptr(ws), ws_bytes,
+                 stream_handle(stream))
+
+
+def bs_bucket_counts_u64(keys, n, min_key, max_key, num_buckets, d_counts, ws, ws_bytes, stream=None) -> int:
+    return _call("bs_bucket_counts_u64", ptr(keys), n, min_key, max_key, num_buckets, ptr(d_counts), ptr(ws), ws_bytes,
+                 stream_handle(stream))
 
 
 RS_KEY_UINT, RS_KEY_INT, RS_KEY_FLOAT = 0, 1, 2

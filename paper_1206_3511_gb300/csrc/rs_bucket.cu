@@ -72,9 +72,30 @@ __global__ void k_bucket_params(BucketParams* bp, const unsigned long long* mm, 
     p.nb = nb;
     p.range = range;
     p.recip = (key_bytes == 4 && range != 0) ? (~0ull / range) : 0ull;
+    p.mul_ok = (key_bytes == 4 && range != 0 && nb < range) ? 1u : 0u;
+    p.mul = p.mul_ok ? (uint64_t)(((unsigned __int128)nb << 64) / range) : 0ull;
     p.bbits = nb > 1 ? 64u - __clzll(nb - 1) : 0u;
     p.valid = 1u;
     *bp = p;
+}
+
+// Count of every bucket (exact bucket ids, Algorithm 2's insert step without
+// the lists): one global atomic per key; keys outside [min, max] are
+// reported in the status word.
+template <typename KeyT>
+__global__ void __launch_bounds__(256) k_bucket_counts(const KeyT* __restrict__ keys, size_t n,
+                                                       const BucketParams* bpp, uint32_t* counts, WsHeader* hdr) {
+    const BucketParams bp = load_bucket_params(bpp);
+    bool bad = false;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const KeyT k = keys[i];
+        if ((uint64_t)k < bp.min || (uint64_t)k > bp.max) {
+            bad = true;
+            continue;
+        }
+        atomicAdd(&counts[bucket_of(bp, k)], 1u);
+    }
+    if (bad) set_device_error(hdr, RS_ERR_KEY_RANGE, blockIdx.x);
 }
 
 // Range check of the declared bounds in the level-1 counting kernel.
@@ -637,6 +658,35 @@ static rs_status bucket_impl(int key_bytes, const void* keys_in, void* keys_out,
                                                  max_key, nb, ws, ws_bytes, stream);
 }
 
+static rs_status bucket_counts_impl(int key_bytes, const void* keys, size_t n, uint64_t min_key, uint64_t max_key,
+                                    size_t nb, uint32_t* counts, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (min_key > max_key || nb == 0 || nb > ((size_t)1 << 32) || !counts || ((uintptr_t)counts % 4))
+        return RS_ERR_INVALID_ARG;
+    if (n > RS_MAX_KEYS || (n && !keys) || ((uintptr_t)keys % key_bytes)) return RS_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws % 256)) return RS_ERR_WORKSPACE;
+    if (ws_bytes < 512 + sizeof(BucketParams)) return RS_ERR_WORKSPACE;
+    unsigned char* base = static_cast<unsigned char*>(ws);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(base);
+    BucketParams* bp = reinterpret_cast<BucketParams*>(base + 256);
+    RS_CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(WsHeader), stream));
+    RS_CUDA_TRY(cudaMemsetAsync(counts, 0, nb * 4, stream));
+    {
+        KernelScope scope("bucket_params", stream);
+        k_bucket_params<<<1, 32, 0, stream>>>(bp, nullptr, min_key, max_key, nb, key_bytes);
+        if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
+    }
+    if (n == 0) return RS_OK;
+    const size_t grid = std::min<size_t>((n + 255) / 256, (size_t)device_sm_count() * 8);
+    KernelScope scope("bucket_counts", stream);
+    if (key_bytes == 4)
+        k_bucket_counts<uint32_t><<<(unsigned)grid, 256, 0, stream>>>(static_cast<const uint32_t*>(keys), n, bp,
+                                                                     counts, hdr);
+    else
+        k_bucket_counts<uint64_t><<<(unsigned)grid, 256, 0, stream>>>(static_cast<const uint64_t*>(keys), n, bp,
+                                                                     counts, hdr);
+    return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
 }  // namespace rs
 
 using namespace rs;
@@ -655,6 +705,16 @@ rs_status bs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_
                       rs_stream_t stream) {
     return bucket_impl(8, keys_in, keys_out, vals_in, vals_out, n, min_key, max_key, num_buckets, ws, ws_bytes,
                        stream);
+}
+
+rs_status bs_bucket_counts_u32(const uint32_t* keys, size_t n, uint32_t min_key, uint32_t max_key, size_t num_buckets,
+                               uint32_t* d_counts, void* ws, size_t ws_bytes, rs_stream_t stream) {
+    return bucket_counts_impl(4, keys, n, min_key, max_key, num_buckets, d_counts, ws, ws_bytes, stream);
+}
+
+rs_status bs_bucket_counts_u64(const uint64_t* keys, size_t n, uint64_t min_key, uint64_t max_key, size_t num_buckets,
+                               uint32_t* d_counts, void* ws, size_t ws_bytes, rs_stream_t stream) {
+    return bucket_counts_impl(8, keys, n, min_key, max_key, num_buckets, d_counts, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

@@ -19,8 +19,11 @@ struct BucketParams {
     uint64_t nb;     // number of buckets
     uint64_t range;  // max - min + 1; 0 stands for 2^64
     uint64_t recip;  // floor((2^64 - 1) / range) when range <= 2^32
+    uint64_t mul;    // floor(2^64 * nb / range) for 32-bit keys when nb < range (mul_ok)
     uint32_t bbits;  // bit length of nb - 1 (0 when nb == 1)
     uint32_t valid;  // 1 once the parameters are set
+    uint32_t mul_ok;
+    uint32_t pad;
 };
 
 // Exact floor((k - min) * nb / range).
@@ -30,8 +33,18 @@ struct BucketParams {
 //   Granlund & Montgomery 1994), and the remainder test corrects it.
 //   64-bit keys: 128-bit product divided exactly; range 2^64 is a plain
 //   high product.
+//   32-bit keys with nb < range take a cheaper estimate first: with
+//   m = floor(2^64 nb / range), e = floor(t m / 2^64) (t = k - min, a 32 x 64
+//   bit high product) is the quotient or one below it (m is short of
+//   2^64 nb / range by less than 1 and t < 2^32), and one exact comparison
+//   (e + 1) * range <= t * nb settles which.
 __device__ __forceinline__ uint64_t bucket_of(const BucketParams& bp, uint32_t k) {
-    const uint64_t x = (uint64_t)(k - (uint32_t)bp.min) * bp.nb;
+    const uint32_t t = k - (uint32_t)bp.min;
+    if (bp.mul_ok) {
+        const uint64_t e = ((uint64_t)t * (uint32_t)(bp.mul >> 32) + __umulhi(t, (uint32_t)bp.mul)) >> 32;
+        return e + (uint64_t)((e + 1) * bp.range <= (uint64_t)t * bp.nb);
+    }
+    const uint64_t x = (uint64_t)t * bp.nb;
     uint64_t q = __umul64hi(x, bp.recip);
     uint64_t r = x - q * bp.range;
 #pragma unroll
@@ -57,8 +70,11 @@ __device__ __forceinline__ BucketParams load_bucket_params(const BucketParams* p
     b.nb = __ldcg(&p->nb);
     b.range = __ldcg(&p->range);
     b.recip = __ldcg(&p->recip);
+    b.mul = __ldcg(&p->mul);
     b.bbits = __ldcg(&p->bbits);
     b.valid = __ldcg(&p->valid);
+    b.mul_ok = __ldcg(&p->mul_ok);
+    b.pad = 0;
     return b;
 }
 

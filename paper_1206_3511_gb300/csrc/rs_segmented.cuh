@@ -210,6 +210,7 @@ struct LocalSmem {
         b += 2 * (size_t)cap * sizeof(KeyT);          // key buffers
         if (VALS) b += 2 * (size_t)cap * 4;           // value buffers
         b += 256 * 4 * 2 + (kWarps + 1 + 3) * 4 + 16; // starts, counts, scan scratch, flags
+        b += (size_t)cap;                             // bucket of each staged key (bucket mode)
         return b;
     }
 };
@@ -219,7 +220,7 @@ struct LocalSmem {
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename DFun>
 __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, KeyT* kb, uint32_t* vb, uint32_t m,
                                            unsigned long long* s_tab, uint32_t* s_start, uint32_t* s_cnt,
-                                           uint32_t* s_scan, DFun dfun) {
+                                           uint32_t* s_scan, DFun dfun, uint8_t* s_dig = nullptr) {
     constexpr int kWarps = BLOCK / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t i = tid; i < (uint32_t)kWarps * 256; i += BLOCK) s_tab[i] = 0ull;
@@ -269,6 +270,7 @@ __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, K
             if (pos < m) {
                 kb[pos] = ka[idx];
                 if (VALS) vb[pos] = va[idx];
+                if (s_dig) s_dig[pos] = (uint8_t)(dr[i] >> 16);
             }
         }
     }
@@ -304,6 +306,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
     uint32_t* s_cnt = s_start + 256;
     uint32_t* s_scan = s_cnt + 256;
     uint32_t* s_flag = s_scan + kWarps + 1;
+    uint8_t* s_dig = reinterpret_cast<uint8_t*>(s_flag + 4);
 
     if (bfn.active()) bfn.init();
     const uint32_t nseg = lp.count ? *lp.count : 1u;
@@ -330,32 +333,37 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
             __syncthreads();
             if (span <= 256) {
                 local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[0], vbuf[0], kbuf[1], vbuf[1], m, s_tab, s_start, s_cnt, s_scan,
-                                                     [&](KeyT k) { return (uint32_t)(bfn.bucket(k) - b_lo); });
+                                                     [&](KeyT k) { return (uint32_t)(bfn.bucket(k) - b_lo); }, s_dig);
                 cur = 1;
                 for (uint32_t d = threadIdx.x; d < 256; d += BLOCK)
                     if (s_cnt[d] > kInsertionMax) *s_flag = 1u;
                 __syncthreads();
                 if (*s_flag == 0u) {
                     by_keys = false;
-                    // Algorithm 1 on every bucket: thread d sorts bucket d in place
-                    for (uint32_t d = threadIdx.x; d < 256; d += BLOCK) {
-                        KeyT* A = kbuf[1] + s_start[d];
-                        uint32_t* V = vbuf[1] + (VALS ? s_start[d] : 0);
-                        const uint32_t len = s_cnt[d];
-                        for (uint32_t j = 1; j < len; ++j) {
-                            const KeyT key = A[j];
-                            uint32_t val = 0;
-                            if (VALS) val = V[j];
-                            uint32_t i = j;
-                            while (i > 0 && A[i - 1] > key) {
-                                A[i] = A[i - 1];
-                                if (VALS) V[i] = V[i - 1];
-                                --i;
-                            }
-                            A[i] = key;
-                            if (VALS) V[i] = val;
+                    // sort every bucket: each key's place in its bucket is the
+                    // number of the bucket's keys that precede it in the
+                    // stable order (smaller, or equal and earlier in input
+                    // order, which the counting pass kept) -- the comparisons
+                    // of insertion sort (Algorithm 1), made for all keys at
+                    // once instead of one bucket per thread
+                    for (uint32_t j = threadIdx.x; j < m; j += BLOCK) {
+                        const KeyT key = kbuf[1][j];
+                        const uint32_t d = s_dig[j];
+                        const uint32_t lo = s_start[d], hi = lo + s_cnt[d];
+                        uint32_t r = 0, q = lo;
+                        for (; q + 4 <= hi; q += 4) {  // four independent reads per step
+                            const KeyT o0 = kbuf[1][q], o1 = kbuf[1][q + 1], o2 = kbuf[1][q + 2], o3 = kbuf[1][q + 3];
+                            r += ((o0 < key) | ((o0 == key) & (q < j))) + ((o1 < key) | ((o1 == key) & (q + 1 < j))) +
+                                 ((o2 < key) | ((o2 == key) & (q + 2 < j))) + ((o3 < key) | ((o3 == key) & (q + 3 < j)));
                         }
+                        for (; q < hi; ++q) {
+                            const KeyT other = kbuf[1][q];
+                            r += (other < key) | ((other == key) & (q < j));
+                        }
+                        kbuf[0][lo + r] = key;
+                        if (VALS) vbuf[0][lo + r] = vbuf[1][j];
                     }
+                    cur = 0;
                     __syncthreads();
                 }
             } else {

@@ -139,3 +139,54 @@ def test_full_size_100m(rs, oracle, dist):
     gk, _ = _bucket(rs, keys, None, lo, hi, 0)
     torch.cuda.empty_cache()
     assert_same(gk, oracle.radix_sort(keys), f"100M {synth.DISTS[dist]}")
+
+
+def _edge_keys(lo, hi, nb, count, seed, dtype):
+    """Keys uniform in [lo, hi] plus the keys next to bucket boundaries: the
+    first key of bucket b is lo + ceil(b * R / nb), R = hi - lo + 1."""
+    R = hi - lo + 1
+    if R <= 2**32:
+        body = [lo + int(x) for x in synth.uniform_below(count, R, seed, 70)] if R < 2**32 else \
+            [lo + int(x) for x in synth.u32(count, seed, 70)]
+    else:
+        body = [lo + (int(x) % R) for x in synth.u64(count, seed, 70)]
+    edges = []
+    for b in [0, 1, 2, nb // 3, nb // 2, nb - 2, nb - 1] + [int(x) for x in synth.uniform_below(64, nb, seed, 71)]:
+        if 0 <= b < nb:
+            first = lo + -(-b * R // nb)
+            edges += [first - 1, first, first + 1]
+    edges = [e for e in edges if lo <= e <= hi] + [lo, hi]
+    return np.array(body + edges, dtype=dtype)
+
+
+@pytest.mark.parametrize("kb,lo,hi,nb", [
+    (4, 0, 2**32 - 1, 6_250_000), (4, 0, 2**31 - 1, 62_500), (4, 10, 12, 7), (4, 5, 5, 1),
+    (4, 0, 2**20 - 1, 300_000), (4, 1000, 10**9, 3), (4, 123, 2**32 - 1, 2**20 + 7), (4, 0, 999, 1000),
+    (8, 0, 2**64 - 1, 12_345), (8, 0, 2**40 - 1, 1 << 22), (8, 7, 2**63, 2**20), (8, 2**63, 2**63 + 5, 9)])
+def test_bucket_counts_are_exact(rs, oracle, kb, lo, hi, nb):
+    """b(k) = floor((k - min) * nb / (max - min + 1)) on the GPU, checked
+    bucket by bucket against the oracle's counts, with keys on both sides of
+    bucket boundaries."""
+    import torch
+
+    dt = np.uint32 if kb == 4 else np.uint64
+    keys = _edge_keys(lo, hi, nb, 200_000, 17 + nb % 89, dt)
+    kd = to_dev(keys)
+    counts = torch.empty(nb, dtype=torch.int32, device="cuda")
+    ws = rs.workspace(4096)
+    fn = rs.bs_bucket_counts_u32 if kb == 4 else rs.bs_bucket_counts_u64
+    assert fn(kd, keys.size, lo, hi, nb, counts, ws, ws.numel()) == 0
+    assert rs.get_status(ws) == 0
+    got = from_dev(counts, np.uint32).astype(np.uint64)
+    assert_same(got, oracle.bucket_counts(keys, lo, hi, nb), f"counts kb={kb} [{lo},{hi}] nb={nb}")
+
+
+def test_bucket_counts_report_keys_outside_the_range(rs):
+    import torch
+
+    keys = np.array([5, 6, 7, 100, 8], np.uint32)
+    counts = torch.empty(4, dtype=torch.int32, device="cuda")
+    ws = rs.workspace(4096)
+    assert rs.bs_bucket_counts_u32(to_dev(keys), 5, 5, 8, 4, counts, ws, ws.numel()) == 0
+    assert rs.get_status(ws) == 3  # RS_ERR_KEY_RANGE
+    assert from_dev(counts, np.uint32).tolist() == [1, 1, 1, 1]
