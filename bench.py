@@ -337,8 +337,11 @@ def run_ours(args):
         nbytes = rs.rs_workspace_bytes(rs.RS_ALGO_BUCKET, kb, has_v, n, 0, nb, 0)
         bfn = rs.bs_sort_u32 if kb == 4 else rs.bs_sort_u64
 
+        def sort_into(kin, kout, vin, vout, ws, strm):
+            return bfn(kin, kout, vin, vout, n, lo, hi, nb, ws, ws.numel(), strm)
+
         def call(ws):
-            return bfn(d_keys, d_out, d_vals, d_outv, n, lo, hi, nb, ws, ws.numel(), stream)
+            return sort_into(d_keys, d_out, d_vals, d_outv, ws, stream)
     else:
         if args.autotune or wl in AUTOTUNED:
             # the plan's autotuner picks the kernel shape and digit width; the
@@ -351,8 +354,11 @@ def run_ours(args):
             nbytes = rs.rs_workspace_bytes(rs.RS_ALGO_RADIX, kb, has_v, n, key_bits, 0, 0)
         rfn = rs.rs_sort_u32_ex if kb == 4 else rs.rs_sort_u64_ex
 
+        def sort_into(kin, kout, vin, vout, ws, strm):
+            return rfn(kin, kout, vin, vout, n, key_bits, ws, ws.numel(), strm, tuned)
+
         def call(ws):
-            return rfn(d_keys, d_out, d_vals, d_outv, n, key_bits, ws, ws.numel(), stream, tuned)
+            return sort_into(d_keys, d_out, d_vals, d_outv, ws, stream)
     ws = rs.workspace(nbytes, d_keys.device)
 
     def step():
@@ -397,28 +403,82 @@ def run_ours(args):
         a = chk.cpu().numpy().view(np.uint64)
     assert np.all(a[1:] >= a[:-1]), "bench output not sorted"
 
-    # end to end through the public API: pinned host keys -> device -> sort -> host
+    # end to end through the public API: every step uploads its keys (and
+    # values) from pinned host memory, sorts, and downloads the sorted keys
+    # (and values).  Serial: one stream, nothing overlaps.
     h_out = torch.empty_like(h_keys).pin_memory()
+    h_outv = torch.empty_like(h_vals).pin_memory() if has_v else None
     e2e_steps = max(3, min(args.steps, 20))
-    for _ in range(2):
-        d_keys.copy_(h_keys, non_blocking=True)
-        step()
-        h_out.copy_(d_out, non_blocking=True)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
+
+    def serial_step():
         d_keys.copy_(h_keys, non_blocking=True)
         if has_v:
             d_vals.copy_(h_vals, non_blocking=True)
         step()
         h_out.copy_(d_out, non_blocking=True)
+        if has_v:
+            h_outv.copy_(d_outv, non_blocking=True)
+
+    for _ in range(2):
+        serial_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        serial_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_serial_ms = e0.elapsed_time(e1)
 
-    ms, e2e_ms = max_over_ranks([ms, e2e_ms], device=dev)
+    # Pipelined: the same steps through three buffer slots with uploads,
+    # sorts and downloads on three streams, so that step i+1's upload and
+    # step i-1's download run while step i sorts (how a stream of sort jobs
+    # is served).  A slot is reused only after its last download finished.
+    S = 3
+    up, comp, down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    slots = [{"k": torch.empty_like(d_keys), "o": torch.empty_like(d_keys),
+              "v": torch.empty_like(d_vals) if has_v else None, "ov": torch.empty_like(d_vals) if has_v else None,
+              "hk": torch.empty_like(h_keys).pin_memory(),
+              "hv": torch.empty_like(h_vals).pin_memory() if has_v else None} for _ in range(S)]
+    ev = {x: [torch.cuda.Event() for _ in range(S)] for x in ("up", "comp", "down")}
+
+    def pipe_step(i):
+        j = i % S
+        sl = slots[j]
+        if i >= S:
+            up.wait_event(ev["down"][j])
+        with torch.cuda.stream(up):
+            sl["k"].copy_(h_keys, non_blocking=True)
+            if has_v:
+                sl["v"].copy_(h_vals, non_blocking=True)
+        ev["up"][j].record(up)
+        comp.wait_event(ev["up"][j])
+        rc = sort_into(sl["k"], sl["o"], sl["v"], sl["ov"], ws, comp)
+        if rc:
+            raise rs.SortError(rc, "sort")
+        ev["comp"][j].record(comp)
+        down.wait_event(ev["comp"][j])
+        with torch.cuda.stream(down):
+            sl["hk"].copy_(sl["o"], non_blocking=True)
+            if has_v:
+                sl["hv"].copy_(sl["ov"], non_blocking=True)
+        ev["down"][j].record(down)
+
+    for i in range(S):
+        pipe_step(i)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(up)
+    for i in range(e2e_steps):
+        pipe_step(S + i)
+    p1.record(down)
+    torch.cuda.synchronize()
+    e2e_ms = p0.elapsed_time(p1)
+    last = slots[(S + e2e_steps - 1) % S]["hk"]
+    assert torch.equal(last, h_out), "pipelined result differs from the serial one"
+
+    ms, e2e_ms, e2e_serial_ms = max_over_ranks([ms, e2e_ms, e2e_serial_ms], device=dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -426,8 +486,9 @@ def run_ours(args):
 
     value = job_rate(n * args.steps, world, ms)
     e2e_value = job_rate(n * e2e_steps, world, e2e_ms)
+    e2e_serial = job_rate(n * e2e_steps, world, e2e_serial_ms)
     h2d = n * kb + (n * 4 if has_v else 0)
-    d2h = n * kb
+    d2h = n * kb + (n * 4 if has_v else 0)
 
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
@@ -509,7 +570,9 @@ def run_ours(args):
                                      "chosen_by": "autotuner"} if algo == "radix" and tuned else None),
                    "l2": "inputs larger than L2 (%d MB keys vs 129 MB L2), no flush" % (n * kb // 2**20)},
         "clocks": clocks, "gpu_launches": launches, "roofline": roofline, "whole_sort": whole,
-        "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "mode": "pipelined: 3 buffer slots; uploads, sorts and downloads on three streams overlap across steps",
+                "serial_value": e2e_serial, "steps": e2e_steps},
         "cpu_baseline": cpu, "context": lib,
     }
     print(json.dumps(line), flush=True)
@@ -946,6 +1009,7 @@ def run_served(args):
             _, r = srv.result(tickets[i])
             done.append(r.t_done_ms)
             lat.append(r.t_done_ms - (t0 + arr[i]))
+            srv.release(tickets[i])
         st = srv.stats()
         srv.close()
         span_ms = max(done) - t0

@@ -355,6 +355,11 @@ RS_API rs_status rs_server_poll(rs_server* s, uint64_t ticket, rs_result* out);
 /* Wait up to timeout_ms (< 0: forever) for a request; its status, or
  * RS_ERR_NOT_READY on timeout. */
 RS_API rs_status rs_server_wait(rs_server* s, uint64_t ticket, int timeout_ms);
+/* Forget a finished request: its record (status and times) is freed and the
+ * ticket becomes unknown (later calls on it return RS_ERR_INVALID_ARG).  A
+ * server keeps every record until it is released or destroyed.
+ * RS_ERR_NOT_READY if the request is still queued or running. */
+RS_API rs_status rs_server_release(rs_server* s, uint64_t ticket);
 RS_API rs_status rs_server_get_stats(rs_server* s, rs_server_stats* out);
 /* Stop accepting requests; finish (cancel_pending = 0) or cancel (nonzero:
  * queued requests end with RS_ERR_SHUTDOWN) the queue, wait for launches in

@@ -14,7 +14,7 @@ bits are sorted as unsigned).  Values are 32-bit (uint32 or int32).
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (bs_bucket_counts_u32, bs_bucket_counts_u64, RS_KEY_FLOAT, RS_KEY_INT, RS_KEY_UINT, rs_sort_typed, RS_PLAN_BUCKET, RS_PLAN_RADIX, RS_PLAN_SEGMENTED, RsPlanDesc, rs_plan_create, rs_plan_destroy,
+from ._lib import (rs_server_release, bs_bucket_counts_u32, bs_bucket_counts_u64, RS_KEY_FLOAT, RS_KEY_INT, RS_KEY_UINT, rs_sort_typed, RS_PLAN_BUCKET, RS_PLAN_RADIX, RS_PLAN_SEGMENTED, RsPlanDesc, rs_plan_create, rs_plan_destroy,
                    rs_plan_info, rs_plan_launch, RsRequest, RsResult, RsServerConfig, RsServerStats, rs_server_create, rs_server_destroy,
                    rs_server_get_stats, rs_server_poll, rs_server_submit, rs_server_wait, bs_sort_u32, bs_sort_u64, rs_segmented_workspace_bytes, rs_sort_segmented_u32, rs_sort_segmented_u64,
                    RS_ALGO_BUCKET, RS_ALGO_RADIX, STATUS, RsConfig, load, rs_config_count, rs_config_get,
@@ -25,17 +25,17 @@ from ._lib import (bs_bucket_counts_u32, bs_bucket_counts_u64, RS_KEY_FLOAT, RS_
 
 __all__ = [
     "SortError", "load", "sort", "counting_pass", "digit_counts", "workspace", "get_status", "key_bytes_of",
-    "rs_sort_u32", "rs_sort_u64", "rs_sort_u32_ex", "rs_sort_u64_ex", "rs_digit_counts_u32",
-    "rs_digit_counts_u64", "rs_counting_pass_u32", "rs_counting_pass_u64", "rs_get_status", "rs_set_debug",
-    "rs_status_string", "rs_version", "rs_workspace_bytes", "rs_workspace_bytes_cfg", "rs_default_config",
-    "rs_config_count", "rs_config_get", "RsConfig", "RS_ALGO_RADIX", "RS_ALGO_BUCKET", "STATUS",
-    "rs_profile_enable", "rs_profile_read", "rs_launch_count", "rs_sort_u32_noalloc",
-    "rs_segmented_workspace_bytes", "rs_sort_segmented_u32", "rs_sort_segmented_u64", "segmented_sort",
-    "bs_sort_u32", "bs_sort_u64", "bucket_sort", "Server", "Plan", "sort_typed", "rs_sort_typed", "bs_bucket_counts_u32", "bs_bucket_counts_u64", "RS_KEY_UINT",
-    "RS_KEY_INT", "RS_KEY_FLOAT", "RsPlanDesc", "rs_plan_create",
-    "rs_plan_destroy", "rs_plan_info", "rs_plan_launch", "RS_PLAN_RADIX", "RS_PLAN_BUCKET", "RS_PLAN_SEGMENTED", "RsRequest", "RsResult", "RsServerConfig",
-    "RsServerStats", "rs_server_create", "rs_server_destroy", "rs_server_get_stats", "rs_server_poll",
-    "rs_server_submit", "rs_server_wait",
+    "rs_sort_u32", "rs_sort_u64", "rs_sort_u32_ex", "rs_sort_u64_ex", "rs_digit_counts_u32", "rs_digit_counts_u64",
+    "rs_counting_pass_u32", "rs_counting_pass_u64", "rs_get_status", "rs_set_debug", "rs_status_string",
+    "rs_version", "rs_workspace_bytes", "rs_workspace_bytes_cfg", "rs_default_config", "rs_config_count",
+    "rs_config_get", "RsConfig", "RS_ALGO_RADIX", "RS_ALGO_BUCKET", "STATUS", "rs_profile_enable",
+    "rs_profile_read", "rs_launch_count", "rs_sort_u32_noalloc", "rs_segmented_workspace_bytes",
+    "rs_sort_segmented_u32", "rs_sort_segmented_u64", "segmented_sort", "bs_sort_u32", "bs_sort_u64",
+    "bucket_sort", "Server", "Plan", "sort_typed", "rs_sort_typed", "bs_bucket_counts_u32", "bs_bucket_counts_u64",
+    "RS_KEY_UINT", "RS_KEY_INT", "RS_KEY_FLOAT", "RsPlanDesc", "rs_plan_create", "rs_plan_destroy", "rs_plan_info",
+    "rs_plan_launch", "RS_PLAN_RADIX", "RS_PLAN_BUCKET", "RS_PLAN_SEGMENTED", "RsRequest", "RsResult",
+    "RsServerConfig", "RsServerStats", "rs_server_create", "rs_server_destroy", "rs_server_get_stats",
+    "rs_server_poll", "rs_server_submit", "rs_server_wait", "rs_server_release",
 ]
 
 
@@ -251,6 +251,11 @@ class Server:
 
     def result(self, ticket: int):
         return rs_server_poll(self.handle, ticket)
+
+    def release(self, ticket: int) -> int:
+        """Forget a finished request (rs_server_release)."""
+        self._keep.pop(ticket, None)
+        return rs_server_release(self.handle, ticket)
 
     def stats(self):
         return rs_server_get_stats(self.handle)

@@ -99,6 +99,7 @@ SIGNATURES: dict[str, tuple] = {
     "rs_server_submit": (_I, [_P, _c.POINTER(RsRequest), _c.POINTER(_c.c_uint64)]),
     "rs_server_poll": (_I, [_P, _c.c_uint64, _c.POINTER(RsResult)]),
     "rs_server_wait": (_I, [_P, _c.c_uint64, _I]),
+    "rs_server_release": (_I, [_P, _c.c_uint64]),
     "rs_server_get_stats": (_I, [_P, _c.POINTER(RsServerStats)]),
     "rs_server_destroy": (_I, [_P, _I]),
     "rs_sort_u32_noalloc": (_I, [_P, _P, _P, _P, _SZ, _I, _P]),
@@ -343,6 +344,10 @@ def rs_server_poll(server, ticket):
     r = RsResult()
     rc = _call("rs_server_poll", server, ticket, _c.byref(r))
     return rc, r
+
+
+def rs_server_release(server, ticket) -> int:
+    return _call("rs_server_release", server, ticket)
 
 
 def rs_server_wait(server, ticket, timeout_ms=-1) -> int:

@@ -438,6 +438,17 @@ rs_status rs_server_poll(rs_server* s, uint64_t ticket, rs_result* out) {
     return r.done ? r.status : RS_ERR_NOT_READY;
 }
 
+rs_status rs_server_release(rs_server* s, uint64_t ticket) {
+    if (!s) return RS_ERR_INVALID_ARG;
+    ServerImpl& m = s->impl;
+    std::lock_guard<std::mutex> lk(m.mu);
+    auto it = m.reqs.find(ticket);
+    if (it == m.reqs.end()) return RS_ERR_INVALID_ARG;
+    if (!it->second.done) return RS_ERR_NOT_READY;
+    m.reqs.erase(it);
+    return RS_OK;
+}
+
 rs_status rs_server_wait(rs_server* s, uint64_t ticket, int timeout_ms) {
     if (!s) return RS_ERR_INVALID_ARG;
     ServerImpl& m = s->impl;

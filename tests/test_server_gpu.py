@@ -153,3 +153,17 @@ def test_shutdown_cancels_queued_requests(rs):
     torch.cuda.synchronize()
     # 40 sorts of 8M keys one after another take far longer than this
     assert elapsed < 0.5, elapsed
+
+
+def test_released_requests_are_forgotten(rs):
+    import torch
+
+    keys = to_dev(synth.u32(10_000, 80, 0))
+    out = torch.empty_like(keys)
+    with rs.Server(pool_bytes=256 << 20, num_streams=2) as srv:
+        t = srv.submit(keys, out)
+        assert srv.wait(t, 60_000) == 0
+        assert srv.release(t) == 0
+        assert srv.release(t) == 1  # RS_ERR_INVALID_ARG: unknown ticket now
+        rc, _ = srv.result(t)
+        assert rc == 1
