@@ -117,6 +117,66 @@ def _dist_env():
     return ws, rank, local
 
 
+# Context only: a library radix sort (CUB's DeviceRadixSort::SortKeys, from
+# the CUDA toolkit's headers) of the same keys on the same GPU, compiled on
+# the fly into a temporary directory.
+_CUB_SRC = r"""
+#include <cub/device/device_radix_sort.cuh>
+#include <cstdint>
+extern "C" int cub_sort_keys_u32(const uint32_t* in, uint32_t* out, size_t n, void* tmp, size_t* tmp_bytes,
+                                 cudaStream_t s) {
+    return (int)cub::DeviceRadixSort::SortKeys(tmp, *tmp_bytes, in, out, (int)n, 0, 32, s);
+}
+"""
+
+
+def cub_context(d_keys, n, stream, reps=20):
+    """Gkeys/s of CUB's keys-only radix sort of d_keys (u32), or None."""
+    import ctypes
+    import shutil
+    import tempfile
+
+    import torch
+
+    try:
+        nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+        tmp = tempfile.mkdtemp(prefix="cubctx")
+        src, lib = os.path.join(tmp, "cub_sort.cu"), os.path.join(tmp, "libcubsort.so")
+        with open(src, "w") as f:
+            f.write(_CUB_SRC)
+        inc = [f"-I{d}" for d in ("/usr/local/cuda/include/cccl",) if os.path.isdir(d)]
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-O3", "-Xcompiler",
+                        "-fPIC", "-shared", *inc, "-o", lib, src], check=True, capture_output=True, timeout=300)
+        cub = ctypes.CDLL(lib)
+        cub.cub_sort_keys_u32.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_size_t), ctypes.c_void_p]
+        out = torch.empty_like(d_keys)
+        nbytes = ctypes.c_size_t(0)
+        if cub.cub_sort_keys_u32(d_keys.data_ptr(), out.data_ptr(), n, None, ctypes.byref(nbytes), None):
+            return None
+        tmpbuf = torch.empty(nbytes.value, dtype=torch.uint8, device=d_keys.device)
+
+        def run():
+            return cub.cub_sort_keys_u32(d_keys.data_ptr(), out.data_ptr(), n, tmpbuf.data_ptr(), ctypes.byref(nbytes),
+                                         stream.cuda_stream)
+
+        for _ in range(3):
+            if run():
+                return None
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            run()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        return {"value": n / (ms / 1e3) / 1e9, "unit": "Gkeys/s", "ms_per_sort": ms,
+                "note": "cub::DeviceRadixSort::SortKeys (CUDA toolkit), uint32 keys only, same keys and GPU"}
+    except Exception:
+        return None
+
+
 def max_over_ranks(values, device=None) -> list[float]:
     """Each value's maximum over all ranks (the job's time is its slowest
     rank's); the values themselves on a single process."""
@@ -547,8 +607,11 @@ def run_ours(args):
         torch.cuda.synchronize()
         lib_ms = c0.elapsed_time(c1) / reps
         lib = {"torch.sort": {"value": n / (lib_ms / 1e3) / 1e9, "unit": "Gkeys/s", "ms_per_sort": lib_ms,
-                              "note": "stable torch.sort of the keys as signed integers, keys only, same GPU"}}
+                              "note": "stable torch.sort of the keys as signed integers (returns indices too), "
+                                      "same GPU"}}
         del t_in
+        if kb == 4 and not has_v and key_bits == 32:
+            lib["cub.DeviceRadixSort.SortKeys"] = cub_context(d_keys, n, stream)
 
     cpu = None
     if not args.no_cpu_baseline:
