@@ -10,8 +10,9 @@
 //   level 2: partitions still larger than one block's shared memory are
 //            partitioned by the next (up to 8) bits with a segmented pass;
 //   leaves:  every partition of at most 4096 keys is sorted inside one block:
-//            a stable counting pass by exact bucket (the insert step) and an
-//            insertion sort of each bucket by one thread (Algorithm 1);
+//            a stable counting pass by exact bucket (the insert step), then
+//            each bucket sorted by a stable rank sort that makes the
+//            comparisons of insertion sort (Algorithm 1) for all keys at once;
 //   overflow: a partition that is still too large when the bucket bits run
 //            out (skewed keys) is radix-sorted on its keys relative to the
 //            lowest key its buckets can hold, using only the bits that span;
@@ -589,7 +590,7 @@ static rs_status bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const uint32
         k_copy_segments<KeyT><<<bins1, 256, 0, stream>>>(tmp_k, tmp_v, keys_out, vals_out, copyl, &h_leaf1->num_next);
         if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
     }
-    // b5: sort each bucket of the shared-memory partitions (Algorithm 1 per bucket)
+    // b5: sort each bucket of the shared-memory partitions
     rs_status st = enqueue_local_sorts(sizeof(KeyT), VALS, tmp_k, tmp_v, keys_out, vals_out, leaf1,
                                        &h_leaf1->num_small, bins1, bp, nullptr, stream);
     if (st != RS_OK) return st;

@@ -6,13 +6,14 @@
 //    prefixes, which are the counting sort's "number of smaller digits".
 //
 //  k_onesweep: one stable counting-sort pass (the placement loop of Algorithm
-//    3) done block-wise: each block takes the next tile (dynamic tile id),
-//    ranks its keys stably by digit in shared memory (warp multisplit with
-//    __match_any_sync, Adinets & Merrill, "Onesweep", arXiv:2206.01784),
-//    obtains the number of equal digits in all earlier tiles through a
-//    decoupled look-back over per-(tile, digit) status words, and writes each
-//    key to  digit_base[d] + (earlier tiles' d) + (rank inside the tile).
-//    The keys are read once and written once per pass.
+//    3) done block-wise, in the manner of Onesweep (Adinets & Merrill,
+//    arXiv:2206.01784): each block takes the next tile (dynamic tile id),
+//    ranks its keys stably by digit inside each warp (lane masks built with
+//    shared-memory atomic OR in a per-warp table, see warp_rank), obtains the
+//    number of equal digits in all earlier tiles through a decoupled
+//    look-back over per-(tile, digit) status words, and writes each key to
+//    digit_base[d] + (earlier tiles' d) + (rank inside the tile).  The keys
+//    are read once and written once per pass.
 #pragma once
 
 #include "rs_common.cuh"

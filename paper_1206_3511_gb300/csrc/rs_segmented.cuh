@@ -196,11 +196,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep_seg(SegPassParams<Digi
 // (each pass ranks keys inside their warps exactly like the scatter pass),
 // write it back.  In bucket mode the first pass sorts by the key's bucket
 // relative to the segment's first bucket (the insert step of Algorithm 2)
-// and each bucket is then insertion-sorted by one thread (Algorithm 1); a
-// segment with a bucket above kInsertionMax keys, or spanning more than 256
-// buckets, is sorted by its key bits instead, which gives the same order
-// because bucket ids grow with the key.
-constexpr uint32_t kInsertionMax = 48;
+// and each bucket is then sorted by a stable rank sort (every key counts the
+// bucket's keys that precede it: the comparisons of insertion sort,
+// Algorithm 1, made for all keys at once); a segment with a bucket above
+// kBucketSortMax keys, or spanning more than 256 buckets, is sorted by its
+// key bits instead, which gives the same order because bucket ids grow with
+// the key.
+constexpr uint32_t kBucketSortMax = 48;
 
 template <typename KeyT, bool VALS, int BLOCK>
 struct LocalSmem {
@@ -336,7 +338,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
                                                      [&](KeyT k) { return (uint32_t)(bfn.bucket(k) - b_lo); }, s_dig);
                 cur = 1;
                 for (uint32_t d = threadIdx.x; d < 256; d += BLOCK)
-                    if (s_cnt[d] > kInsertionMax) *s_flag = 1u;
+                    if (s_cnt[d] > kBucketSortMax) *s_flag = 1u;
                 __syncthreads();
                 if (*s_flag == 0u) {
                     by_keys = false;
