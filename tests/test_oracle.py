@@ -293,6 +293,20 @@ def test_typed_float_total_order_of_special_values(oracle):
         assert np.array_equal(got, want)
 
 
+def test_typed_float32_total_order_golden(oracle):
+    """The IEEE-754 totalOrder sequence of tests/golden/ieee754_total_order.txt,
+    shuffled, comes back in order; reversed for descending."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ieee754_total_order.txt")
+    with open(path) as f:
+        want = np.array([int(x, 16) for x in (ln.strip() for ln in f) if x and not x.startswith("#")], np.uint32)
+    perm = np.array([3, 9, 0, 6, 1, 8, 4, 2, 7, 5])
+    assert np.array_equal(oracle.sort_typed(want[perm].view(np.float32)).view(np.uint32), want)
+    assert np.array_equal(oracle.sort_typed(want[perm].view(np.float32), descending=True).view(np.uint32),
+                          want[::-1])
+
+
 def test_typed_descending_is_the_stable_reverse_order(oracle):
     rng = np.random.default_rng(7)
     x = rng.integers(-50, 50, 5000, dtype=np.int32)

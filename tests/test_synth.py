@@ -1,20 +1,29 @@
 """The seeded input generator: pinned to SplitMix64's published outputs, the
 device (torch) form equal to the numpy form bit for bit, and the
 distributions with the shapes they claim."""
+import os
+
 import numpy as np
 import pytest
 
 import synth
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def read_golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [int(x, 16) for x in (ln.strip() for ln in f) if x and not x.startswith("#")]
+
+
 def test_splitmix64_published_outputs():
-    # SplitMix64 seeded with state 0 (Steele, Lea and Flood 2014; the
-    # reference generator of Vigna's xoshiro seeding code) starts
-    # 0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F.  Seed 0 of
-    # dist 0, stream 0 has base mix(0) = 0, so its draws are that sequence.
+    """SplitMix64 seeded with state 0 (tests/golden/splitmix64_state0.txt).
+    Seed 0 of dist 0, stream 0 has base mix(0) = 0, so its draws are that
+    sequence."""
     assert int(synth.stream_base(0, 0, 0)) == 0
-    got = [int(v) for v in synth.u64(3, 0, 0, 0)]
-    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    want = read_golden("splitmix64_state0.txt")
+    assert [int(v) for v in synth.u64(len(want), 0, 0, 0)] == want
 
 
 @pytest.mark.parametrize("seed,dist,stream", [(0, 0, 0), (5, 20, 0), (3, 6, 11), (2**40 + 7, 9, 3)])
