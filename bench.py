@@ -73,7 +73,8 @@ PAPER_TABLE1_S = {
 # n = number of arrays (batched) or requests per arrival rate (served)
 WORKLOADS["batched_u32_20k"] = ("batched", 4, False, 20_000, 32, 0,
                                 "segmented sort of 20,000 uint32 arrays, sizes log-uniform in [256, 2,000,000] "
-                                "(seed 0), uniform keys, one CUDA-graph launch; vs one rs_sort_u32 call per array")
+                                "(seed 0), uniform keys, one CUDA-graph launch with the autotuned pass shape; "
+                                "vs one rs_sort_u32 call per array")
 WORKLOADS["served_mix"] = ("served", 4, False, 1_000, 32, None,
                            "sort server: Poisson arrivals at 1k-50k req/s, sizes log-uniform in [1e3, 5e7] keys, "
                            "70% uint32 keys-only / 30% uint64 keys + uint32 values, distributions 0-6, 80 GB budget; "
@@ -700,8 +701,10 @@ def run_batched(args):
     d_out = torch.empty_like(d_keys)
     d_off = torch.from_numpy(off.view(np.int64)).to(dev)
     stream = torch.cuda.current_stream()
-    plan = rs.Plan(rs.RS_PLAN_SEGMENTED, d_keys, d_out, seg_offsets=d_off)
-    _, graph_kernels, _ = plan.info()
+    # the plan's autotuner times every compiled pass shape on this batch and
+    # captures the fastest into the graph
+    plan = rs.Plan(rs.RS_PLAN_SEGMENTED, d_keys, d_out, seg_offsets=d_off, autotune=True)
+    seg_shape, graph_kernels, _ = plan.info()
 
     sampler = ClockSampler(dev)
     sampler.start()
@@ -733,8 +736,8 @@ def run_batched(args):
     rs.rs_profile_enable(True)
     launches0 = rs.rs_launch_count()
     for _ in range(prof_steps):
-        rs.check(rs.rs_sort_segmented_u32(d_keys, d_out, None, None, d_off, count, n_total, 32, seg_ws,
-                                          seg_ws.numel(), stream), "segmented")
+        rs.check(rs.rs_sort_segmented_u32_ex(d_keys, d_out, None, None, d_off, count, n_total, 32, seg_ws,
+                                             seg_ws.numel(), stream, seg_shape), "segmented")
     torch.cuda.synchronize()
     launches_per_step = (rs.rs_launch_count() - launches0) / prof_steps
     rs.rs_profile_enable(False)
@@ -839,6 +842,8 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOADS["batched_u32_20k"][6], "arrays": count, "n_total": n_total,
                    "parallelism": f"replicas x{world}",
+                   "kernel_shape": {"digit_bits": seg_shape[0], "block_threads": seg_shape[1],
+                                    "items_per_thread": seg_shape[2], "chosen_by": "autotuner"},
                    "l2": "inputs larger than L2 (%d MB keys vs 129 MB L2), no flush" % (n_total * 4 // 2**20)},
         "clocks": clocks, "gpu_launches": graph_kernels * args.steps, "graph_kernel_nodes": graph_kernels,
         "eager_launches_per_step": launches_per_step,

@@ -248,6 +248,18 @@ RS_API rs_status rs_sort_segmented_u32(const uint32_t* keys_in, uint32_t* keys_o
 RS_API rs_status rs_sort_segmented_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
                                        uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg,
                                        size_t n_total, int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream);
+/* Same with an explicit kernel shape for the scatter passes of the large
+ * segments (NULL = default).  Every shape rs_config_get lists is compiled for
+ * segmented passes at digit_bits = 8; another digit width or shape gives
+ * RS_ERR_UNSUPPORTED.  The output does not depend on the shape. */
+RS_API rs_status rs_sort_segmented_u32_ex(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
+                                          uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg,
+                                          size_t n_total, int key_bits, void* ws, size_t ws_bytes,
+                                          rs_stream_t stream, const rs_config* cfg);
+RS_API rs_status rs_sort_segmented_u64_ex(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
+                                          uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg,
+                                          size_t n_total, int key_bits, void* ws, size_t ws_bytes,
+                                          rs_stream_t stream, const rs_config* cfg);
 
 /* ---------------------------------------------------------------------------
  * Plans: one sort call with fixed buffers and sizes, captured once into a
@@ -256,10 +268,11 @@ RS_API rs_status rs_sort_segmented_u64(const uint64_t* keys_in, uint64_t* keys_o
  * planned call is rs_sort_* (RS_PLAN_RADIX), bs_sort_* (RS_PLAN_BUCKET) or
  * rs_sort_segmented_* (RS_PLAN_SEGMENTED, n = n_total) with the arguments in
  * the descriptor; argument errors are returned by rs_plan_create.
- * autotune (radix only): every compiled kernel shape whose workspace fits
- * ws_bytes is timed on the plan's buffers and the fastest is kept (all
- * shapes give identical bits); results are cached per GPU, key width,
- * values, key_bits and floor(log2 n) for the life of the process.
+ * autotune (radix and segmented): every compiled kernel shape (radix: whose
+ * workspace fits ws_bytes; segmented: every 8-bit shape) is timed on the
+ * plan's buffers and the fastest is kept (all shapes give identical bits);
+ * results are cached per GPU, algorithm, key width, values, key_bits and
+ * floor(log2 n) for the life of the process.
  * rs_plan_create runs the planned sort at least once (more when tuning) on
  * the plan's buffers and waits for it.  The buffers must stay valid for the
  * life of the plan; a plan must not be launched concurrently with itself.
@@ -287,7 +300,7 @@ typedef struct rs_plan_desc {
 } rs_plan_desc;
 RS_API rs_status rs_plan_create(const rs_plan_desc* desc, rs_plan** out);
 RS_API rs_status rs_plan_launch(rs_plan* plan, rs_stream_t stream);
-/* The kernel shape in use (radix plans; zeros otherwise), the number of
+/* The kernel shape in use (radix and segmented plans; zeros otherwise), the number of
  * kernel nodes in the graph, and the tuned time per sort in ms (-1 if not
  * tuned in this call). */
 RS_API rs_status rs_plan_info(const rs_plan* plan, rs_config* cfg, size_t* kernel_nodes, float* tuned_ms);

@@ -14,7 +14,7 @@ bits are sorted as unsigned).  Values are 32-bit (uint32 or int32).
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (rs_server_release, bs_bucket_counts_u32, bs_bucket_counts_u64, RS_KEY_FLOAT, RS_KEY_INT, RS_KEY_UINT, rs_sort_typed, RS_PLAN_BUCKET, RS_PLAN_RADIX, RS_PLAN_SEGMENTED, RsPlanDesc, rs_plan_create, rs_plan_destroy,
+from ._lib import (rs_sort_segmented_u32_ex, rs_sort_segmented_u64_ex, rs_server_release, bs_bucket_counts_u32, bs_bucket_counts_u64, RS_KEY_FLOAT, RS_KEY_INT, RS_KEY_UINT, rs_sort_typed, RS_PLAN_BUCKET, RS_PLAN_RADIX, RS_PLAN_SEGMENTED, RsPlanDesc, rs_plan_create, rs_plan_destroy,
                    rs_plan_info, rs_plan_launch, RsRequest, RsResult, RsServerConfig, RsServerStats, rs_server_create, rs_server_destroy,
                    rs_server_get_stats, rs_server_poll, rs_server_submit, rs_server_wait, bs_sort_u32, bs_sort_u64, rs_segmented_workspace_bytes, rs_sort_segmented_u32, rs_sort_segmented_u64,
                    RS_ALGO_BUCKET, RS_ALGO_RADIX, STATUS, RsConfig, load, rs_config_count, rs_config_get,
@@ -35,7 +35,8 @@ __all__ = [
     "RS_KEY_UINT", "RS_KEY_INT", "RS_KEY_FLOAT", "RsPlanDesc", "rs_plan_create", "rs_plan_destroy", "rs_plan_info",
     "rs_plan_launch", "RS_PLAN_RADIX", "RS_PLAN_BUCKET", "RS_PLAN_SEGMENTED", "RsRequest", "RsResult",
     "RsServerConfig", "RsServerStats", "rs_server_create", "rs_server_destroy", "rs_server_get_stats",
-    "rs_server_poll", "rs_server_submit", "rs_server_wait", "rs_server_release",
+    "rs_server_poll", "rs_server_submit", "rs_server_wait", "rs_server_release", "rs_sort_segmented_u32_ex",
+    "rs_sort_segmented_u64_ex",
 ]
 
 

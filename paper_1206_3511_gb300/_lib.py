@@ -88,6 +88,8 @@ SIGNATURES: dict[str, tuple] = {
     "rs_segmented_workspace_bytes": (_SZ, [_I, _I, _SZ, _SZ, _I]),
     "rs_sort_segmented_u32": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P]),
     "rs_sort_segmented_u64": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P]),
+    "rs_sort_segmented_u32_ex": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P, _c.POINTER(RsConfig)]),
+    "rs_sort_segmented_u64_ex": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P, _c.POINTER(RsConfig)]),
     "rs_sort_typed": (_I, [_I, _I, _I, _P, _P, _P, _P, _SZ, _P, _SZ, _P]),
     "bs_bucket_counts_u32": (_I, [_P, _SZ, _c.c_uint32, _c.c_uint32, _SZ, _P, _P, _SZ, _P]),
     "bs_bucket_counts_u64": (_I, [_P, _SZ, _c.c_uint64, _c.c_uint64, _SZ, _P, _P, _SZ, _P]),
@@ -277,6 +279,22 @@ def rs_sort_segmented_u64(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, n
                           stream=None) -> int:
     return _call("rs_sort_segmented_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out),
                  ptr(d_seg_offsets), nseg, n_total, key_bits, ptr(ws), ws_bytes, stream_handle(stream))
+
+
+def rs_sort_segmented_u32_ex(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, key_bits, ws,
+                             ws_bytes, stream=None, cfg=None) -> int:
+    c = _as_cfg(cfg)
+    return _call("rs_sort_segmented_u32_ex", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out),
+                 ptr(d_seg_offsets), nseg, n_total, key_bits, ptr(ws), ws_bytes, stream_handle(stream),
+                 _c.byref(c) if c is not None else None)
+
+
+def rs_sort_segmented_u64_ex(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, key_bits, ws,
+                             ws_bytes, stream=None, cfg=None) -> int:
+    c = _as_cfg(cfg)
+    return _call("rs_sort_segmented_u64_ex", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out),
+                 ptr(d_seg_offsets), nseg, n_total, key_bits, ptr(ws), ws_bytes, stream_handle(stream),
+                 _c.byref(c) if c is not None else None)
 
 
 def bs_bucket_counts_u32(keys, n, min_key, max_key, num_buckets, d_counts, ws, ws_bytes, stream=None) -> int:

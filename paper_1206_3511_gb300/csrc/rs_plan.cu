@@ -37,17 +37,17 @@ rs_status enqueue_plan(const rs_plan_desc& d, const rs_config* cfg, cudaStream_t
                                      d.ws_bytes, s);
         case RS_PLAN_SEGMENTED:
             return d.key_bytes == 4
-                       ? rs_sort_segmented_u32(static_cast<const uint32_t*>(d.keys_in),
-                                               static_cast<uint32_t*>(d.keys_out), d.vals_in, d.vals_out,
-                                               d.d_seg_offsets, d.nseg, d.n, d.key_bits, d.ws, d.ws_bytes, s)
-                       : rs_sort_segmented_u64(static_cast<const uint64_t*>(d.keys_in),
-                                               static_cast<uint64_t*>(d.keys_out), d.vals_in, d.vals_out,
-                                               d.d_seg_offsets, d.nseg, d.n, d.key_bits, d.ws, d.ws_bytes, s);
+                       ? rs_sort_segmented_u32_ex(static_cast<const uint32_t*>(d.keys_in),
+                                                  static_cast<uint32_t*>(d.keys_out), d.vals_in, d.vals_out,
+                                                  d.d_seg_offsets, d.nseg, d.n, d.key_bits, d.ws, d.ws_bytes, s, cfg)
+                       : rs_sort_segmented_u64_ex(static_cast<const uint64_t*>(d.keys_in),
+                                                  static_cast<uint64_t*>(d.keys_out), d.vals_in, d.vals_out,
+                                                  d.d_seg_offsets, d.nseg, d.n, d.key_bits, d.ws, d.ws_bytes, s, cfg);
     }
     return RS_ERR_INVALID_ARG;
 }
 
-using TuneKey = std::tuple<std::string, int, int, int, int>;
+using TuneKey = std::tuple<std::string, int, int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, rs_config> g_tune_cache;
 
@@ -57,7 +57,7 @@ TuneKey tune_key(const rs_plan_desc& d) {
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, dev);
     const int kbits = d.key_bits ? d.key_bits : 8 * d.key_bytes;
-    return TuneKey(std::string(prop.name), d.key_bytes, d.vals_in != nullptr, kbits,
+    return TuneKey(std::string(prop.name), d.algo, d.key_bytes, d.vals_in != nullptr, kbits,
                    d.n ? (int)std::floor(std::log2((double)d.n)) : 0);
 }
 
@@ -76,6 +76,18 @@ float time_config(const rs_plan_desc& d, const rs_config& cfg, cudaStream_t s, c
     return ms / reps;
 }
 
+// The shape a plan uses without tuning: the radix default, or the default
+// segmented shape at 8-bit digits.
+rs_status default_shape(const rs_plan_desc& d, rs_config* out) {
+    if (d.algo == RS_PLAN_SEGMENTED) {
+        out->digit_bits = kSegDigitBits;
+        return seg_shape_get(d.key_bytes, d.vals_in != nullptr, 0, &out->block_threads, &out->items_per_thread)
+                   ? RS_OK
+                   : RS_ERR_UNSUPPORTED;
+    }
+    return rs_default_config(d.key_bytes, d.vals_in != nullptr, d.n, out);
+}
+
 rs_status autotune(const rs_plan_desc& d, cudaStream_t s, rs_config* best, float* best_ms) {
     const TuneKey key = tune_key(d);
     {
@@ -90,13 +102,21 @@ rs_status autotune(const rs_plan_desc& d, cudaStream_t s, rs_config* best, float
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return RS_ERR_CUDA;
     const int kbits = d.key_bits ? d.key_bits : 8 * d.key_bytes;
-    const int count = rs_config_count(d.key_bytes, d.vals_in != nullptr);
+    const bool vals = d.vals_in != nullptr;
+    const bool seg = d.algo == RS_PLAN_SEGMENTED;
+    const int count = seg ? seg_shape_count(d.key_bytes, vals) : rs_config_count(d.key_bytes, vals);
     float found = -1.f;
     for (int i = 0; i < count; ++i) {
         rs_config c{};
-        if (rs_config_get(d.key_bytes, d.vals_in != nullptr, i, &c) != RS_OK) continue;
-        const size_t need = rs_workspace_bytes_cfg(d.key_bytes, d.vals_in != nullptr, d.n, kbits, &c);
-        if (need == 0 || need > d.ws_bytes) continue;
+        if (seg) {
+            // segmented passes: every compiled shape at 8-bit digits, one workspace for all
+            c.digit_bits = kSegDigitBits;
+            if (!seg_shape_get(d.key_bytes, vals, i, &c.block_threads, &c.items_per_thread)) continue;
+        } else {
+            if (rs_config_get(d.key_bytes, vals, i, &c) != RS_OK) continue;
+            const size_t need = rs_workspace_bytes_cfg(d.key_bytes, vals, d.n, kbits, &c);
+            if (need == 0 || need > d.ws_bytes) continue;
+        }
         const float ms = time_config(d, c, s, a, b, 3);
         if (ms > 0.f && (found < 0.f || ms < found)) {
             found = ms;
@@ -105,7 +125,7 @@ rs_status autotune(const rs_plan_desc& d, cudaStream_t s, rs_config* best, float
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    if (found < 0.f) return rs_default_config(d.key_bytes, d.vals_in != nullptr, d.n, best);
+    if (found < 0.f) return default_shape(d, best);
     *best_ms = found;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = *best;
@@ -142,11 +162,11 @@ rs_status rs_plan_create(const rs_plan_desc* desc, rs_plan** out) {
     p->has_cfg = false;
     p->tuned_ms = -1.f;
     rs_status st = RS_OK;
-    if (d.algo == RS_PLAN_RADIX) {
+    if (d.algo == RS_PLAN_RADIX || d.algo == RS_PLAN_SEGMENTED) {
         if (d.autotune)
             st = autotune(d, s, &p->cfg, &p->tuned_ms);
         else
-            st = rs_default_config(d.key_bytes, d.vals_in != nullptr, d.n, &p->cfg);
+            st = default_shape(d, &p->cfg);
         p->has_cfg = st == RS_OK;
     }
     if (st == RS_OK) {

@@ -13,8 +13,6 @@ namespace rs {
 
 namespace {
 
-constexpr int kSegDigitBits = 8;
-
 template <typename KeyT, bool VALS, typename BucketFn>
 cudaError_t launch_local(const LocalParams& lp, BucketFn bfn, size_t grid, cudaStream_t s) {
     using LS = LocalSmem<KeyT, VALS, kLocalBlock>;
@@ -39,10 +37,75 @@ uint32_t seg_tile_keys(int key_bytes, bool vals) {
     return vals ? SegShape<uint64_t, true>::kTile : SegShape<uint64_t, false>::kTile;
 }
 
+namespace {
+
+struct SegVariant {
+    int key_bytes;
+    bool vals;
+    int block, items;
+    cudaError_t (*launch)(const SegPassParams<RadixDigit>&, size_t, cudaStream_t);
+};
+
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB>
+constexpr SegVariant seg_variant() {
+    return SegVariant{(int)sizeof(KeyT), VALS, BLOCK, ITEMS,
+                      &launch_seg_pass_shape<KeyT, VALS, BLOCK, ITEMS, MINB, RadixDigit>};
+}
+
+// The first entry of each (key width, values) group is SegShape's.
+const SegVariant kSegVariants[] = {
+    seg_variant<uint32_t, false, 384, 16, 3>(), seg_variant<uint32_t, false, 256, 18, 4>(),
+    seg_variant<uint32_t, false, 256, 15, 4>(), seg_variant<uint32_t, false, 512, 15, 2>(),
+    seg_variant<uint32_t, true, 256, 12, 4>(),  seg_variant<uint32_t, true, 256, 15, 3>(),
+    seg_variant<uint64_t, false, 256, 12, 4>(), seg_variant<uint64_t, false, 256, 9, 4>(),
+    seg_variant<uint64_t, true, 256, 10, 3>(),  seg_variant<uint64_t, true, 256, 8, 4>(),
+};
+
+const SegVariant* seg_variant_at(int key_bytes, bool vals, int i) {
+    for (const SegVariant& v : kSegVariants)
+        if (v.key_bytes == key_bytes && v.vals == vals && i-- == 0) return &v;
+    return nullptr;
+}
+
+}  // namespace
+
+int seg_shape_count(int key_bytes, bool vals) {
+    int c = 0;
+    for (const SegVariant& v : kSegVariants) c += v.key_bytes == key_bytes && v.vals == vals;
+    return c;
+}
+
+int seg_shape_find(int key_bytes, bool vals, int block, int items) {
+    for (int i = 0; const SegVariant* v = seg_variant_at(key_bytes, vals, i); ++i)
+        if (v->block == block && v->items == items) return i;
+    return -1;
+}
+
+bool seg_shape_get(int key_bytes, bool vals, int i, int* block, int* items) {
+    const SegVariant* v = seg_variant_at(key_bytes, vals, i);
+    if (!v) return false;
+    *block = v->block;
+    *items = v->items;
+    return true;
+}
+
+uint32_t seg_shape_tile(int key_bytes, bool vals, int i) {
+    const SegVariant* v = seg_variant_at(key_bytes, vals, i);
+    return v ? (uint32_t)(v->block * v->items) : 0u;
+}
+
+uint32_t seg_min_tile(int key_bytes, bool vals) {
+    uint32_t t = 0;
+    for (const SegVariant& v : kSegVariants)
+        if (v.key_bytes == key_bytes && v.vals == vals && (t == 0 || (uint32_t)(v.block * v.items) < t))
+            t = (uint32_t)(v.block * v.items);
+    return t;
+}
+
 SegLayout seg_layout(int key_bytes, bool vals, size_t n_total, size_t max_segs, int max_passes, int max_bins,
                      size_t extra_head) {
     SegLayout L{};
-    const uint32_t tk = seg_tile_keys(key_bytes, vals);
+    const uint32_t tk = std::min(seg_min_tile(key_bytes, vals), seg_tile_keys(key_bytes, vals));
     L.max_segs = max_segs ? max_segs : 1;
     L.max_tiles = n_total / tk + L.max_segs + 1;
     L.max_chunks = n_total / kSegChunk + L.max_segs + 1;
@@ -90,7 +153,9 @@ template <typename KeyT, bool VALS>
 static rs_status large_passes_t(const void* src_k, const uint32_t* src_v, void* out_k, uint32_t* out_v,
                                 const SegBuffers& B, int passes, int D, int first_ctr, cudaStream_t stream) {
     const uint32_t bins = 1u << D;
-    const uint32_t tk = seg_tile_keys(sizeof(KeyT), VALS);
+    const uint32_t tk = B.tile_keys ? B.tile_keys : seg_tile_keys(sizeof(KeyT), VALS);
+    const SegVariant* var = B.shape ? seg_variant_at(sizeof(KeyT), VALS, B.shape) : nullptr;
+    if (B.shape && (!var || (uint32_t)(var->block * var->items) != tk)) return RS_ERR_UNSUPPORTED;
     {
         KernelScope scope("plan_maps", stream);
         k_plan_maps<<<(unsigned)std::min<size_t>(B.max_segs, (size_t)device_sm_count() * 8), 256, 0, stream>>>(
@@ -133,7 +198,9 @@ static rs_status large_passes_t(const void* src_k, const uint32_t* src_v, void* 
         sp.base.status_next = (p + 1 < passes) ? B.status[(p + 1) & 1] : nullptr;
         sp.base.tile_ctr = &B.ws_hdr->tile_ctr[(first_ctr + p) % kMaxPasses];
         sp.pass = p;
-        if (launch_seg_pass<KeyT, VALS, RadixDigit>(sp, B.max_tiles, stream) != cudaSuccess) return RS_ERR_CUDA;
+        const cudaError_t e = var ? var->launch(sp, B.max_tiles, stream)
+                                  : launch_seg_pass<KeyT, VALS, RadixDigit>(sp, B.max_tiles, stream);
+        if (e != cudaSuccess) return RS_ERR_CUDA;
         cur_k = dst_k;
         cur_v = dst_v;
     }
@@ -210,7 +277,7 @@ size_t segmented_workspace_bytes(int key_bytes, bool vals, size_t n_total, size_
 
 static rs_status segmented_impl(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
                                 uint32_t* vals_out, const uint64_t* d_offsets, size_t nseg, size_t n_total,
-                                int key_bits, void* ws, size_t ws_bytes, cudaStream_t stream) {
+                                int key_bits, void* ws, size_t ws_bytes, cudaStream_t stream, const rs_config* cfg) {
     const int width = 8 * key_bytes;
     if (key_bits == 0) key_bits = width;
     if (key_bits < 1 || key_bits > width) return RS_ERR_INVALID_ARG;
@@ -224,17 +291,25 @@ static rs_status segmented_impl(int key_bytes, const void* keys_in, void* keys_o
     if (vals && vals_in != vals_out && ranges_overlap(vals_in, vb, vals_out, vb)) return RS_ERR_INVALID_ARG;
     if (((uintptr_t)keys_in | (uintptr_t)keys_out) % key_bytes) return RS_ERR_INVALID_ARG;
     if (!ws || ((uintptr_t)ws % 256)) return RS_ERR_WORKSPACE;
+    int shape = 0;
+    if (cfg) {
+        if (cfg->digit_bits != kSegDigitBits) return RS_ERR_UNSUPPORTED;
+        shape = seg_shape_find(key_bytes, vals, cfg->block_threads, cfg->items_per_thread);
+        if (shape < 0) return RS_ERR_UNSUPPORTED;
+    }
     const int D = kSegDigitBits;
     const int P = (key_bits + D - 1) / D;
     const SegLayout L = seg_layout(key_bytes, vals, n_total, nseg, P, 1 << D, 0);
     if (ws_bytes < L.total) return RS_ERR_WORKSPACE;
-    const SegBuffers B = carve_seg_buffers(ws, L);
+    SegBuffers B = carve_seg_buffers(ws, L);
+    B.shape = shape;
+    B.tile_keys = seg_shape_tile(key_bytes, vals, shape);
     RS_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(WsHeader), stream));
     RS_CUDA_TRY(cudaMemsetAsync(B.hdr, 0, sizeof(SegPlanHdr), stream));
     {
         KernelScope scope("plan_segments", stream);
         k_plan_from_offsets<<<(unsigned)((nseg + 255) / 256), 256, 0, stream>>>(
-            d_offsets, nseg, kLocalCap, seg_tile_keys(key_bytes, vals), key_bits, B.large, B.small, B.hdr, B.ws_hdr);
+            d_offsets, nseg, kLocalCap, B.tile_keys, key_bits, B.large, B.small, B.hdr, B.ws_hdr);
         if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
     }
     // large segments: scatter passes from keys_in (in place with an odd pass
@@ -275,14 +350,28 @@ rs_status rs_sort_segmented_u32(const uint32_t* keys_in, uint32_t* keys_out, con
                                 uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg, size_t n_total,
                                 int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream) {
     return segmented_impl(4, keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, key_bits, ws,
-                          ws_bytes, stream);
+                          ws_bytes, stream, nullptr);
 }
 
 rs_status rs_sort_segmented_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
                                 uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg, size_t n_total,
                                 int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream) {
     return segmented_impl(8, keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, key_bits, ws,
-                          ws_bytes, stream);
+                          ws_bytes, stream, nullptr);
+}
+
+rs_status rs_sort_segmented_u32_ex(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
+                                   uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg, size_t n_total,
+                                   int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream, const rs_config* cfg) {
+    return segmented_impl(4, keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, key_bits, ws,
+                          ws_bytes, stream, cfg);
+}
+
+rs_status rs_sort_segmented_u64_ex(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
+                                   uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg, size_t n_total,
+                                   int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream, const rs_config* cfg) {
+    return segmented_impl(8, keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, key_bits, ws,
+                          ws_bytes, stream, cfg);
 }
 
 }  // extern "C"

@@ -9,6 +9,9 @@
 
 namespace rs {
 
+// Digit width of the segmented scatter passes.
+constexpr int kSegDigitBits = 8;
+
 // Shared-memory sort capacity: segments of at most this many keys are
 // sorted inside one block.
 constexpr int kLocalBlock = 256;
@@ -35,11 +38,11 @@ struct SegShape<uint64_t, true> {
     static constexpr int kBlock = 256, kItems = 10, kMinB = 3, kTile = kBlock * kItems;
 };
 
-template <typename KeyT, bool VALS, typename DigitOp>
-cudaError_t launch_seg_pass(const SegPassParams<DigitOp>& sp, size_t grid, cudaStream_t s) {
-    using S = SegShape<KeyT, VALS>;
-    using Shape = OnesweepShape<KeyT, VALS, S::kBlock, S::kItems>;
-    auto kern = k_onesweep_seg<KeyT, VALS, S::kBlock, S::kItems, S::kMinB, DigitOp>;
+// One segmented scatter pass with an explicit kernel shape.
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB, typename DigitOp>
+cudaError_t launch_seg_pass_shape(const SegPassParams<DigitOp>& sp, size_t grid, cudaStream_t s) {
+    using Shape = OnesweepShape<KeyT, VALS, BLOCK, ITEMS>;
+    auto kern = k_onesweep_seg<KeyT, VALS, BLOCK, ITEMS, MINB, DigitOp>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -49,11 +52,29 @@ cudaError_t launch_seg_pass(const SegPassParams<DigitOp>& sp, size_t grid, cudaS
     if (attr_err != cudaSuccess) return attr_err;
     const size_t smem = Shape::smem_bytes(sp.base.digit_bits);
     if (smem > max_fitting_pass_smem<Shape>()) return cudaErrorInvalidValue;
-    grid = std::min<size_t>(grid, (size_t)resident_grid(kern, S::kBlock, smem));
+    grid = std::min<size_t>(grid, (size_t)resident_grid(kern, BLOCK, smem));
     KernelScope scope("onesweep_seg_pass", s);
-    kern<<<(unsigned)(grid ? grid : 1), S::kBlock, smem, s>>>(sp);
+    kern<<<(unsigned)(grid ? grid : 1), BLOCK, smem, s>>>(sp);
     return cudaGetLastError();
 }
+
+// One segmented scatter pass with the default shape of its key type.
+template <typename KeyT, bool VALS, typename DigitOp>
+cudaError_t launch_seg_pass(const SegPassParams<DigitOp>& sp, size_t grid, cudaStream_t s) {
+    using S = SegShape<KeyT, VALS>;
+    return launch_seg_pass_shape<KeyT, VALS, S::kBlock, S::kItems, S::kMinB, DigitOp>(sp, grid, s);
+}
+
+// Kernel shapes compiled for the segmented radix passes (8-bit digits): the
+// same shapes as the plain radix sort; index 0 of each key type is SegShape.
+int seg_shape_count(int key_bytes, bool vals);
+// Index of the shape (block, items), or -1 if it is not compiled.
+int seg_shape_find(int key_bytes, bool vals, int block, int items);
+// Block size and keys per thread of shape i; false if there is none.
+bool seg_shape_get(int key_bytes, bool vals, int i, int* block, int* items);
+// Keys per tile of shape i, and the smallest over all shapes (workspace sizing).
+uint32_t seg_shape_tile(int key_bytes, bool vals, int i);
+uint32_t seg_min_tile(int key_bytes, bool vals);
 
 template <typename KeyT, typename Digits>
 cudaError_t launch_seg_counts(const KeyT* keys, const SegDesc* segs, const SegPlanHdr* hdr, const uint32_t* chunk_seg,
@@ -88,6 +109,8 @@ struct SegBuffers {
     uint32_t* tmp_vals;    // [n_total] or null
     size_t max_segs, max_tiles, max_chunks;
     int max_passes, max_bins;
+    int shape;             // segmented pass shape (index into the compiled shapes; 0 = default)
+    uint32_t tile_keys;    // keys per tile of that shape (0: the default shape's)
 };
 
 // Workspace layout of a segmented sort: sizes for every region, the offsets

@@ -161,3 +161,23 @@ def test_plan_rejects_bad_arguments(rs):
     desc = rs.RsPlanDesc(7, 4, kd.data_ptr(), ok.data_ptr(), None, None, 1000, 0, 1, 0, 0, None, 0, None, 0, 0)
     rc, h = rs.rs_plan_create(desc)
     assert rc == 1 and not h  # RS_ERR_INVALID_ARG
+
+
+def test_segmented_plan_autotune_picks_a_compiled_shape(rs, oracle):
+    import torch
+
+    sizes = synth.log_uniform_sizes(200, 256, 300_000, seed=81)
+    n = int(sizes.sum())
+    keys = synth.u32(n, 82, 0)
+    off = synth.segment_offsets(sizes)
+    kd, od = to_dev(keys), to_dev(off.astype(np.uint64))
+    ok = torch.empty_like(kd)
+    plan = rs.Plan(rs.RS_PLAN_SEGMENTED, kd, ok, seg_offsets=od, autotune=True)
+    cfg, nodes, ms = plan.info()
+    shapes = {rs.rs_config_get(4, False, i).as_tuple()[1:] for i in range(rs.rs_config_count(4, False))}
+    assert cfg[0] == 8 and cfg[1:] in shapes and ms > 0.0
+    ok.zero_()
+    plan.launch()
+    torch.cuda.synchronize()
+    assert_same(from_dev(ok, np.uint32), oracle.segmented_radix_sort(keys, off, None, 32), "autotuned segmented")
+    plan.close()

@@ -164,3 +164,39 @@ def test_full_batched_workload_sampled_against_oracle(rs, oracle):
             assert torch.equal(sx, sy), f"arrays {i0}..{i1}: multiset changed"
         i0 = i1
     plan.close()
+
+
+@pytest.mark.parametrize("kb,with_values", [(4, False), (4, True), (8, False), (8, True)])
+def test_every_compiled_shape_gives_identical_bits(rs, oracle, kb, with_values):
+    """rs_sort_segmented_*_ex with each kernel shape compiled for segmented
+    passes (every radix shape at 8-bit digits): the same bits as the oracle;
+    another digit width is refused."""
+    import torch
+
+    sizes = [70_001, 5000, 4097, 300, 12_289, 0, 40_000]
+    n = sum(sizes)
+    keys = synth.u32(n, 48, 0) if kb == 4 else synth.keys_u64(n, 64, seed=48)
+    vals = synth.index_values(n) if with_values else None
+    off = synth.segment_offsets(sizes)
+    kd, od = to_dev(keys), to_dev(off.astype(np.uint64))
+    vd = to_dev(vals) if with_values else None
+    ws = rs.workspace(rs.rs_segmented_workspace_bytes(kb, with_values, n, len(sizes), 0))
+    fn = rs.rs_sort_segmented_u32_ex if kb == 4 else rs.rs_sort_segmented_u64_ex
+    want = oracle.segmented_radix_sort(keys, off, vals, 8 * kb)
+    shapes = sorted({rs.rs_config_get(kb, with_values, i).as_tuple()[1:]
+                     for i in range(rs.rs_config_count(kb, with_values))})
+    assert len(shapes) >= 2
+    for block, items in shapes:
+        ok = torch.empty_like(kd)
+        ov = torch.empty_like(vd) if with_values else None
+        assert fn(kd, ok, vd, ov, od, len(sizes), n, 0, ws, ws.numel(), None, (8, block, items)) == 0
+        torch.cuda.synchronize()
+        assert rs.get_status(ws) == 0
+        if with_values:
+            assert_same(from_dev(ok, keys.dtype), want[0], f"{block}x{items} keys")
+            assert_same(from_dev(ov, np.uint32), want[1], f"{block}x{items} values")
+        else:
+            assert_same(from_dev(ok, keys.dtype), want, f"{block}x{items}")
+    ok = torch.empty_like(kd)
+    ov = torch.empty_like(vd) if with_values else None
+    assert fn(kd, ok, vd, ov, od, len(sizes), n, 0, ws, ws.numel(), None, (7,) + shapes[0]) == 9  # UNSUPPORTED
