@@ -152,56 +152,60 @@ struct PlanLevel {
     uint32_t* num_copy;
 };
 
-// A run of consecutive sibling partitions being grouped into one leaf.
-struct LeafRun {
-    uint64_t start, n, b_lo, span, key_lo, width;
-};
-
-// Per-parent staging of the planner's output in shared memory, written to the
-// global lists with one atomic reservation per list.
-struct PlanStage {
-    SegDesc leaf[256];
-    SegDesc copy[256];
-    SegDesc big[256];  // to the next level or to the overflow radix
-    uint32_t n_leaf, n_copy, n_big, big_tiles, big_chunks;
-};
-
-__device__ __forceinline__ void stage_run(const PlanLevel& pl, PlanStage& st, LeafRun& r) {
-    if (r.n == 0) {
-        r.span = 0;
-        return;
+// Exclusive prefix sum of one 64-bit value per thread across the block (the
+// block total in *total).  Contains __syncthreads(); every thread calls it.
+template <int BLOCK>
+__device__ __forceinline__ uint64_t block_exclusive_sum_u64(uint64_t x, uint64_t* s_warp, uint64_t* total) {
+    constexpr int kWarps = BLOCK / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(kFullMask, inc, o);
+        if (lane >= o) inc += y;
     }
-    SegDesc c{};
-    c.start = r.start;
-    c.n = (uint32_t)r.n;
-    c.key_lo = r.key_lo;
-    c.aux = r.b_lo;
-    c.bits = r.width <= 1 ? 0u : min(bit_length(r.width - 1), (uint32_t)pl.key_width);
-    c.chunk0 = r.span > 0xffffffffull ? 0xffffffffu : (uint32_t)r.span;
-    if (c.bits == 0) {  // one possible key: already in order, only moved if needed
-        if (!pl.in_out) st.copy[st.n_copy++] = c;
-    } else {
-        st.leaf[st.n_leaf++] = c;
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t run = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const uint64_t v = s_warp[w];
+            s_warp[w] = run;
+            run += v;
+        }
+        s_warp[kWarps] = run;
     }
-    r.n = 0;
-    r.span = 0;
+    __syncthreads();
+    const uint64_t r = inc - x + s_warp[warp];
+    *total = s_warp[kWarps];
+    __syncthreads();
+    return r;
 }
 
-// One block per parent.  Its threads describe the children (digit values)
-// in parallel; then one thread walks them in order.  A child above the
-// shared-memory capacity goes to the next level (while bucket bits remain) or
-// to the overflow radix; the others are grouped, in order, into runs of at
-// most `cap` keys and 256 buckets, each sorted by one block: a run's buckets
-// are contiguous and ordered, so sorting the run by bucket and then each
-// bucket is sorting each child.
+// One block per parent, one thread per child (digit value).  A child above
+// the shared-memory capacity whose keys can differ goes to the next level
+// (while bucket bits remain) or to the overflow radix; the others are
+// grouped, in order, into runs of at most `cap` keys and 256 buckets, each
+// sorted by one block: a run's buckets are contiguous and ordered, so sorting
+// the run by bucket and then each bucket is sorting each child.  The runs
+// are the greedy ones (a child joins the open run unless that would pass
+// either limit); each thread finds, by binary search over prefix sums, where
+// a run that starts at its child would end, and one thread follows the chain
+// of run starts.  Key-value widths are carried as width - 1 so that a range
+// of 2^64 values does not wrap to 0.
 __global__ void __launch_bounds__(256) k_bucket_plan(PlanLevel pl) {
-    __shared__ uint64_t s_off[256], s_n[256], s_below[257];
-    __shared__ PlanStage st;
-    __shared__ uint32_t s_base[5];
+    constexpr int kBlock = 256;
+    __shared__ uint64_t s_pn[257], s_ps[257], s_below[257];
+    __shared__ uint32_t s_next[256];
+    __shared__ uint8_t s_big[256], s_start[256];
+    __shared__ uint64_t s_warp64[kBlock / 32 + 1];
+    __shared__ uint32_t s_scan[kBlock / 32 + 1];
+    __shared__ uint32_t s_valid, s_base[5];
     const uint32_t bins = 1u << pl.digit_bits;
     const uint32_t nparents = pl.parents ? *pl.num_parents : 1u;
     const BucketParams bp = load_bucket_params(pl.bp);
     const bool to_next = pl.next && pl.shift > 0;
+    const uint32_t d = threadIdx.x;
     for (uint32_t parent = blockIdx.x; parent < nparents; parent += gridDim.x) {
         uint64_t pstart = 0, pn = pl.n_total, pb_lo = 0;
         if (pl.parents) {
@@ -212,72 +216,128 @@ __global__ void __launch_bounds__(256) k_bucket_plan(PlanLevel pl) {
         }
         const uint32_t* row = pl.starts + (size_t)parent * bins;
         __syncthreads();
-        for (uint32_t d = threadIdx.x; d <= bins; d += blockDim.x) {
+        if (d == 0) s_valid = bins;
+        // this child's bucket range, keys and key values
+        const uint64_t b_lo = pb_lo + ((uint64_t)d << pl.shift);
+        const bool valid = d < bins && b_lo < bp.nb;
+        uint64_t off = 0, n = 0, span = 0;
+        if (valid) {
+            off = row[d];
+            const uint64_t end = pl.counts ? off + pl.counts[d] : ((d + 1 < bins) ? row[d + 1] : pn);
+            n = end > off ? end - off : 0;
+            span = (uint64_t)1 << pl.shift;
+            if (span > bp.nb - b_lo) span = bp.nb - b_lo;
+        }
+        if (d <= bins) {
             uint64_t b = pb_lo + ((uint64_t)d << pl.shift);
             if (b > bp.nb) b = bp.nb;
             s_below[d] = keys_below_bucket(bp, b);
-            if (d < bins) {
-                const uint64_t off = row[d];
-                const uint64_t end = pl.counts ? off + pl.counts[d] : ((d + 1 < bins) ? row[d + 1] : pn);
-                s_off[d] = off;
-                s_n[d] = end > off ? end - off : 0;
-            }
+        }
+        if (d == 0 && bins == kBlock) {  // the entry past the last child
+            uint64_t b = pb_lo + ((uint64_t)bins << pl.shift);
+            if (b > bp.nb) b = bp.nb;
+            s_below[bins] = keys_below_bucket(bp, b);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            st.n_leaf = st.n_copy = st.n_big = st.big_tiles = st.big_chunks = 0;
-            LeafRun run{};
-            for (uint32_t d = 0; d < bins; ++d) {
-                const uint64_t b_lo = pb_lo + ((uint64_t)d << pl.shift);
-                if (b_lo >= bp.nb) break;  // no bucket, no key beyond this point
-                uint64_t span = (uint64_t)1 << pl.shift;
-                if (span > bp.nb - b_lo) span = bp.nb - b_lo;
-                const uint64_t off = s_off[d], n = s_n[d];
-                const uint64_t below = s_below[d];
-                const uint64_t width = s_below[d + 1] - below;  // key values the span can hold
-                if (n > pl.cap && width > 1) {
-                    stage_run(pl, st, run);
-                    SegDesc c{};
-                    c.start = pstart + off;
-                    c.n = (uint32_t)n;
-                    c.aux = b_lo;
-                    c.key_lo = to_next ? 0 : bp.min + below;  // the next level digits the whole key's bucket id
-                    c.bits = to_next ? 0u : min(bit_length(width - 1), (uint32_t)pl.key_width);
-                    c.tile0 = st.big_tiles;  // offsets inside this parent's reservation
-                    c.chunk0 = st.big_chunks;
-                    st.big_tiles += ceil_div_u32(c.n, pl.tile_keys);
-                    st.big_chunks += ceil_div_u32(c.n, kSegChunk);
-                    st.big[st.n_big++] = c;
+        if (d < bins && !valid) atomicMin(&s_valid, d);
+        uint64_t tot_n, tot_s;
+        const uint64_t pn_d = block_exclusive_sum_u64<kBlock>(n, s_warp64, &tot_n);
+        const uint64_t ps_d = block_exclusive_sum_u64<kBlock>(span, s_warp64, &tot_s);
+        const uint32_t nvalid = s_valid;
+        // width - 1 of this child's key values (valid whenever it holds a key)
+        const uint64_t wm1 = valid ? s_below[d + 1] - s_below[d] - 1 : 0;
+        const bool big = valid && n > pl.cap && wm1 >= 1;
+        if (d < kBlock) {
+            s_pn[d] = pn_d;
+            s_ps[d] = ps_d;
+            s_big[d] = big;
+            s_start[d] = 0;
+        }
+        if (d == 0) {
+            s_pn[kBlock] = tot_n;
+            s_ps[kBlock] = tot_s;
+        }
+        __syncthreads();
+        // where a run starting at this child ends: the first later child that
+        // is big, invalid, or would take the run past cap keys or 256 buckets
+        if (valid && !big) {
+            uint32_t limit = d + 1;
+            while (limit < nvalid && !s_big[limit]) ++limit;  // next big child (bounded by bins)
+            uint32_t lo = d + 1, hi = limit;                 // the answer lies in [lo, hi]
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (s_pn[mid] - pn_d <= pl.cap && s_ps[mid] - ps_d <= 256) lo = mid;
+                else hi = mid - 1;
+            }
+            s_next[d] = lo;
+        }
+        __syncthreads();
+        if (d == 0) {  // follow the chain of run starts
+            uint32_t st = 0;
+            while (st < nvalid) {
+                if (s_big[st]) {
+                    ++st;
                     continue;
                 }
-                if (run.span > 0 && (run.n + n > pl.cap || run.span + span > 256)) stage_run(pl, st, run);
-                if (run.span == 0) {
-                    run.start = pstart + off;
-                    run.b_lo = b_lo;
-                    run.key_lo = bp.min + below;
-                    run.width = 0;
-                }
-                run.n += n;
-                run.span += span;
-                run.width += width;
+                s_start[st] = 1;
+                st = s_next[st];
             }
-            stage_run(pl, st, run);
-            SegPlanHdr* bh = to_next ? pl.next_hdr : pl.ovf_hdr;
-            s_base[0] = st.n_leaf ? atomicAdd(pl.num_leaf, st.n_leaf) : 0u;
-            s_base[1] = st.n_copy ? atomicAdd(pl.num_copy, st.n_copy) : 0u;
-            s_base[2] = st.n_big ? atomicAdd(&bh->num_large, st.n_big) : 0u;
-            s_base[3] = st.n_big ? atomicAdd(&bh->total_tiles, st.big_tiles) : 0u;
-            s_base[4] = st.n_big ? atomicAdd(&bh->total_chunks, st.big_chunks) : 0u;
         }
         __syncthreads();
-        SegDesc* big_list = to_next ? pl.next : pl.ovf;
-        for (uint32_t i = threadIdx.x; i < st.n_leaf; i += blockDim.x) pl.leaf[s_base[0] + i] = st.leaf[i];
-        for (uint32_t i = threadIdx.x; i < st.n_copy; i += blockDim.x) pl.copy[s_base[1] + i] = st.copy[i];
-        for (uint32_t i = threadIdx.x; i < st.n_big; i += blockDim.x) {
-            SegDesc c = st.big[i];
-            c.tile0 += s_base[3];
-            c.chunk0 += s_base[4];
-            big_list[s_base[2] + i] = c;
+        // this child's outputs: a run starting here, and/or itself as a big child
+        SegDesc run{}, bigc{};
+        uint32_t is_leaf = 0, is_copy = 0, is_big = 0, big_tiles = 0, big_chunks = 0;
+        if (valid && s_start[d]) {
+            const uint32_t e = s_next[d];
+            const uint64_t rn = s_pn[e] - pn_d;
+            if (rn > 0) {
+                const uint64_t rwm1 = s_below[e] - s_below[d] - 1;
+                run.start = pstart + off;
+                run.n = (uint32_t)rn;
+                run.key_lo = bp.min + s_below[d];
+                run.aux = b_lo;
+                run.bits = rwm1 == 0 ? 0u : min(bit_length(rwm1), (uint32_t)pl.key_width);
+                const uint64_t rspan = s_ps[e] - ps_d;
+                run.chunk0 = rspan > 0xffffffffull ? 0xffffffffu : (uint32_t)rspan;
+                if (run.bits == 0) is_copy = pl.in_out ? 0u : 1u;  // one possible key: in order already
+                else is_leaf = 1;
+            }
+        }
+        if (big) {
+            bigc.start = pstart + off;
+            bigc.n = (uint32_t)n;
+            bigc.aux = b_lo;
+            bigc.key_lo = to_next ? 0 : bp.min + s_below[d];  // the next level digits the key's bucket id
+            bigc.bits = to_next ? 0u : min(bit_length(wm1), (uint32_t)pl.key_width);
+            is_big = 1;
+            big_tiles = ceil_div_u32(bigc.n, pl.tile_keys);
+            big_chunks = ceil_div_u32(bigc.n, kSegChunk);
+        }
+        const uint32_t at_leaf = block_exclusive_sum<kBlock>(is_leaf, s_scan);
+        const uint32_t n_leaf = s_scan[kBlock / 32];
+        const uint32_t at_copy = block_exclusive_sum<kBlock>(is_copy, s_scan);
+        const uint32_t n_copy = s_scan[kBlock / 32];
+        const uint32_t at_big = block_exclusive_sum<kBlock>(is_big, s_scan);
+        const uint32_t n_big = s_scan[kBlock / 32];
+        const uint32_t at_tiles = block_exclusive_sum<kBlock>(big_tiles, s_scan);
+        const uint32_t n_tiles = s_scan[kBlock / 32];
+        const uint32_t at_chunks = block_exclusive_sum<kBlock>(big_chunks, s_scan);
+        const uint32_t n_chunks = s_scan[kBlock / 32];
+        if (d == 0) {
+            SegPlanHdr* bh = to_next ? pl.next_hdr : pl.ovf_hdr;
+            s_base[0] = n_leaf ? atomicAdd(pl.num_leaf, n_leaf) : 0u;
+            s_base[1] = n_copy ? atomicAdd(pl.num_copy, n_copy) : 0u;
+            s_base[2] = n_big ? atomicAdd(&bh->num_large, n_big) : 0u;
+            s_base[3] = n_big ? atomicAdd(&bh->total_tiles, n_tiles) : 0u;
+            s_base[4] = n_big ? atomicAdd(&bh->total_chunks, n_chunks) : 0u;
+        }
+        __syncthreads();
+        if (is_leaf) pl.leaf[s_base[0] + at_leaf] = run;
+        if (is_copy) pl.copy[s_base[1] + at_copy] = run;
+        if (is_big) {
+            bigc.tile0 = s_base[3] + at_tiles;
+            bigc.chunk0 = s_base[4] + at_chunks;
+            (to_next ? pl.next : pl.ovf)[s_base[2] + at_big] = bigc;
         }
     }
 }

@@ -190,3 +190,14 @@ def test_bucket_counts_report_keys_outside_the_range(rs):
     assert rs.bs_bucket_counts_u32(to_dev(keys), 5, 5, 8, 4, counts, ws, ws.numel()) == 0
     assert rs.get_status(ws) == 3  # RS_ERR_KEY_RANGE
     assert from_dev(counts, np.uint32).tolist() == [1, 1, 1, 1]
+
+
+@pytest.mark.parametrize("n,nb", [(1000, 0), (4000, 200), (100_000, 1), (100_000, 2), (3000, 1)])
+def test_u64_full_range_small_bucket_counts(rs, oracle, n, nb):
+    """64-bit keys over the whole range [0, 2^64 - 1] with few buckets: a
+    group of buckets (or one bucket) then covers all 2^64 key values, a
+    width that only fits 64 bits as width - 1."""
+    keys = synth.keys_u64(n, 64, seed=n + nb)
+    keys[:2] = [0, 2**64 - 1]
+    _check(rs, oracle, keys, synth.index_values(n), 0, 2**64 - 1, nb, what=f"u64 full n={n} nb={nb}",
+           use_bucket_oracle=False)
