@@ -75,11 +75,16 @@ WORKLOADS["batched_u32_20k"] = ("batched", 4, False, 20_000, 32, 0,
                                 "segmented sort of 20,000 uint32 arrays, sizes log-uniform in [256, 2,000,000] "
                                 "(seed 0), uniform keys, one CUDA-graph launch with the autotuned pass shape; "
                                 "vs one rs_sort_u32 call per array")
+WORKLOADS["batched_u32_tiny"] = ("batched", 4, False, 200_000, 32, 0,
+                                 "segmented sort of 200,000 uint32 arrays, sizes log-uniform in [1, 256] (seed 0), "
+                                 "uniform keys, one CUDA-graph launch; vs one rs_sort_u32 call per array")
 WORKLOADS["served_mix"] = ("served", 4, False, 1_000, 32, None,
                            "sort server: Poisson arrivals at 1k-50k req/s, sizes log-uniform in [1e3, 5e7] keys, "
                            "70% uint32 keys-only / 30% uint64 keys + uint32 values, distributions 0-6, 80 GB budget; "
                            "vs a FIFO of one sort per request on one stream")
 BATCH_LO, BATCH_HI = 256, 2_000_000
+# size law of each batched workload: log-uniform in [lo, hi]
+BATCH_SIZES = {"batched_u32_20k": (BATCH_LO, BATCH_HI), "batched_u32_tiny": (1, 256)}
 SERVED_LO, SERVED_HI = 1_000, 50_000_000
 SERVED_RATES = (1_000, 2_000, 5_000, 10_000, 20_000, 35_000, 50_000)
 SERVED_BUDGET = 80 * 10**9
@@ -675,12 +680,12 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
 
 
-def batched_inputs(count, rank, dev):
+def batched_inputs(count, rank, dev, lo=BATCH_LO, hi=BATCH_HI):
     import numpy as np
 
     import synth
 
-    sizes = synth.log_uniform_sizes(count, BATCH_LO, BATCH_HI, seed=0)
+    sizes = synth.log_uniform_sizes(count, lo, hi, seed=0)
     off = synth.segment_offsets(sizes)
     n_total = int(off[-1])
     keys = synth.u32_torch(n_total, seed=rank, dist_id=0, device=dev)
@@ -703,8 +708,9 @@ def run_batched(args):
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     rs.load()
-    count = args.n or WORKLOADS["batched_u32_20k"][3]
-    sizes, off, d_keys = batched_inputs(count, rank, dev)
+    wl = args.workload
+    count = args.n or WORKLOADS[wl][3]
+    sizes, off, d_keys = batched_inputs(count, rank, dev, *BATCH_SIZES[wl])
     n_total = int(off[-1])
     d_out = torch.empty_like(d_keys)
     d_off = torch.from_numpy(off.view(np.int64)).to(dev)
@@ -831,16 +837,21 @@ def run_batched(args):
     n_large = int(sizes[sizes > 4096].sum())
     n_small = n_total - n_large
 
+    n_tiny = int(sizes[sizes <= 256].sum())
+
     def step_bytes_of(name, per_step):
         if name == "onesweep_seg_pass":
             return 2 * n_large * 4 * per_step
         if name == "local_sort":
-            return 2 * n_small * 4
+            return 2 * (n_small - n_tiny) * 4
+        if name == "tiny_sort":
+            return 2 * n_tiny * 4
         return n_large * 4 * per_step
 
     roofline = _roofline_from_stats(kstats, prof_steps, step_bytes_of, hbm_peak, peak_src)
-    if roofline and roofline["kernel"] == "onesweep_seg_pass" and count == WORKLOADS["batched_u32_20k"][3]:
-        roofline["traffic"] = ncu_traffic("onesweep_seg_pass", "batched_u32_20k")
+    if roofline and roofline["kernel"] == "onesweep_seg_pass" and wl == "batched_u32_20k" and \
+            count == WORKLOADS[wl][3]:
+        roofline["traffic"] = ncu_traffic("onesweep_seg_pass", wl)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = _batched_cpu_sample(sizes, off, d_keys)
@@ -848,7 +859,7 @@ def run_batched(args):
         "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOADS["batched_u32_20k"][6], "arrays": count, "n_total": n_total,
+        "config": {"workload": WORKLOADS[wl][6], "arrays": count, "n_total": n_total,
                    "parallelism": f"replicas x{world}",
                    "kernel_shape": {"digit_bits": seg_shape[0], "block_threads": seg_shape[1],
                                     "items_per_thread": seg_shape[2], "chosen_by": "autotuner"},
@@ -1221,8 +1232,8 @@ def run_reference_batched(args):
         return
     import synth
 
-    count = args.n or WORKLOADS["batched_u32_20k"][3]
-    sizes = synth.log_uniform_sizes(count, BATCH_LO, BATCH_HI, seed=0)
+    count = args.n or WORKLOADS[args.workload][3]
+    sizes = synth.log_uniform_sizes(count, *BATCH_SIZES[args.workload], seed=0)
     total_steps = max(1, args.warmup + args.steps)
     budget = max(5_000_000, 60 * 50_000_000 // total_steps)
     rates = []
@@ -1238,7 +1249,7 @@ def run_reference_batched(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": cpu["sample_keys"] / value / 1e6,
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOADS["batched_u32_20k"][6], "arrays": count, "parallelism": "none (1 CPU thread)"},
+        "config": {"workload": WORKLOADS[args.workload][6], "arrays": count, "parallelism": "none (1 CPU thread)"},
         "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 

@@ -116,6 +116,7 @@ SegLayout seg_layout(int key_bytes, bool vals, size_t n_total, size_t max_segs, 
     L.off_plan = c.take(sizeof(SegPlanHdr));
     L.off_large = c.take(L.max_segs * sizeof(SegDesc));
     L.off_small = c.take(L.max_segs * sizeof(SegDesc));
+    L.off_tiny = c.take(L.max_segs * sizeof(SegDesc));
     L.off_tile_seg = c.take(L.max_tiles * 4);
     L.off_chunk_seg = c.take(L.max_chunks * 4);
     L.off_rows = c.take(L.max_segs * (size_t)max_passes * max_bins * 4);
@@ -134,6 +135,7 @@ SegBuffers carve_seg_buffers(void* ws, const SegLayout& L) {
     B.hdr = reinterpret_cast<SegPlanHdr*>(b + L.off_plan);
     B.large = reinterpret_cast<SegDesc*>(b + L.off_large);
     B.small = reinterpret_cast<SegDesc*>(b + L.off_small);
+    B.tiny = reinterpret_cast<SegDesc*>(b + L.off_tiny);
     B.tile_seg = reinterpret_cast<uint32_t*>(b + L.off_tile_seg);
     B.chunk_seg = reinterpret_cast<uint32_t*>(b + L.off_chunk_seg);
     B.seg_rows = reinterpret_cast<uint32_t*>(b + L.off_rows);
@@ -309,7 +311,7 @@ static rs_status segmented_impl(int key_bytes, const void* keys_in, void* keys_o
     {
         KernelScope scope("plan_segments", stream);
         k_plan_from_offsets<<<(unsigned)((nseg + 255) / 256), 256, 0, stream>>>(
-            d_offsets, nseg, kLocalCap, B.tile_keys, key_bits, B.large, B.small, B.hdr, B.ws_hdr);
+            d_offsets, nseg, kLocalCap, B.tile_keys, key_bits, B.large, B.small, B.tiny, B.hdr, B.ws_hdr);
         if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
     }
     // large segments: scatter passes from keys_in (in place with an odd pass
@@ -329,8 +331,32 @@ static rs_status segmented_impl(int key_bytes, const void* keys_in, void* keys_o
     if (st != RS_OK) return st;
     // small segments: one block each, straight from the input (a block reads
     // its whole segment before writing, so in place is fine)
-    return enqueue_local_sorts(key_bytes, vals, keys_in, vals_in, keys_out, vals_out, B.small, &B.hdr->num_small,
-                               nseg, nullptr, B.ws_hdr, stream);
+    st = enqueue_local_sorts(key_bytes, vals, keys_in, vals_in, keys_out, vals_out, B.small, &B.hdr->num_small,
+                             nseg, nullptr, B.ws_hdr, stream);
+    if (st != RS_OK) return st;
+    // tiny segments: one warp each (it too reads a segment before writing it)
+    const unsigned grid = (unsigned)std::min<size_t>((nseg + 7) / 8, (size_t)device_sm_count() * 8);
+    KernelScope scope("tiny_sort", stream);
+    if (key_bytes == 4) {
+        if (vals)
+            k_tiny_sort<uint32_t, true><<<grid, 256, 0, stream>>>(static_cast<const uint32_t*>(keys_in),
+                                                                  static_cast<uint32_t*>(keys_out), vals_in, vals_out,
+                                                                  B.tiny, &B.hdr->num_tiny, B.ws_hdr);
+        else
+            k_tiny_sort<uint32_t, false><<<grid, 256, 0, stream>>>(static_cast<const uint32_t*>(keys_in),
+                                                                   static_cast<uint32_t*>(keys_out), nullptr, nullptr,
+                                                                   B.tiny, &B.hdr->num_tiny, B.ws_hdr);
+    } else {
+        if (vals)
+            k_tiny_sort<uint64_t, true><<<grid, 256, 0, stream>>>(static_cast<const uint64_t*>(keys_in),
+                                                                  static_cast<uint64_t*>(keys_out), vals_in, vals_out,
+                                                                  B.tiny, &B.hdr->num_tiny, B.ws_hdr);
+        else
+            k_tiny_sort<uint64_t, false><<<grid, 256, 0, stream>>>(static_cast<const uint64_t*>(keys_in),
+                                                                   static_cast<uint64_t*>(keys_out), nullptr, nullptr,
+                                                                   B.tiny, &B.hdr->num_tiny, B.ws_hdr);
+    }
+    return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
 
 }  // namespace rs

@@ -31,7 +31,7 @@ struct SegPlanHdr {
     uint32_t num_next;      // partitions handed to the next level (bucket sort)
     uint32_t next_tiles;
     uint32_t next_chunks;
-    uint32_t pad;
+    uint32_t num_tiny;      // segments sorted by one warp each
 };
 
 constexpr uint32_t kSegChunk = 32768;  // keys per counting block
@@ -46,12 +46,16 @@ __device__ __forceinline__ void append_large(SegDesc* list, uint32_t* count, uin
     list[atomicAdd(count, 1u)] = d;
 }
 
+// Segments of at most this many keys are sorted by one warp each.
+constexpr uint32_t kTinyCap = 256;
+
 // Segments from an offset table: empty ones are dropped, those of at most
-// `small_cap` keys go to the shared-memory list, the others to the scatter
+// kTinyCap keys go to the warp list (when `tiny` is given), those of at most
+// `small_cap` keys to the shared-memory list, the others to the scatter
 // list.  One thread per segment.
 static __global__ void k_plan_from_offsets(const uint64_t* __restrict__ offsets, size_t nseg, uint32_t small_cap,
-                                    uint32_t tile_keys, int bits, SegDesc* large, SegDesc* small, SegPlanHdr* hdr,
-                                    WsHeader* ws_hdr) {
+                                    uint32_t tile_keys, int bits, SegDesc* large, SegDesc* small, SegDesc* tiny,
+                                    SegPlanHdr* hdr, WsHeader* ws_hdr) {
     const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg) return;
     const uint64_t a = offsets[s], b = offsets[s + 1];
@@ -65,7 +69,9 @@ static __global__ void k_plan_from_offsets(const uint64_t* __restrict__ offsets,
     d.key_lo = 0;
     d.n = (uint32_t)(b - a);
     d.bits = (uint32_t)bits;
-    if (d.n <= small_cap)
+    if (tiny && d.n <= kTinyCap)
+        tiny[atomicAdd(&hdr->num_tiny, 1u)] = d;
+    else if (d.n <= small_cap)
         small[atomicAdd(&hdr->num_small, 1u)] = d;
     else
         append_large(large, &hdr->num_large, &hdr->total_tiles, &hdr->total_chunks, d, tile_keys);
@@ -389,6 +395,92 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
         }
         __syncthreads();
     }
+}
+
+// One tiny segment ranked by one warp with KPL keys per lane (KPL * 32 >= m):
+// each lane's keys are compared with every key of the segment in the warp's
+// shared-memory row (the same word for every lane: a broadcast), four at a
+// time; a key's rank is the number of keys before it in stable order
+// (smaller, or equal and earlier), and the key (and its value) is written
+// there.
+template <int KPL, typename KeyT, bool VALS>
+__device__ __forceinline__ void rank_tiny(const KeyT* row, uint32_t m, const KeyT (&k)[kTinyCap / 32],
+                                          const uint32_t (&v)[VALS ? kTinyCap / 32 : 1], KeyT* kout,
+                                          uint32_t* vout, int lane) {
+    uint32_t r[KPL];
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) r[j] = 0;
+    uint32_t q = 0;
+    for (; q + 4 <= m; q += 4) {
+        const KeyT o0 = row[q], o1 = row[q + 1], o2 = row[q + 2], o3 = row[q + 3];
+#pragma unroll
+        for (int j = 0; j < KPL; ++j) {
+            const uint32_t i = (uint32_t)j * 32 + lane;
+            r[j] += ((o0 < k[j]) | ((o0 == k[j]) & (q < i))) + ((o1 < k[j]) | ((o1 == k[j]) & (q + 1 < i))) +
+                    ((o2 < k[j]) | ((o2 == k[j]) & (q + 2 < i))) + ((o3 < k[j]) | ((o3 == k[j]) & (q + 3 < i)));
+        }
+    }
+    for (; q < m; ++q) {
+        const KeyT o = row[q];
+#pragma unroll
+        for (int j = 0; j < KPL; ++j) r[j] += (o < k[j]) | ((o == k[j]) & (q < (uint32_t)j * 32 + lane));
+    }
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) {
+        const uint32_t i = (uint32_t)j * 32 + lane;
+        if (i < m && r[j] < m) {
+            kout[r[j]] = k[j];
+            if (VALS) vout[r[j]] = v[j];
+        }
+    }
+}
+
+// Warp sort of tiny segments: each warp takes segments of at most kTinyCap
+// keys from the list, copies the keys to its shared-memory row and ranks
+// them (rank_tiny, with as many keys per lane as the segment needs).  Keys at
+// or above 2^bits are reported in hdr.
+template <typename KeyT, bool VALS>
+__global__ void __launch_bounds__(256) k_tiny_sort(const KeyT* __restrict__ keys_in, KeyT* keys_out,
+                                                   const uint32_t* __restrict__ vals_in, uint32_t* vals_out,
+                                                   const SegDesc* __restrict__ segs, const uint32_t* count,
+                                                   WsHeader* hdr) {
+    constexpr int kWarps = 256 / 32, kPerLane = kTinyCap / 32;
+    __shared__ KeyT s_keys[kWarps][kTinyCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    KeyT* row = s_keys[warp];
+    const uint32_t nseg = *count;
+    bool bad = false;
+    for (uint32_t si = blockIdx.x * kWarps + warp; si < nseg; si += gridDim.x * kWarps) {
+        const SegDesc sd = segs[si];
+        const uint32_t m = sd.n;
+        KeyT k[kPerLane];
+        uint32_t v[VALS ? kPerLane : 1];
+#pragma unroll
+        for (int j = 0; j < kPerLane; ++j) {
+            const uint32_t i = (uint32_t)j * 32 + lane;
+            k[j] = 0;
+            if (VALS) v[j] = 0;
+            if (i < m) {
+                k[j] = keys_in[sd.start + i];
+                if (VALS) v[j] = vals_in[sd.start + i];
+                row[i] = k[j];
+                bad |= sd.bits < 8 * sizeof(KeyT) && (k[j] >> sd.bits) != 0;
+            }
+        }
+        __syncwarp();
+        KeyT* kout = keys_out + sd.start;
+        uint32_t* vout = VALS ? vals_out + sd.start : nullptr;
+        if (m <= 32)
+            rank_tiny<1, KeyT, VALS>(row, m, k, v, kout, vout, lane);
+        else if (m <= 64)
+            rank_tiny<2, KeyT, VALS>(row, m, k, v, kout, vout, lane);
+        else if (m <= 128)
+            rank_tiny<4, KeyT, VALS>(row, m, k, v, kout, vout, lane);
+        else
+            rank_tiny<8, KeyT, VALS>(row, m, k, v, kout, vout, lane);
+        __syncwarp();
+    }
+    if (bad && hdr) set_device_error(hdr, RS_ERR_KEY_RANGE, blockIdx.x);
 }
 
 // Bucket function placeholder for plain segmented sorts (no bucket step).

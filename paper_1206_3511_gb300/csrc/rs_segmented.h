@@ -101,6 +101,7 @@ struct SegBuffers {
     SegPlanHdr* hdr;
     SegDesc* large;        // [max_segs]
     SegDesc* small;        // [max_segs]
+    SegDesc* tiny;         // [max_segs] segments for the warp sort (null: none)
     uint32_t* tile_seg;    // [max_tiles]
     uint32_t* chunk_seg;   // [max_chunks]
     uint32_t* seg_rows;    // [max_segs][max_passes][max_bins]
@@ -116,7 +117,7 @@ struct SegBuffers {
 // Workspace layout of a segmented sort: sizes for every region, the offsets
 // filled in by carve_seg_buffers.
 struct SegLayout {
-    size_t off_plan, off_large, off_small, off_tile_seg, off_chunk_seg, off_rows, off_status0, off_status1,
+    size_t off_plan, off_large, off_small, off_tiny, off_tile_seg, off_chunk_seg, off_rows, off_status0, off_status1,
         off_tmp_keys, off_tmp_vals, total;
     size_t max_segs, max_tiles, max_chunks;
     int max_passes, max_bins;

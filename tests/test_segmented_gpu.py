@@ -200,3 +200,32 @@ def test_every_compiled_shape_gives_identical_bits(rs, oracle, kb, with_values):
     ok = torch.empty_like(kd)
     ov = torch.empty_like(vd) if with_values else None
     assert fn(kd, ok, vd, ov, od, len(sizes), n, 0, ws, ws.numel(), None, (7,) + shapes[0]) == 9  # UNSUPPORTED
+
+
+@pytest.mark.parametrize("kb,with_values,in_place", [(4, False, False), (4, True, True), (8, False, True),
+                                                     (8, True, False)])
+def test_many_tiny_segments(rs, oracle, kb, with_values, in_place):
+    """Thousands of segments of 0..256 keys (sorted one warp each) mixed with
+    a few larger ones, with repeated keys so that stability shows."""
+    sizes = synth.uniform_below(6000, 257, 90 + kb, 91).astype(np.int64)
+    sizes[::500] = 5000  # a few shared-memory segments
+    sizes[7] = 20_000    # and a scatter-pass one
+    n = int(sizes.sum())
+    keys = (synth.u32(n, 92, 0) >> np.uint32(26)) if kb == 4 else (synth.keys_u64(n, 64, seed=92) >> np.uint64(58))
+    vals = synth.index_values(n) if with_values else None
+    _check(rs, oracle, keys, sizes, vals, in_place=in_place, what=f"tiny kb={kb} v={with_values} ip={in_place}")
+
+
+def test_key_above_key_bits_in_a_tiny_segment_is_reported(rs):
+    import torch
+
+    sizes = [100, 20_000, 40]
+    n = sum(sizes)
+    keys = synth.u32(n, 93, 0) >> np.uint32(20)  # 12-bit keys
+    keys[20_120] = 1 << 12  # inside the last (warp) segment
+    kd = to_dev(keys)
+    off = to_dev(synth.segment_offsets(sizes))
+    ws = rs.workspace(rs.rs_segmented_workspace_bytes(4, 0, n, 3, 12))
+    out = torch.empty_like(kd)
+    assert rs.rs_sort_segmented_u32(kd, out, None, None, off, 3, n, 12, ws, ws.numel()) == 0
+    assert rs.get_status(ws) == 3  # RS_ERR_KEY_RANGE
