@@ -121,11 +121,6 @@ struct KeyXform {
     }
 };
 
-template <typename KeyT>
-__device__ __forceinline__ uint32_t digit_of(KeyT k, int shift, uint32_t mask) {
-    return (uint32_t)(k >> shift) & mask;
-}
-
 // Exclusive prefix sum of one value per thread across the block.  s_warp needs
 // BLOCK/32 + 1 words; the block total lands in s_warp[BLOCK/32].  Contains
 // __syncthreads() and must be reached by every thread.
