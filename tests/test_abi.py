@@ -86,3 +86,45 @@ def test_argument_errors_are_returned_before_any_launch(lib):
     assert _lib.rs_sort_u32(None, None, None, None, 0, 32, fake, 1 << 20, 0) == 0
     # a configuration that is not compiled
     assert _lib.rs_sort_u32_ex(fake, fake + 4096, None, None, 16, 32, fake, 1 << 20, 0, (8, 256, 3)) == 9
+
+
+def test_argument_errors_of_the_other_entry_points(lib):
+    """Bucket, segmented, typed, bucket-count and server entry points reject
+    bad arguments on the host, before any CUDA call (so this runs without a
+    GPU)."""
+    from paper_1206_3511_gb300 import _lib
+
+    _lib.load()
+    fake = 1 << 40
+    big_ws = fake + (1 << 30)
+    # bucket sort: values without outputs, overlap, misaligned keys, workspace
+    assert _lib.bs_sort_u32(fake, fake + 4096, fake, None, 16, 0, 99, 0, big_ws, 1 << 30, 0) == 1
+    assert _lib.bs_sort_u32(fake, fake + 8, None, None, 16, 0, 99, 0, big_ws, 1 << 30, 0) == 1
+    assert _lib.bs_sort_u64(fake + 4, fake + 4096, None, None, 16, 0, 99, 0, big_ws, 1 << 30, 0) == 1
+    assert _lib.bs_sort_u32(fake, fake + 4096, None, None, 16, 0, 99, 0, None, 1 << 30, 0) == 2
+    assert _lib.bs_sort_u32(fake, fake + 4096, None, None, 1000, 0, 99, 0, big_ws, 64, 0) == 2
+    assert _lib.bs_sort_u32(fake, fake + 4096, None, None, 16, 0, 99, (1 << 32) + 1, big_ws, 1 << 30, 0) == 1
+    assert _lib.bs_sort_u32(None, None, None, None, 0, 0, 99, 0, big_ws, 1 << 30, 0) == 0  # n == 0
+    # segmented: key_bits, workspace, a shape that is not compiled
+    assert _lib.rs_sort_segmented_u32(fake, fake + 4096, None, None, fake, 3, 16, 33, big_ws, 1 << 30, 0) == 1
+    assert _lib.rs_sort_segmented_u32(fake, fake + 4096, None, None, fake, 3, 16, 32, None, 1 << 30, 0) == 2
+    assert _lib.rs_sort_segmented_u32(fake, fake + 4096, None, None, fake, 3, 1000, 32, big_ws, 64, 0) == 2
+    assert _lib.rs_sort_segmented_u32_ex(fake, fake + 4096, None, None, fake, 3, 16, 32, big_ws, 1 << 30, 0,
+                                         (7, 256, 18)) == 9
+    assert _lib.rs_sort_segmented_u32(fake, fake + 4096, None, None, fake, 0, 0, 32, big_ws, 1 << 30, 0) == 0
+    # typed keys: kind, width
+    assert _lib.rs_sort_typed(3, 4, 0, fake, fake + 4096, None, None, 16, big_ws, 1 << 30, 0) == 1
+    assert _lib.rs_sort_typed(1, 2, 0, fake, fake + 4096, None, None, 16, big_ws, 1 << 30, 0) == 1
+    assert _lib.rs_sort_typed(2, 8, 1, fake, fake + 8, None, None, 16, big_ws, 1 << 30, 0) == 1  # overlap
+    # bucket counts: bounds, bucket count, output pointer, workspace
+    assert _lib.bs_bucket_counts_u32(fake, 16, 9, 5, 4, fake + 4096, big_ws, 4096, 0) == 1
+    assert _lib.bs_bucket_counts_u32(fake, 16, 0, 99, 0, fake + 4096, big_ws, 4096, 0) == 1
+    assert _lib.bs_bucket_counts_u32(fake, 16, 0, 99, 4, None, big_ws, 4096, 0) == 1
+    assert _lib.bs_bucket_counts_u64(fake, 16, 0, 99, 4, fake + 4096, big_ws, 64, 0) == 2
+    # server: configuration
+    bad = _lib.RsServerConfig(None, 1 << 20, 0, 4, 8, 0)
+    assert _lib.rs_server_create(bad)[0] == 1
+    bad = _lib.RsServerConfig(fake, 1 << 20, 0, 0, 8, 0)  # no streams
+    assert _lib.rs_server_create(bad)[0] == 1
+    bad = _lib.RsServerConfig(fake + 8, 1 << 20, 0, 4, 8, 0)  # misaligned pool
+    assert _lib.rs_server_create(bad)[0] == 1
