@@ -1162,7 +1162,8 @@ def run_served(args):
                 "submit_lag_p99_ms": _pct(lag, 99), "submitted": int(st.submitted),
                 "admitted": int(st.submitted - st.rejected), "rejected": int(st.rejected),
                 "completed": int(st.completed), "batches": int(st.batches),
-                "batched_requests": int(st.batched_requests), "max_in_use_gb": st.max_in_use_bytes / 1e9}
+                "batched_requests": int(st.batched_requests), "max_queued": int(st.max_queued),
+                "max_in_use_gb": st.max_in_use_bytes / 1e9}
 
     def knee(rows, mode):
         """The highest rate whose p99 stays within 4x the p99 at the lowest rate."""

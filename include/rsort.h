@@ -357,6 +357,7 @@ typedef struct rs_server_stats {
     uint64_t submitted, completed, rejected, queued;
     size_t in_use_bytes, max_in_use_bytes, budget_bytes;
     uint64_t batches, batched_requests;
+    uint64_t max_queued; /* the longest the queue of waiting requests has been */
 } rs_server_stats;
 
 RS_API rs_status rs_server_create(const rs_server_config* cfg, rs_server** out);

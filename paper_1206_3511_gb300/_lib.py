@@ -55,7 +55,8 @@ class RsResult(_c.Structure):
 class RsServerStats(_c.Structure):
     _fields_ = [("submitted", _c.c_uint64), ("completed", _c.c_uint64), ("rejected", _c.c_uint64),
                 ("queued", _c.c_uint64), ("in_use_bytes", _c.c_size_t), ("max_in_use_bytes", _c.c_size_t),
-                ("budget_bytes", _c.c_size_t), ("batches", _c.c_uint64), ("batched_requests", _c.c_uint64)]
+                ("budget_bytes", _c.c_size_t), ("batches", _c.c_uint64), ("batched_requests", _c.c_uint64),
+                ("max_queued", _c.c_uint64)]
 
 
 class RsPlanDesc(_c.Structure):

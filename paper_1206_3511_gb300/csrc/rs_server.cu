@@ -117,6 +117,7 @@ struct ServerImpl {
     std::vector<Slot> slots;
     uint64_t next_ticket = 1;
     size_t in_use = 0, max_in_use = 0;
+    size_t max_queued = 0;  // longest the queue of waiting requests has been
     uint64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batched_requests = 0;
     bool stopping = false, cancel = false;
     std::thread worker;
@@ -416,6 +417,7 @@ rs_status rs_server_submit(rs_server* s, const rs_request* req, uint64_t* ticket
     r.status = RS_ERR_NOT_READY;
     m.reqs[r.ticket] = r;
     m.pending.push_back(r.ticket);
+    m.max_queued = std::max(m.max_queued, m.pending.size());
     ++m.submitted;
     *ticket = r.ticket;
     m.cv.notify_all();
@@ -479,6 +481,7 @@ rs_status rs_server_get_stats(rs_server* s, rs_server_stats* out) {
     out->budget_bytes = m.cfg.budget_bytes;
     out->batches = m.batches;
     out->batched_requests = m.batched_requests;
+    out->max_queued = m.max_queued;
     return RS_OK;
 }
 

@@ -86,7 +86,8 @@ def test_budget_is_never_exceeded_and_everything_completes(rs):
         for t in tickets:
             assert srv.wait(t, 60_000) == 0
         st = srv.stats()
-        assert st.completed == 24
+        assert st.completed == 24 and st.queued == 0
+        assert 1 <= st.max_queued <= 24
         assert 0 < st.max_in_use_bytes <= budget
         for kd, ko in outs:
             a = ko.cpu().numpy().view(np.uint32)
@@ -146,6 +147,7 @@ def test_shutdown_cancels_queued_requests(rs):
         srv.submit(keys, ko)
     st = srv.stats()
     assert st.submitted == 40 and st.queued >= 30
+    assert st.queued <= st.max_queued <= 40
     t0 = time.perf_counter()
     assert rs.rs_server_destroy(srv.handle, True) == 0
     elapsed = time.perf_counter() - t0
