@@ -476,80 +476,72 @@ def run_ours(args):
         a = chk.cpu().numpy().view(np.uint64)
     assert np.all(a[1:] >= a[:-1]), "bench output not sorted"
 
-    # end to end through the public API: every step uploads its keys (and
-    # values) from pinned host memory, sorts, and downloads the sorted keys
-    # (and values).  Serial: one stream, nothing overlaps.
-    h_out = torch.empty_like(h_keys).pin_memory()
-    h_outv = torch.empty_like(h_vals).pin_memory() if has_v else None
+    # end to end through the host-buffer C calls (rs_sort_host_* /
+    # bs_sort_host_*): every step copies its keys (and values) from pinned
+    # host memory into a device buffer, sorts them there and copies the sorted
+    # keys (and values) back, all inside one library call.  Serial: one
+    # stream, nothing overlaps.
     e2e_steps = max(3, min(args.steps, 20))
+    if algo == "bucket":
+        hbytes = rs.rs_host_sort_bytes(rs.RS_ALGO_BUCKET, kb, has_v, n, 0, nb)
+        hfn = rs.bs_sort_host_u32 if kb == 4 else rs.bs_sort_host_u64
 
-    def serial_step():
-        d_keys.copy_(h_keys, non_blocking=True)
-        if has_v:
-            d_vals.copy_(h_vals, non_blocking=True)
-        step()
-        h_out.copy_(d_out, non_blocking=True)
-        if has_v:
-            h_outv.copy_(d_outv, non_blocking=True)
+        def host_call(hk_out, hv_out, buf, strm):
+            return hfn(h_keys, hk_out, h_vals, hv_out, n, lo, hi, nb, buf, buf.numel(), strm)
+    else:
+        hbytes = rs.rs_host_sort_bytes(rs.RS_ALGO_RADIX, kb, has_v, n, key_bits, 0)
+        hfn = rs.rs_sort_host_u32 if kb == 4 else rs.rs_sort_host_u64
+
+        def host_call(hk_out, hv_out, buf, strm):
+            return hfn(h_keys, hk_out, h_vals, hv_out, n, key_bits, buf, buf.numel(), strm)
+
+    S = 3
+    hbufs = [rs.workspace(hbytes, d_keys.device) for _ in range(S)]
+    houts = [torch.empty_like(h_keys).pin_memory() for _ in range(S)]
+    houtv = [torch.empty_like(h_vals).pin_memory() if has_v else None for _ in range(S)]
+
+    def host_step(j, strm):
+        rc = host_call(houts[j], houtv[j], hbufs[j], strm)
+        if rc:
+            raise rs.SortError(rc, "host-buffer sort")
 
     for _ in range(2):
-        serial_step()
+        host_step(0, stream)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(e2e_steps):
-        serial_step()
+        host_step(0, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_serial_ms = e0.elapsed_time(e1)
+    h_out = houts[0].clone()
 
-    # Pipelined: the same steps through three buffer slots with uploads,
-    # sorts and downloads on three streams, so that step i+1's upload and
-    # step i-1's download run while step i sorts (how a stream of sort jobs
-    # is served).  A slot is reused only after its last download finished.
-    S = 3
-    up, comp, down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    slots = [{"k": torch.empty_like(d_keys), "o": torch.empty_like(d_keys),
-              "v": torch.empty_like(d_vals) if has_v else None, "ov": torch.empty_like(d_vals) if has_v else None,
-              "hk": torch.empty_like(h_keys).pin_memory(),
-              "hv": torch.empty_like(h_vals).pin_memory() if has_v else None} for _ in range(S)]
-    ev = {x: [torch.cuda.Event() for _ in range(S)] for x in ("up", "comp", "down")}
-
-    def pipe_step(i):
-        j = i % S
-        sl = slots[j]
-        if i >= S:
-            up.wait_event(ev["down"][j])
-        with torch.cuda.stream(up):
-            sl["k"].copy_(h_keys, non_blocking=True)
-            if has_v:
-                sl["v"].copy_(h_vals, non_blocking=True)
-        ev["up"][j].record(up)
-        comp.wait_event(ev["up"][j])
-        rc = sort_into(sl["k"], sl["o"], sl["v"], sl["ov"], ws, comp)
-        if rc:
-            raise rs.SortError(rc, "sort")
-        ev["comp"][j].record(comp)
-        down.wait_event(ev["comp"][j])
-        with torch.cuda.stream(down):
-            sl["hk"].copy_(sl["o"], non_blocking=True)
-            if has_v:
-                sl["hv"].copy_(sl["ov"], non_blocking=True)
-        ev["down"][j].record(down)
-
-    for i in range(S):
-        pipe_step(i)
+    # Pipelined: successive calls go round-robin to three streams, each with
+    # its own device buffer and host output, so that one call's upload and
+    # another's download run while a third sorts (how a stream of sort jobs
+    # is served).  Calls on one stream run in order.
+    hstreams = [torch.cuda.Stream() for _ in range(S)]
+    for j in range(S):
+        host_step(j, hstreams[j])
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(up)
+    p0.record(stream)
+    for hs in hstreams:
+        hs.wait_event(p0)
     for i in range(e2e_steps):
-        pipe_step(S + i)
-    p1.record(down)
+        host_step(i % S, hstreams[i % S])
+    for hs in hstreams:
+        done = torch.cuda.Event()
+        done.record(hs)
+        stream.wait_event(done)
+    p1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = p0.elapsed_time(p1)
-    last = slots[(S + e2e_steps - 1) % S]["hk"]
-    assert torch.equal(last, h_out), "pipelined result differs from the serial one"
+    for j in range(S):
+        assert rs.get_status(hbufs[j]) == 0
+        assert torch.equal(houts[j], h_out), "pipelined result differs from the serial one"
 
     ms, e2e_ms, e2e_serial_ms = max_over_ranks([ms, e2e_ms, e2e_serial_ms], device=dev)
     if rank != 0:
@@ -648,7 +640,9 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (%d MB keys vs 129 MB L2), no flush" % (n * kb // 2**20)},
         "clocks": clocks, "gpu_launches": launches, "roofline": roofline, "whole_sort": whole,
         "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "mode": "pipelined: 3 buffer slots; uploads, sorts and downloads on three streams overlap across steps",
+                "api": "rs_sort_host_u32/u64 or bs_sort_host_u32/u64 (host arrays in and out, one call per step)",
+                "mode": "pipelined: calls round-robin over 3 streams with their own device buffers, so one call's "
+                        "copies overlap another's sort",
                 "serial_value": e2e_serial, "steps": e2e_steps},
         "cpu_baseline": cpu, "context": lib,
     }
@@ -804,31 +798,39 @@ def run_batched(args):
     torch.cuda.synchronize()
     batched_lat = g0.elapsed_time(g1)
 
-    # end to end: pinned host keys -> device -> graph -> host
+    # end to end through the host-buffer segmented call
+    # (rs_sort_segmented_host_u32): pinned host keys and offsets in, sorted
+    # keys out, one library call copying in, sorting with the tuned shape and
+    # copying out.  Serial: the whole batch in one call per step.
     h_keys = torch.empty(n_total, dtype=torch.int32, pin_memory=True)
     h_keys.copy_(d_keys)
     h_out = torch.empty_like(h_keys, pin_memory=True)
+    h_off = torch.from_numpy(off.view(np.int64)).pin_memory()
     e2e_steps = max(3, min(args.steps, 5))
-    d_keys.copy_(h_keys, non_blocking=True)
-    plan.launch(stream)
-    h_out.copy_(d_out, non_blocking=True)
+    hbytes = rs.rs_segmented_host_bytes(4, 0, n_total, count, 32)
+    hbuf = rs.workspace(hbytes, d_keys.device)
+
+    def host_batch(strm):
+        rs.check(rs.rs_sort_segmented_host_u32(h_keys, h_out, None, None, h_off, count, n_total, 32, hbuf, hbytes,
+                                               strm, seg_shape), "segmented host-buffer sort")
+
+    host_batch(stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(e2e_steps):
-        d_keys.copy_(h_keys, non_blocking=True)
-        plan.launch(stream)
-        h_out.copy_(d_out, non_blocking=True)
+        host_batch(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_serial_ms = e0.elapsed_time(e1)
+    assert rs.get_status(hbuf) == 0
+    del hbuf
 
-    # Pipelined end to end: the batch in G groups of consecutive arrays, each
-    # uploaded, sorted (segmented, the tuned shape) and downloaded on its own
-    # stream stage, so that one group's copies overlap other groups' sorts.
-    # A group's input waits for its previous sort, its output for its
-    # previous download.
-    G = 8
+    # Pipelined end to end: the batch in G groups of consecutive arrays, one
+    # host-buffer call per group, the calls round-robin over three streams
+    # with their own device buffers, so that one group's copies overlap other
+    # groups' sorts.
+    G, S = 8, 3
     bounds = [int(x) for x in np.linspace(0, count, G + 1).round()]
     groups = []
     for g in range(G):
@@ -836,42 +838,36 @@ def run_batched(args):
         if b <= a:
             continue
         k0, k1 = int(off[a]), int(off[b])
-        goff = torch.from_numpy((off[a:b + 1] - off[a]).view(np.int64)).to(dev)
+        goff = torch.from_numpy((off[a:b + 1] - off[a]).view(np.int64)).pin_memory()
         groups.append((a, b, k0, k1, goff))
-    gws = rs.workspace(max(rs.rs_segmented_workspace_bytes(4, 0, k1 - k0, b - a, 32) for a, b, k0, k1, _ in groups),
-                       d_keys.device)
-    up, comp, down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    ev = {x: [torch.cuda.Event() for _ in groups] for x in ("up", "comp", "down")}
-    started = [False] * len(groups)
+    gbytes = max(rs.rs_segmented_host_bytes(4, 0, k1 - k0, b - a, 32) for a, b, k0, k1, _ in groups)
+    gbufs = [rs.workspace(gbytes, d_keys.device) for _ in range(S)]
+    gstreams = [torch.cuda.Stream() for _ in range(S)]
 
     def pipe_step():
         for gi, (a, b, k0, k1, goff) in enumerate(groups):
-            if started[gi]:
-                up.wait_event(ev["comp"][gi])
-            with torch.cuda.stream(up):
-                d_keys[k0:k1].copy_(h_keys[k0:k1], non_blocking=True)
-            ev["up"][gi].record(up)
-            comp.wait_event(ev["up"][gi])
-            if started[gi]:
-                comp.wait_event(ev["down"][gi])
-            rs.check(rs.rs_sort_segmented_u32_ex(d_keys[k0:k1], d_out[k0:k1], None, None, goff, b - a, k1 - k0, 32,
-                                                 gws, gws.numel(), comp, seg_shape), "segmented group")
-            ev["comp"][gi].record(comp)
-            down.wait_event(ev["comp"][gi])
-            with torch.cuda.stream(down):
-                h_out[k0:k1].copy_(d_out[k0:k1], non_blocking=True)
-            ev["down"][gi].record(down)
-            started[gi] = True
+            j = gi % S
+            rs.check(rs.rs_sort_segmented_host_u32(h_keys[k0:k1], h_out[k0:k1], None, None, goff, b - a, k1 - k0,
+                                                   32, gbufs[j], gbytes, gstreams[j], seg_shape),
+                     "segmented host-buffer group")
 
     pipe_step()
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(up)
+    p0.record(stream)
+    for gs in gstreams:
+        gs.wait_event(p0)
     for _ in range(e2e_steps):
         pipe_step()
-    p1.record(down)
+    for gs in gstreams:
+        done = torch.cuda.Event()
+        done.record(gs)
+        stream.wait_event(done)
+    p1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = p0.elapsed_time(p1)
+    for j in range(S):
+        assert rs.get_status(gbufs[j]) == 0
     for i in (0, count // 2, count - 1):  # the downloaded result, spot-checked
         a, b = int(off[i]), int(off[i + 1])
         assert torch.equal(h_out[a:b], d_out[a:b].cpu()), f"pipelined result wrong in array {i}"
@@ -929,8 +925,9 @@ def run_batched(args):
         "kernels": {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in kstats.items()},
         "e2e": {"value": job_rate(n_total * e2e_steps, world, e2e_ms), "unit": "Gkeys/s",
                 "h2d_bytes_per_step": n_total * 4, "d2h_bytes_per_step": n_total * 4,
-                "mode": "pipelined: the batch in 8 groups of consecutive arrays, each uploaded, sorted and "
-                        "downloaded on its own stream stage",
+                "api": "rs_sort_segmented_host_u32 (host arrays and offsets in, sorted keys out)",
+                "mode": "pipelined: the batch in 8 groups of consecutive arrays, one call per group, the calls "
+                        "round-robin over 3 streams with their own device buffers",
                 "serial_value": job_rate(n_total * e2e_steps, world, e2e_serial_ms), "steps": e2e_steps},
         "cpu_baseline": cpu,
     }

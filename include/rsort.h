@@ -14,8 +14,9 @@
  *
  * Conventions shared by every call below:
  *   - All key, value, offset and workspace pointers are DEVICE pointers of the
- *     current CUDA device.  The caller owns and allocates all of them; no sort
- *     call allocates device memory.
+ *     current CUDA device, except the h_* arrays of the host-buffer sorts
+ *     (rs_sort_host_*, bs_sort_host_*, rs_sort_segmented_host_*).  The caller owns and allocates all of
+ *     them; no sort call allocates device memory.
  *   - Calls are asynchronous: they validate their arguments on the host,
  *     enqueue kernels on `stream` and return.  Argument errors are returned
  *     synchronously and nothing is enqueued.  Errors found on the device (a
@@ -403,6 +404,73 @@ RS_API rs_status rs_server_destroy(rs_server* s, int cancel_pending);
 #define RS_NOALLOC_MAX_KEYS ((size_t)1 << 20)
 RS_API rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
                                      uint32_t* vals_out, size_t n, int key_bits, rs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Sorting arrays that live in host memory.  The paper has no counterpart (its
+ * arrays are in the one memory of a CPU); these calls solve Sec. 2's problem
+ * for a caller whose keys are in host memory.
+ *
+ * rs_sort_host_u32 / rs_sort_host_u64 (radix) and bs_sort_host_u32 /
+ * bs_sort_host_u64 (bucket) enqueue on `stream`, in this order: a copy of the
+ * keys (and values) from host memory into `dev_buf`; the same sort as
+ * rs_sort_u32 / rs_sort_u64 or bs_sort_u32 / bs_sort_u64, run in place
+ * there; and a copy of the sorted keys (and values) back into host memory.
+ * The result in h_keys_out / h_vals_out equals that of the device call.
+ *   - h_keys_in, h_keys_out, h_vals_in, h_vals_out are HOST pointers with the
+ *     keys' natural alignment (device memory is RS_ERR_INVALID_ARG).
+ *     h_keys_out == h_keys_in is allowed, likewise for the values; any other
+ *     overlap is RS_ERR_INVALID_ARG.  The values are both NULL (keys only)
+ *     or both non-NULL.
+ *   - With page-locked host memory (cudaHostAlloc, cudaHostRegister) the call
+ *     returns at once and the copies run asynchronously; the host buffers
+ *     must then stay untouched until the stream has passed the call.  With
+ *     pageable memory the CUDA runtime stages the copies and the call may
+ *     block the calling thread.
+ *   - dev_buf is a DEVICE buffer owned by the caller, 256-byte aligned and at
+ *     least rs_host_sort_bytes(algo, key_bytes, has_values, n, key_bits,
+ *     num_buckets) bytes (RS_ERR_WORKSPACE otherwise).  It holds the sort's
+ *     workspace at its start, so rs_get_status(dev_buf, stream) reads the
+ *     device status of the call, then the keys and the values.  Calls on
+ *     different streams with different dev_buf run concurrently: one call's
+ *     copies overlap another call's sort.
+ *   - key_bits (radix), min_key, max_key and num_buckets (bucket) as for the
+ *     device calls.
+ * rs_host_sort_bytes returns 0 for an invalid algo, key_bytes, key_bits, n or
+ * num_buckets.
+ */
+RS_API size_t rs_host_sort_bytes(int algo, int key_bytes, int has_values, size_t n, int key_bits,
+                                 size_t num_buckets);
+RS_API rs_status rs_sort_host_u32(const uint32_t* h_keys_in, uint32_t* h_keys_out, const uint32_t* h_vals_in,
+                                  uint32_t* h_vals_out, size_t n, int key_bits, void* dev_buf,
+                                  size_t dev_buf_bytes, rs_stream_t stream);
+RS_API rs_status rs_sort_host_u64(const uint64_t* h_keys_in, uint64_t* h_keys_out, const uint32_t* h_vals_in,
+                                  uint32_t* h_vals_out, size_t n, int key_bits, void* dev_buf,
+                                  size_t dev_buf_bytes, rs_stream_t stream);
+RS_API rs_status bs_sort_host_u32(const uint32_t* h_keys_in, uint32_t* h_keys_out, const uint32_t* h_vals_in,
+                                  uint32_t* h_vals_out, size_t n, uint32_t min_key, uint32_t max_key,
+                                  size_t num_buckets, void* dev_buf, size_t dev_buf_bytes, rs_stream_t stream);
+RS_API rs_status bs_sort_host_u64(const uint64_t* h_keys_in, uint64_t* h_keys_out, const uint32_t* h_vals_in,
+                                  uint32_t* h_vals_out, size_t n, uint64_t min_key, uint64_t max_key,
+                                  size_t num_buckets, void* dev_buf, size_t dev_buf_bytes, rs_stream_t stream);
+
+/* The segmented sort of rs_sort_segmented_u32_ex / _u64_ex on host arrays:
+ * h_seg_offsets is a HOST array of nseg+1 uint64 offsets (same rules as
+ * d_seg_offsets), copied into dev_buf with the keys and values; cfg as for
+ * the _ex calls (NULL = default).  dev_buf: at least
+ * rs_segmented_host_bytes(key_bytes, has_values, n_total, nseg, key_bits)
+ * bytes.  Other rules as for rs_sort_host_u32 above; the offsets must not
+ * overlap the outputs.  nseg = 0 or n_total = 0 is a no-op. */
+RS_API size_t rs_segmented_host_bytes(int key_bytes, int has_values, size_t n_total, size_t nseg, int key_bits);
+RS_API rs_status rs_sort_segmented_host_u32(const uint32_t* h_keys_in, uint32_t* h_keys_out,
+                                            const uint32_t* h_vals_in, uint32_t* h_vals_out,
+                                            const uint64_t* h_seg_offsets, size_t nseg, size_t n_total,
+                                            int key_bits, void* dev_buf, size_t dev_buf_bytes, rs_stream_t stream,
+                                            const rs_config* cfg);
+RS_API rs_status rs_sort_segmented_host_u64(const uint64_t* h_keys_in, uint64_t* h_keys_out,
+                                            const uint32_t* h_vals_in, uint32_t* h_vals_out,
+                                            const uint64_t* h_seg_offsets, size_t nseg, size_t n_total,
+                                            int key_bits, void* dev_buf, size_t dev_buf_bytes, rs_stream_t stream,
+                                            const rs_config* cfg);
 
 /* ---------------------------------------------------------------------------
  * Device status.

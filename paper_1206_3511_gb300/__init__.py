@@ -21,6 +21,8 @@ from ._lib import (rs_sort_segmented_u32_ex, rs_sort_segmented_u64_ex, rs_server
                    rs_counting_pass_u32, rs_counting_pass_u64, rs_default_config, rs_digit_counts_u32,
                    rs_digit_counts_u64, rs_get_status, rs_launch_count, rs_profile_enable, rs_profile_read,
                    rs_set_debug, rs_sort_u32, rs_sort_u32_ex, rs_sort_u32_noalloc, rs_sort_u64,
+                   rs_host_sort_bytes, rs_sort_host_u32, rs_sort_host_u64, bs_sort_host_u32, bs_sort_host_u64,
+                   rs_segmented_host_bytes, rs_sort_segmented_host_u32, rs_sort_segmented_host_u64,
                    rs_sort_u64_ex, rs_status_string, rs_version, rs_workspace_bytes, rs_workspace_bytes_cfg)
 
 __all__ = [
@@ -36,7 +38,9 @@ __all__ = [
     "rs_plan_launch", "RS_PLAN_RADIX", "RS_PLAN_BUCKET", "RS_PLAN_SEGMENTED", "RsRequest", "RsResult",
     "RsServerConfig", "RsServerStats", "rs_server_create", "rs_server_destroy", "rs_server_get_stats",
     "rs_server_poll", "rs_server_submit", "rs_server_wait", "rs_server_release", "rs_sort_segmented_u32_ex",
-    "rs_sort_segmented_u64_ex",
+    "rs_sort_segmented_u64_ex", "rs_host_sort_bytes", "rs_sort_host_u32", "rs_sort_host_u64", "sort_host",
+    "bs_sort_host_u32", "bs_sort_host_u64", "rs_segmented_host_bytes", "rs_sort_segmented_host_u32",
+    "rs_sort_segmented_host_u64",
 ]
 
 
@@ -99,6 +103,42 @@ def sort(keys, values=None, key_bits: int = 0, out=None, out_values=None, ws=Non
         ws = workspace(nbytes, keys.device)
     fn = rs_sort_u32_ex if kb == 4 else rs_sort_u64_ex
     check(fn(keys, out, values, out_values, n, key_bits, ws, ws.numel(), stream, cfg), "rs_sort")
+    return out, out_values
+
+
+def sort_host(keys, values=None, key_bits: int = 0, out=None, out_values=None, dev_buf=None, stream=None,
+              algo: int = RS_ALGO_RADIX, min_key=None, max_key=None, num_buckets: int = 0):
+    """Sort a 1-D CPU tensor on the GPU through the host-buffer calls:
+    rs_sort_host_* for algo RS_ALGO_RADIX, bs_sort_host_* for RS_ALGO_BUCKET
+    (bounds and bucket count as in bucket_sort).  Copy in, sort and copy out
+    are all enqueued on `stream`.  Returns (sorted_keys, sorted_values or
+    None) as CPU tensors; with pinned tensors the copies are asynchronous and
+    the results are ready once `stream` has passed the call."""
+    import torch
+
+    if keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous CPU tensor")
+    kb = key_bytes_of(keys)
+    n = keys.numel()
+    if values is not None:
+        if values.is_cuda or not values.is_contiguous() or values.numel() != n or values.element_size() != 4:
+            raise ValueError("values must be a contiguous 32-bit CPU tensor with one entry per key")
+    out = torch.empty_like(keys, pin_memory=keys.is_pinned()) if out is None else out
+    if values is not None and out_values is None:
+        out_values = torch.empty_like(values, pin_memory=values.is_pinned())
+    if dev_buf is None:
+        dev_buf = workspace(rs_host_sort_bytes(algo, kb, values is not None, n, key_bits, num_buckets))
+    if algo == RS_ALGO_RADIX:
+        fn = rs_sort_host_u32 if kb == 4 else rs_sort_host_u64
+        rc = fn(keys, out, values, out_values, n, key_bits, dev_buf, dev_buf.numel(), stream)
+    else:
+        if (min_key is None) != (max_key is None):
+            raise ValueError("give both min_key and max_key, or neither")
+        if min_key is None:
+            min_key, max_key = (1, 0)  # min > max: bounds from the data
+        fn = bs_sort_host_u32 if kb == 4 else bs_sort_host_u64
+        rc = fn(keys, out, values, out_values, n, min_key, max_key, num_buckets, dev_buf, dev_buf.numel(), stream)
+    check(rc, "sort_host")
     return out, out_values
 
 

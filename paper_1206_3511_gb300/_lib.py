@@ -106,6 +106,14 @@ SIGNATURES: dict[str, tuple] = {
     "rs_server_get_stats": (_I, [_P, _c.POINTER(RsServerStats)]),
     "rs_server_destroy": (_I, [_P, _I]),
     "rs_sort_u32_noalloc": (_I, [_P, _P, _P, _P, _SZ, _I, _P]),
+    "rs_host_sort_bytes": (_SZ, [_I, _I, _I, _SZ, _I, _SZ]),
+    "rs_sort_host_u32": (_I, [_P, _P, _P, _P, _SZ, _I, _P, _SZ, _P]),
+    "rs_sort_host_u64": (_I, [_P, _P, _P, _P, _SZ, _I, _P, _SZ, _P]),
+    "bs_sort_host_u32": (_I, [_P, _P, _P, _P, _SZ, _U32, _U32, _SZ, _P, _SZ, _P]),
+    "bs_sort_host_u64": (_I, [_P, _P, _P, _P, _SZ, _U64, _U64, _SZ, _P, _SZ, _P]),
+    "rs_segmented_host_bytes": (_SZ, [_I, _I, _SZ, _SZ, _I]),
+    "rs_sort_segmented_host_u32": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P, _c.POINTER(RsConfig)]),
+    "rs_sort_segmented_host_u64": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P, _c.POINTER(RsConfig)]),
     "rs_get_status": (_I, [_P, _P]),
     "rs_set_debug": (None, [_U32, _I]),
     "rs_profile_enable": (None, [_I]),
@@ -394,6 +402,56 @@ def rs_sort_u32_noalloc(keys_in, keys_out, vals_in, vals_out, n, key_bits, strea
     overlap on the GPU)."""
     return _call("rs_sort_u32_noalloc", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out), n, key_bits,
                  stream_handle(stream))
+
+
+def rs_host_sort_bytes(algo, key_bytes, has_values, n, key_bits, num_buckets) -> int:
+    return _call("rs_host_sort_bytes", algo, key_bytes, int(bool(has_values)), n, key_bits, num_buckets)
+
+
+def rs_sort_host_u32(h_keys_in, h_keys_out, h_vals_in, h_vals_out, n, key_bits, dev_buf, dev_buf_bytes,
+                     stream=None) -> int:
+    """Host pointers in and out; dev_buf is a device buffer of
+    rs_host_sort_bytes(...) bytes."""
+    return _call("rs_sort_host_u32", ptr(h_keys_in), ptr(h_keys_out), ptr(h_vals_in), ptr(h_vals_out), n, key_bits,
+                 ptr(dev_buf), dev_buf_bytes, stream_handle(stream))
+
+
+def rs_sort_host_u64(h_keys_in, h_keys_out, h_vals_in, h_vals_out, n, key_bits, dev_buf, dev_buf_bytes,
+                     stream=None) -> int:
+    return _call("rs_sort_host_u64", ptr(h_keys_in), ptr(h_keys_out), ptr(h_vals_in), ptr(h_vals_out), n, key_bits,
+                 ptr(dev_buf), dev_buf_bytes, stream_handle(stream))
+
+
+def bs_sort_host_u32(h_keys_in, h_keys_out, h_vals_in, h_vals_out, n, min_key, max_key, num_buckets, dev_buf,
+                     dev_buf_bytes, stream=None) -> int:
+    return _call("bs_sort_host_u32", ptr(h_keys_in), ptr(h_keys_out), ptr(h_vals_in), ptr(h_vals_out), n, min_key,
+                 max_key, num_buckets, ptr(dev_buf), dev_buf_bytes, stream_handle(stream))
+
+
+def bs_sort_host_u64(h_keys_in, h_keys_out, h_vals_in, h_vals_out, n, min_key, max_key, num_buckets, dev_buf,
+                     dev_buf_bytes, stream=None) -> int:
+    return _call("bs_sort_host_u64", ptr(h_keys_in), ptr(h_keys_out), ptr(h_vals_in), ptr(h_vals_out), n, min_key,
+                 max_key, num_buckets, ptr(dev_buf), dev_buf_bytes, stream_handle(stream))
+
+
+def rs_segmented_host_bytes(key_bytes, has_values, n_total, nseg, key_bits) -> int:
+    return _call("rs_segmented_host_bytes", key_bytes, int(bool(has_values)), n_total, nseg, key_bits)
+
+
+def rs_sort_segmented_host_u32(h_keys_in, h_keys_out, h_vals_in, h_vals_out, h_seg_offsets, nseg, n_total, key_bits,
+                               dev_buf, dev_buf_bytes, stream=None, cfg=None) -> int:
+    c = _as_cfg(cfg)
+    return _call("rs_sort_segmented_host_u32", ptr(h_keys_in), ptr(h_keys_out), ptr(h_vals_in), ptr(h_vals_out),
+                 ptr(h_seg_offsets), nseg, n_total, key_bits, ptr(dev_buf), dev_buf_bytes, stream_handle(stream),
+                 _c.byref(c) if c is not None else None)
+
+
+def rs_sort_segmented_host_u64(h_keys_in, h_keys_out, h_vals_in, h_vals_out, h_seg_offsets, nseg, n_total, key_bits,
+                               dev_buf, dev_buf_bytes, stream=None, cfg=None) -> int:
+    c = _as_cfg(cfg)
+    return _call("rs_sort_segmented_host_u64", ptr(h_keys_in), ptr(h_keys_out), ptr(h_vals_in), ptr(h_vals_out),
+                 ptr(h_seg_offsets), nseg, n_total, key_bits, ptr(dev_buf), dev_buf_bytes, stream_handle(stream),
+                 _c.byref(c) if c is not None else None)
 
 
 def rs_get_status(ws, stream=None) -> int:

@@ -128,3 +128,62 @@ def test_argument_errors_of_the_other_entry_points(lib):
     assert _lib.rs_server_create(bad)[0] == 1
     bad = _lib.RsServerConfig(fake + 8, 1 << 20, 0, 4, 8, 0)  # misaligned pool
     assert _lib.rs_server_create(bad)[0] == 1
+
+
+def test_host_buffer_sorts_size_and_reject_bad_arguments(lib):
+    """The host-buffer sorts: dev_buf holds the workspace, the keys and the
+    values; arguments that need no CUDA call are checked first."""
+    from paper_1206_3511_gb300 import _lib
+
+    _lib.load()
+    n = 10**6
+    ws = _lib.rs_workspace_bytes(0, 4, 0, n, 32, 0, 1)
+    assert _lib.rs_host_sort_bytes(0, 4, 0, n, 32, 0) >= ws + 4 * n
+    assert _lib.rs_host_sort_bytes(0, 8, 1, n, 0, 0) >= _lib.rs_workspace_bytes(0, 8, 1, n, 0, 0, 1) + 12 * n
+    assert _lib.rs_host_sort_bytes(1, 4, 0, n, 0, 0) >= _lib.rs_workspace_bytes(1, 4, 0, n, 0, 0, 1) + 4 * n
+    assert _lib.rs_host_sort_bytes(0, 4, 0, n, 33, 0) == 0
+    assert _lib.rs_host_sort_bytes(2, 4, 0, n, 0, 0) == 0
+    assert _lib.rs_host_sort_bytes(1, 4, 0, n, 0, (1 << 32) + 1) == 0
+    h = ctypes.create_string_buffer(1 << 16)
+    a = ctypes.addressof(h)
+    a += (-a) % 16
+    fake_dev = 1 << 40
+    # values without outputs, key_bits, n above the limit, null keys
+    assert _lib.rs_sort_host_u32(a, a + 4096, a, None, 16, 32, fake_dev, 1 << 30, 0) == 1
+    assert _lib.rs_sort_host_u32(a, a + 4096, None, None, 16, 33, fake_dev, 1 << 30, 0) == 1
+    assert _lib.rs_sort_host_u32(a, a + 4096, None, None, (1 << 30) + 1, 32, fake_dev, 1 << 30, 0) == 1
+    assert _lib.rs_sort_host_u64(None, a, None, None, 16, 0, fake_dev, 1 << 30, 0) == 1
+    # misaligned keys, partial overlap of keys in and out, keys over values
+    assert _lib.rs_sort_host_u64(a + 4, a + 4096, None, None, 16, 0, fake_dev, 1 << 30, 0) == 1
+    assert _lib.rs_sort_host_u32(a, a + 8, None, None, 16, 32, fake_dev, 1 << 30, 0) == 1
+    assert _lib.rs_sort_host_u32(a, a + 4096, a + 2048, a + 32, 16, 32, fake_dev, 1 << 30, 0) == 1
+    # n == 0 is a no-op
+    assert _lib.rs_sort_host_u32(None, None, None, None, 0, 32, None, 0, 0) == 0
+    # bucket: bucket count above 2^32, values without outputs, overlap
+    assert _lib.bs_sort_host_u32(a, a + 4096, None, None, 16, 0, 99, (1 << 32) + 1, fake_dev, 1 << 30, 0) == 1
+    assert _lib.bs_sort_host_u32(a, a + 4096, a, None, 16, 0, 99, 0, fake_dev, 1 << 30, 0) == 1
+    assert _lib.bs_sort_host_u64(a, a + 8, None, None, 16, 0, 99, 0, fake_dev, 1 << 30, 0) == 1
+    assert _lib.bs_sort_host_u64(None, None, None, None, 0, 0, 99, 0, None, 0, 0) == 0
+
+
+def test_segmented_host_sort_rejects_bad_arguments(lib):
+    from paper_1206_3511_gb300 import _lib
+
+    _lib.load()
+    n, nseg = 10**6, 1000
+    assert _lib.rs_segmented_host_bytes(4, 0, n, nseg, 32) >= (
+        _lib.rs_segmented_workspace_bytes(4, 0, n, nseg, 32) + 4 * n + 8 * (nseg + 1))
+    assert _lib.rs_segmented_host_bytes(4, 0, n, nseg, 33) == 0
+    h = ctypes.create_string_buffer(1 << 16)
+    a = ctypes.addressof(h)
+    a += (-a) % 16
+    offs = a + 8192
+    fake_dev = 1 << 40
+    f = _lib.rs_sort_segmented_host_u32
+    assert f(a, a + 4096, None, None, offs, 3, 16, 33, fake_dev, 1 << 30, 0, None) == 1      # key_bits
+    assert f(a, a + 4096, a + 6000, None, offs, 3, 16, 32, fake_dev, 1 << 30, 0, None) == 1  # values
+    assert f(a, a + 4096, None, None, None, 3, 16, 32, fake_dev, 1 << 30, 0, None) == 1      # no offsets
+    assert f(a, a + 4096, None, None, offs + 4, 3, 16, 32, fake_dev, 1 << 30, 0, None) == 1  # misaligned
+    assert f(a, a + 4096, None, None, a + 4104, 3, 16, 32, fake_dev, 1 << 30, 0, None) == 1  # offsets in output
+    assert f(a, a + 8, None, None, offs, 3, 16, 32, fake_dev, 1 << 30, 0, None) == 1         # keys overlap
+    assert f(None, None, None, None, None, 0, 0, 32, None, 0, 0, None) == 0                  # nothing to sort
