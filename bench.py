@@ -183,6 +183,61 @@ def cub_context(d_keys, n, stream, reps=20):
         return None
 
 
+def host_link_rates(h_src, h_dst, d_a, d_b, reps=3) -> dict:
+    """Copy rates of the host link on the step's own pinned buffers: host to
+    device alone, device to host alone, and both at once on two streams
+    (GB/s, median of reps).  The copied size is that of h_src, up to 1 GB."""
+    import torch
+
+    nb = min(h_src.numel() * h_src.element_size(), 1 << 30)
+    hs, hd = h_src.view(torch.uint8)[:nb], h_dst.view(torch.uint8)[:nb]
+    da, db = d_a.view(torch.uint8)[:nb], d_b.view(torch.uint8)[:nb]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps + 1):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            cur = torch.cuda.current_stream()
+            e0.record(cur)
+            s1.wait_event(e0)
+            s2.wait_event(e0)
+            fn()
+            for s in (s1, s2):
+                d = torch.cuda.Event()
+                d.record(s)
+                cur.wait_event(d)
+            e1.record(cur)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sorted(ts[1:])[len(ts[1:]) // 2] / 1e3
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            da.copy_(hs, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            hd.copy_(db, non_blocking=True)
+
+    def both():
+        h2d()
+        d2h()
+
+    return {"h2d_gbs": nb / timed(h2d) / 1e9, "d2h_gbs": nb / timed(d2h) / 1e9,
+            "both_gbs": 2 * nb / timed(both) / 1e9}
+
+
+def link_bound(units, h2d_bytes, d2h_bytes, sort_ms, rates) -> float:
+    """Throughput ceiling of the pipelined end-to-end steps: a step takes at
+    least the longest of its sort, its upload, its download and both copies
+    sharing the link (units per second / 1e9)."""
+    t = max(sort_ms / 1e3, h2d_bytes / (rates["h2d_gbs"] * 1e9), d2h_bytes / (rates["d2h_gbs"] * 1e9),
+            (h2d_bytes + d2h_bytes) / (rates["both_gbs"] * 1e9))
+    return units / t / 1e9
+
+
 def max_over_ranks(values, device=None) -> list[float]:
     """Each value's maximum over all ranks (the job's time is its slowest
     rank's); the values themselves on a single process."""
@@ -542,6 +597,7 @@ def run_ours(args):
     for j in range(S):
         assert rs.get_status(hbufs[j]) == 0
         assert torch.equal(houts[j], h_out), "pipelined result differs from the serial one"
+    link = host_link_rates(h_keys, houts[1], d_out, d_keys)  # overwrites houts[1] and d_out
 
     ms, e2e_ms, e2e_serial_ms = max_over_ranks([ms, e2e_ms, e2e_serial_ms], device=dev)
     if rank != 0:
@@ -643,7 +699,10 @@ def run_ours(args):
                 "api": "rs_sort_host_u32/u64 or bs_sort_host_u32/u64 (host arrays in and out, one call per step)",
                 "mode": "pipelined: calls round-robin over 3 streams with their own device buffers, so one call's "
                         "copies overlap another's sort",
-                "serial_value": e2e_serial, "steps": e2e_steps},
+                "serial_value": e2e_serial, "steps": e2e_steps,
+                "link": dict(link, bound_value=link_bound(n, h2d, d2h, ms / args.steps, link),
+                             note="bound_value: the pipelined ceiling set by the sort time and the host link's "
+                                  "measured copy rates on these pinned buffers")},
         "cpu_baseline": cpu, "context": lib,
     }
     print(json.dumps(line), flush=True)
@@ -843,10 +902,12 @@ def run_batched(args):
     gbytes = max(rs.rs_segmented_host_bytes(4, 0, k1 - k0, b - a, 32) for a, b, k0, k1, _ in groups)
     gbufs = [rs.workspace(gbytes, d_keys.device) for _ in range(S)]
     gstreams = [torch.cuda.Stream() for _ in range(S)]
+    calls = [0]  # the rotation over the streams continues across steps
 
     def pipe_step():
-        for gi, (a, b, k0, k1, goff) in enumerate(groups):
-            j = gi % S
+        for a, b, k0, k1, goff in groups:
+            j = calls[0] % S
+            calls[0] += 1
             rs.check(rs.rs_sort_segmented_host_u32(h_keys[k0:k1], h_out[k0:k1], None, None, goff, b - a, k1 - k0,
                                                    32, gbufs[j], gbytes, gstreams[j], seg_shape),
                      "segmented host-buffer group")
@@ -871,6 +932,7 @@ def run_batched(args):
     for i in (0, count // 2, count - 1):  # the downloaded result, spot-checked
         a, b = int(off[i]), int(off[i + 1])
         assert torch.equal(h_out[a:b], d_out[a:b].cpu()), f"pipelined result wrong in array {i}"
+    link = host_link_rates(h_keys, h_out, d_out, d_keys)  # overwrites the start of h_out and d_out
 
     ms, e2e_ms, e2e_serial_ms, plain_ms = max_over_ranks([ms, e2e_ms, e2e_serial_ms, plain_ms], device=dev)
     if rank != 0:
@@ -928,7 +990,10 @@ def run_batched(args):
                 "api": "rs_sort_segmented_host_u32 (host arrays and offsets in, sorted keys out)",
                 "mode": "pipelined: the batch in 8 groups of consecutive arrays, one call per group, the calls "
                         "round-robin over 3 streams with their own device buffers",
-                "serial_value": job_rate(n_total * e2e_steps, world, e2e_serial_ms), "steps": e2e_steps},
+                "serial_value": job_rate(n_total * e2e_steps, world, e2e_serial_ms), "steps": e2e_steps,
+                "link": dict(link, bound_value=link_bound(n_total, 4 * n_total, 4 * n_total, ms / args.steps, link),
+                             note="bound_value: the pipelined ceiling set by the sort time and the host link's "
+                                  "measured copy rates on these pinned buffers")},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

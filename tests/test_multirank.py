@@ -69,3 +69,15 @@ def test_single_process_max_is_identity():
 
     assert bench.max_over_ranks([1.5, 2.5]) == [1.5, 2.5]
     assert np.isfinite(bench.job_rate(1, 1, 1.0))
+
+
+def test_link_bound_is_the_slowest_stage():
+    import bench
+
+    rates = {"h2d_gbs": 200.0, "d2h_gbs": 190.0, "both_gbs": 333.0}
+    # 100M u32 keys: 400 MB each way; both directions share 333 GB/s -> 2.4 ms
+    assert bench.link_bound(100_000_000, 4e8, 4e8, 2.1, rates) == pytest.approx(100e6 / (8e8 / 333e9) / 1e9)
+    # a sort slower than the copies sets the bound
+    assert bench.link_bound(100_000_000, 4e8, 4e8, 5.0, rates) == pytest.approx(20.0)
+    # one direction alone can be the bound
+    assert bench.link_bound(1, 1.9e9, 0, 0.0, rates) == pytest.approx(1 / (1.9e9 / 200e9) / 1e9)
