@@ -442,6 +442,42 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
         scatter_staged<KeyT, VALS, BLOCK, ITEMS, FULL, false>(p, op, sm, c);
 }
 
+// A pass whose keys all carry one digit: the counting sort leaves their
+// order unchanged (Algorithm 3 places the keys of one digit in input order),
+// so the pass is a copy of its input, with the typed-key mapping of its place
+// in the sort.  The status words of the next pass are still cleared.
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename DigitOp, bool XF>
+__device__ __forceinline__ void identity_pass(const PassParams<DigitOp>& p, uint32_t bins) {
+    constexpr uint32_t kTile = BLOCK * ITEMS;
+    const KeyT* kin = static_cast<const KeyT*>(p.keys_in);
+    KeyT* kout = static_cast<KeyT*>(p.keys_out);
+    for (uint32_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+        if (p.status_next)
+            for (uint32_t d = threadIdx.x; d < bins; d += BLOCK) p.status_next[(size_t)tile * bins + d] = 0u;
+        const uint32_t base = tile * kTile;
+        const uint32_t m = min(kTile, p.n - base);
+        KeyT k[ITEMS];
+        uint32_t v[VALS ? ITEMS : 1];
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t idx = i * BLOCK + threadIdx.x;
+            k[i] = idx < m ? kin[base + idx] : (KeyT)0;
+            if (VALS) v[i] = idx < m ? p.vals_in[base + idx] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t idx = i * BLOCK + threadIdx.x;
+            if (idx < m) {
+                KeyT key = k[i];
+                if (XF && p.xf_in) key = p.xf.to_ordered(key);
+                if (XF && p.xf_out) key = p.xf.from_ordered(key);
+                kout[base + idx] = key;
+                if (VALS) p.vals_out[base + idx] = v[i];
+            }
+        }
+    }
+}
+
 // Persistent: every block claims tiles from the pass's counter until none is
 // left.  A block holds one tile at a time and only waits on tiles claimed
 // earlier, whose blocks are running, so the waits always end.
@@ -455,6 +491,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p)
     DigitOp op = p.op;
     op.init();
     const int tid = threadIdx.x;
+    // every key carries the first key's digit iff that digit's exclusive
+    // prefix is 0 and the next digit's is n
+    if (tid == 0) {
+        KeyT k0 = static_cast<const KeyT*>(p.keys_in)[0];
+        if (XF && p.xf_in) k0 = p.xf.to_ordered(k0);
+        const uint32_t d0 = op(k0);
+        s_tile = p.digit_base[d0] == 0u && (d0 + 1u == bins || p.digit_base[d0 + 1u] == p.n);
+    }
+    __syncthreads();
+    if (s_tile) {
+        identity_pass<KeyT, VALS, BLOCK, ITEMS, DigitOp, XF>(p, bins);
+        return;
+    }
+    __syncthreads();  // s_tile is reused for the tile ids below
     while (true) {
         for (uint32_t i = tid; i < (uint32_t)(BLOCK / 32) * bins; i += BLOCK) sm.tab[i] = 0ull;
         if (tid == 0) s_tile = atomicAdd(p.tile_ctr, 1u);

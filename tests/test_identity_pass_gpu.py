@@ -1,0 +1,121 @@
+"""GPU parity of passes whose keys all carry one digit.  Such a pass keeps the
+input order (the counting sort places the keys of one digit in input order),
+and the scatter kernel then copies its input instead of ranking it.  These
+cases put identity passes first, last, in the middle and everywhere, for
+plain and typed keys, with and without values, in place and not, and
+compare with the oracle bit for bit."""
+import numpy as np
+import pytest
+
+import synth
+from tests._util import assert_same, from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+N = 300_001  # well above one block's shared-memory sort, with a ragged last tile
+
+
+def _radix(rs, oracle, keys, vals=None, key_bits=0, in_place=False, what=""):
+    import torch
+
+    kbits = key_bits or 8 * keys.dtype.itemsize
+    k = to_dev(keys)
+    v = to_dev(vals) if vals is not None else None
+    if in_place:
+        out, outv = rs.sort(k, v, key_bits, out=k, out_values=v)
+    else:
+        out, outv = rs.sort(k, v, key_bits)
+    torch.cuda.synchronize()
+    if vals is None:
+        assert_same(from_dev(out, keys.dtype), oracle.radix_sort(keys, None, kbits), what)
+    else:
+        wk, wv = oracle.radix_sort(keys, vals, kbits)
+        assert_same(from_dev(out, keys.dtype), wk, what + " keys")
+        assert_same(from_dev(outv, np.uint32), wv, what + " values")
+
+
+@pytest.mark.parametrize("with_values", [False, True])
+@pytest.mark.parametrize("in_place", [False, True])
+def test_u32_identity_passes(rs, oracle, with_values, in_place):
+    vals = synth.index_values(N) if with_values else None
+    u = synth.u32(N, 601, 0)
+    # passes 1..3 identity (keys < 256), then pass 0 identity (low byte fixed),
+    # then the two middle passes identity, then every pass (one key repeated)
+    cases = {
+        "keys below 256": u & np.uint32(0xFF),
+        "constant low byte": (u & np.uint32(0xFFFFFF00)) | np.uint32(0x5A),
+        "constant middle bytes": (u & np.uint32(0xFF0000FF)) | np.uint32(0x00ABCD00),
+        "one repeated key": np.full(N, 0xDEADBEEF, np.uint32),
+    }
+    for what, keys in cases.items():
+        _radix(rs, oracle, keys, vals, 0, in_place, what)
+
+
+def test_u32_identity_passes_with_trimmed_key_bits(rs, oracle):
+    keys = synth.u32(N, 602, 0) & np.uint32(0x000F00FF)  # 24 bits: pass 1 identity, 3 passes
+    _radix(rs, oracle, keys, None, 24, what="24-bit keys, middle pass identity")
+    _radix(rs, oracle, keys, synth.index_values(N), 24, in_place=True, what="24-bit keys in place")
+
+
+@pytest.mark.parametrize("with_values", [False, True])
+def test_u64_identity_passes(rs, oracle, with_values):
+    vals = synth.index_values(N) if with_values else None
+    keys = synth.keys_u64(N, 32, seed=603)  # the upper four passes are identities
+    _radix(rs, oracle, keys, vals, 64, what="u64 keys below 2^32")
+    keys = synth.keys_u64(N, 64, seed=604) & np.uint64(0xFFFF00000000FFFF)
+    _radix(rs, oracle, keys, vals, 64, in_place=True, what="u64 keys with zero middle bytes")
+
+
+@pytest.mark.parametrize("dt,desc", [(np.int32, False), (np.int32, True), (np.float32, False),
+                                     (np.float64, True)])
+def test_typed_identity_passes(rs, oracle, dt, desc):
+    """Small non-negative integers (as int or float): the ordered images share
+    their high bytes, and small integers as floats have zero low mantissa
+    bytes, so the first and the last pass (which carry the typed-key mapping)
+    are identities."""
+    import torch
+
+    ints = (synth.u32(N, 605, 0) % np.uint32(1000)).astype(np.int64)
+    x = ints.astype(dt)
+    ut = {4: np.uint32, 8: np.uint64}[x.dtype.itemsize]
+    kind = 2 if np.issubdtype(dt, np.floating) else 1
+    vals = synth.index_values(N)
+    signed = {4: np.int32, 8: np.int64}[x.dtype.itemsize]
+    kd = torch.from_numpy(np.ascontiguousarray(x).view(signed)).cuda()
+    vd = to_dev(vals)
+    ok, ov = rs.sort_typed(kd, vd, kind=kind, descending=desc)
+    torch.cuda.synchronize()
+    wk, wv = oracle.sort_typed(x, vals, kind, desc)
+    assert_same(ok.cpu().numpy().view(ut), wk.view(ut), f"{dt.__name__} desc={desc} keys")
+    assert_same(ov.cpu().numpy().view(np.uint32), wv, f"{dt.__name__} desc={desc} values")
+
+
+def test_bucket_identity_level_pass(rs, oracle):
+    """Keys in [0, 1000) under declared bounds [0, 2^32 - 1]: every key falls
+    in the first level-1 digit of the bucket id, so that pass is an identity."""
+    import torch
+
+    keys = synth.keys_u32(N, 1, seed=606)
+    vals = synth.index_values(N)
+    nb = N // 16
+    kd, vd = to_dev(keys), to_dev(vals)
+    ok, ov = rs.bucket_sort(kd, vd, min_key=0, max_key=2**32 - 1, num_buckets=nb)
+    torch.cuda.synchronize()
+    wk, wv = oracle.bucket_sort(keys, vals, 0, 2**32 - 1, nb)
+    assert_same(from_dev(ok, np.uint32), wk, "bucket keys")
+    assert_same(from_dev(ov, np.uint32), wv, "bucket values")
+
+
+def test_counting_pass_on_a_constant_digit(rs, oracle):
+    """The counting-sort building block on a digit every key shares returns
+    its input unchanged."""
+    import torch
+
+    keys = (synth.u32(N, 607, 0) & np.uint32(0xFFFF00FF)) | np.uint32(0x3C00)
+    vals = synth.index_values(N)
+    ok, ov = rs.counting_pass(to_dev(keys), to_dev(vals), shift=8, digit_bits=8)
+    torch.cuda.synchronize()
+    wk, wv = oracle.counting_pass(keys, vals, 8, 8)
+    assert_same(wk, keys, "oracle: identity")
+    assert_same(from_dev(ok, np.uint32), wk, "identity counting pass keys")
+    assert_same(from_dev(ov, np.uint32), wv, "identity counting pass values")
