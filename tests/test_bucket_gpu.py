@@ -201,3 +201,25 @@ def test_u64_full_range_small_bucket_counts(rs, oracle, n, nb):
     keys[:2] = [0, 2**64 - 1]
     _check(rs, oracle, keys, synth.index_values(n), 0, 2**64 - 1, nb, what=f"u64 full n={n} nb={nb}",
            use_bucket_oracle=False)
+
+
+@pytest.mark.parametrize("nb,lo,hi", [(125_000, 0, 2**32 - 1), ((1 << 22) + 12_345, 0, 2**32 - 1),
+                                      (300_007, 17, 3_000_000_017)])
+def test_bucket_ids_at_partition_boundaries(rs, oracle, nb, lo, hi):
+    """Keys at the first key of buckets whose id is a multiple of a partition
+    level's 2^shift (and the key just below): there the cheap bucket-id
+    estimate and the exact id can differ in the partition digit, and the
+    remainder test must run.  Level shifts as the sort plans them (8-bit
+    digits from the top of the bucket id)."""
+    R = hi - lo + 1
+    bbits = (nb - 1).bit_length()
+    d1 = min(8, bbits)
+    s1 = bbits - d1
+    s2 = s1 - min(8, s1)
+    bs = sorted(set(range(0, nb, 1 << s1)) | set(range(0, nb, 1 << s2)))
+    first = np.array([lo + (b * R + nb - 1) // nb for b in bs], dtype=np.uint64)
+    edge = np.concatenate([first, first[first > lo] - np.uint64(1)]).astype(np.uint32)
+    rest = (synth.u64(400_000, 610, 0) % np.uint64(R) + np.uint64(lo)).astype(np.uint32)
+    keys = np.concatenate([edge, rest])
+    keys = keys[synth.u64(keys.size, 611, 0).argsort(kind="stable")]  # mixed order
+    _check(rs, oracle, keys, synth.index_values(keys.size), lo, hi, nb, what=f"boundaries nb={nb}")
