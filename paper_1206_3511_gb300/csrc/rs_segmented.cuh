@@ -435,10 +435,93 @@ __device__ __forceinline__ void rank_tiny(const KeyT* row, uint32_t m, const Key
     }
 }
 
+// One tiny segment sorted by one warp with a bitonic network (Batcher 1968)
+// over N = 32 * KPL slots, KPL per lane: slot lane * KPL + r holds the key
+// loaded as item r (input position r * 32 + lane).  Slots past the segment
+// hold the largest key.  Pairs KPL or more slots apart are exchanged between
+// lanes, nearer pairs inside a lane.  Keys compare by (key, input position),
+// a total order, so the sort is stable: equal keys keep their input order,
+// and each value is fetched from its key's input position at the end (all
+// reads before the first write, so the sort may run in place).  For
+// keys only the position is not needed (equal keys are indistinguishable).
+// Costs O(m log^2 m) comparisons against rank_tiny's O(m^2).
+template <int KPL, typename KeyT, bool VALS>
+__device__ __forceinline__ void bitonic_tiny(uint32_t m, const KeyT (&k)[kTinyCap / 32], const uint32_t* vin,
+                                             KeyT* kout, uint32_t* vout, int lane) {
+    constexpr int N = 32 * KPL;
+    KeyT a[KPL];
+    uint32_t ix[KPL];
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const uint32_t i = (uint32_t)r * 32 + lane;
+        a[r] = i < m ? k[r] : ~(KeyT)0;
+        ix[r] = i;
+    }
+    // x before y in (key, position) order (keys only: by key)
+    auto before = [](KeyT x, uint32_t xi, KeyT y, uint32_t yi) {
+        return VALS ? (x < y || (x == y && xi < yi)) : x < y;
+    };
+#pragma unroll
+    for (int kk = 2; kk <= N; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            if (j < KPL) {
+#pragma unroll
+                for (int r = 0; r < KPL; ++r) {
+                    if ((r & j) == 0) {
+                        const int r2 = r | j;
+                        const bool up = (((uint32_t)lane * KPL + r) & kk) == 0;
+                        const bool sw = up ? before(a[r2], ix[r2], a[r], ix[r]) : before(a[r], ix[r], a[r2], ix[r2]);
+                        if (sw) {
+                            const KeyT t = a[r];
+                            a[r] = a[r2];
+                            a[r2] = t;
+                            const uint32_t ti = ix[r];
+                            ix[r] = ix[r2];
+                            ix[r2] = ti;
+                        }
+                    }
+                }
+            } else {
+                const int lj = j / KPL;
+#pragma unroll
+                for (int r = 0; r < KPL; ++r) {
+                    const KeyT o = __shfl_xor_sync(0xffffffffu, a[r], lj);
+                    const uint32_t oi = VALS ? __shfl_xor_sync(0xffffffffu, ix[r], lj) : 0u;
+                    const uint32_t e = (uint32_t)lane * KPL + r;
+                    const bool lower = (e & j) == 0, up = (e & kk) == 0;
+                    // the lower slot of an ascending pair keeps the earlier key
+                    const bool take = lower == up ? before(o, oi, a[r], ix[r]) : before(a[r], ix[r], o, oi);
+                    if (take) {
+                        a[r] = o;
+                        ix[r] = oi;
+                    }
+                }
+            }
+        }
+    }
+    // every value is read before any is written: in place, vout is vin
+    uint32_t vv[VALS ? KPL : 1];
+    if (VALS) {
+#pragma unroll
+        for (int r = 0; r < KPL; ++r) vv[r] = ((uint32_t)lane * KPL + r) < m ? vin[ix[r]] : 0u;
+        __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < KPL; ++r) {
+        const uint32_t e = (uint32_t)lane * KPL + r;
+        if (e < m) {
+            kout[e] = a[r];
+            if (VALS) vout[e] = vv[r];
+        }
+    }
+}
+
 // Warp sort of tiny segments: each warp takes segments of at most kTinyCap
-// keys from the list, copies the keys to its shared-memory row and ranks
-// them (rank_tiny, with as many keys per lane as the segment needs).  Keys at
-// or above 2^bits are reported in hdr.
+// keys from the list.  Segments of at most 32 keys are ranked against the
+// warp's shared-memory row (rank_tiny), larger ones go through a bitonic
+// network in registers (bitonic_tiny).  Keys at or above 2^bits are reported
+// in hdr.
 template <typename KeyT, bool VALS>
 __global__ void __launch_bounds__(256) k_tiny_sort(const KeyT* __restrict__ keys_in, KeyT* keys_out,
                                                    const uint32_t* __restrict__ vals_in, uint32_t* vals_out,
@@ -454,30 +537,34 @@ __global__ void __launch_bounds__(256) k_tiny_sort(const KeyT* __restrict__ keys
         const SegDesc sd = segs[si];
         const uint32_t m = sd.n;
         KeyT k[kPerLane];
-        uint32_t v[VALS ? kPerLane : 1];
 #pragma unroll
         for (int j = 0; j < kPerLane; ++j) {
             const uint32_t i = (uint32_t)j * 32 + lane;
             k[j] = 0;
-            if (VALS) v[j] = 0;
             if (i < m) {
                 k[j] = keys_in[sd.start + i];
-                if (VALS) v[j] = vals_in[sd.start + i];
-                row[i] = k[j];
                 bad |= sd.bits < 8 * sizeof(KeyT) && (k[j] >> sd.bits) != 0;
             }
         }
-        __syncwarp();
         KeyT* kout = keys_out + sd.start;
         uint32_t* vout = VALS ? vals_out + sd.start : nullptr;
-        if (m <= 32)
+        const uint32_t* vin = VALS ? vals_in + sd.start : nullptr;
+        if (m <= 32) {
+            // rank_tiny with one key per lane reads the keys from the row
+            uint32_t v[VALS ? kPerLane : 1] = {};
+            if (lane < (int)m) {
+                row[lane] = k[0];
+                if (VALS) v[0] = vin[lane];
+            }
+            __syncwarp();
             rank_tiny<1, KeyT, VALS>(row, m, k, v, kout, vout, lane);
-        else if (m <= 64)
-            rank_tiny<2, KeyT, VALS>(row, m, k, v, kout, vout, lane);
-        else if (m <= 128)
-            rank_tiny<4, KeyT, VALS>(row, m, k, v, kout, vout, lane);
-        else
-            rank_tiny<8, KeyT, VALS>(row, m, k, v, kout, vout, lane);
+        } else if (m <= 64) {
+            bitonic_tiny<2, KeyT, VALS>(m, k, vin, kout, vout, lane);
+        } else if (m <= 128) {
+            bitonic_tiny<4, KeyT, VALS>(m, k, vin, kout, vout, lane);
+        } else {
+            bitonic_tiny<8, KeyT, VALS>(m, k, vin, kout, vout, lane);
+        }
         __syncwarp();
     }
     if (bad && hdr) set_device_error(hdr, RS_ERR_KEY_RANGE, blockIdx.x);

@@ -216,6 +216,21 @@ def test_many_tiny_segments(rs, oracle, kb, with_values, in_place):
     _check(rs, oracle, keys, sizes, vals, in_place=in_place, what=f"tiny kb={kb} v={with_values} ip={in_place}")
 
 
+@pytest.mark.parametrize("kb", [4, 8])
+def test_tiny_segments_holding_the_largest_key(rs, oracle, kb):
+    """Warp-sorted segments whose keys are the largest value of the key type
+    (which also pads the sorting network past the segment's end) or one below
+    it: the largest keys stay in the segment, in input order."""
+    sizes = np.array([33, 64, 65, 100, 128, 129, 200, 256, 255, 31, 1, 0, 77] * 40, dtype=np.int64)
+    n = int(sizes.sum())
+    top = np.uint32(0xFFFFFFFF) if kb == 4 else np.uint64(0xFFFFFFFFFFFFFFFF)
+    bit = synth.u32(n, 94, 0) & np.uint32(1)
+    keys = (top - bit.astype(top.dtype)).astype(top.dtype)
+    for with_values in (False, True):
+        vals = synth.index_values(n) if with_values else None
+        _check(rs, oracle, keys, sizes, vals, what=f"largest keys kb={kb} v={with_values}")
+
+
 def test_key_above_key_bits_in_a_tiny_segment_is_reported(rs):
     import torch
 
