@@ -315,9 +315,18 @@ def measured_peaks() -> dict:
     return {}
 
 
-def kernel_source_sha() -> str:
+# the sources that define each kernel whose DRAM traffic profiles/traffic.json
+# records; a recorded figure is used only while these files are unchanged
+KERNEL_SOURCES = {
+    "onesweep_pass": ("rs_onesweep.cuh", "rs_common.cuh", "rs_radix.cu", "rs_radix.h"),
+    "onesweep_seg_pass": ("rs_onesweep.cuh", "rs_common.cuh", "rs_segmented.cuh", "rs_segmented.cu",
+                          "rs_segmented.h"),
+}
+
+
+def kernel_source_sha(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in ("rs_onesweep.cuh", "rs_radix.cu", "rs_common.cuh", "rs_segmented.cuh", "rs_segmented.cu", "rs_segmented.h"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1206_3511_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -327,12 +336,12 @@ def ncu_traffic(kernel: str, workload: str):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it
     was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
         return None
     with open(p) as f:
         d = json.load(f)
     e = d.get(f"{kernel}@{workload}")
-    if not e or e.get("source_sha") != kernel_source_sha():
+    if not e or e.get("source_sha") != kernel_source_sha(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 

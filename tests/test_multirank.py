@@ -81,3 +81,32 @@ def test_link_bound_is_the_slowest_stage():
     assert bench.link_bound(100_000_000, 4e8, 4e8, 5.0, rates) == pytest.approx(20.0)
     # one direction alone can be the bound
     assert bench.link_bound(1, 1.9e9, 0, 0.0, rates) == pytest.approx(1 / (1.9e9 / 200e9) / 1e9)
+
+
+def test_traffic_is_used_only_for_the_sources_it_was_taken_on(tmp_path, monkeypatch):
+    import json
+
+    import bench
+
+    sha = bench.kernel_source_sha("onesweep_pass")
+    assert len(sha) == 16 and sha != bench.kernel_source_sha("onesweep_seg_pass")
+    p = tmp_path / "profiles"
+    p.mkdir()
+    (p / "traffic.json").write_text(json.dumps({
+        "onesweep_pass@w": {"dram_bytes_per_launch": 123, "source_sha": sha},
+        "onesweep_seg_pass@w": {"dram_bytes_per_launch": 456, "source_sha": "stale"}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    csrc = tmp_path / "paper_1206_3511_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    import os
+    import shutil
+
+    real = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1206_3511_gb300", "csrc")
+    for f in set(bench.KERNEL_SOURCES["onesweep_pass"]) | set(bench.KERNEL_SOURCES["onesweep_seg_pass"]):
+        shutil.copy(os.path.join(real, f), csrc / f)
+    assert bench.ncu_traffic("onesweep_pass", "w") == 123
+    assert bench.ncu_traffic("onesweep_seg_pass", "w") is None   # taken on other sources
+    assert bench.ncu_traffic("digit_counts", "w") is None        # no entry
+    with open(csrc / "rs_radix.cu", "a") as f:
+        f.write("\n// changed\n")
+    assert bench.ncu_traffic("onesweep_pass", "w") is None       # its kernel changed since
