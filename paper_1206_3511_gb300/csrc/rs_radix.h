@@ -49,7 +49,9 @@ RadixLayout radix_layout(int key_bytes, bool vals, size_t n, int key_bits, int d
 size_t radix_workspace_bytes(int key_bytes, bool vals, size_t n, int key_bits);
 size_t radix_workspace_bytes_cfg(int key_bytes, bool vals, size_t n, int key_bits, const rs_config& cfg);
 const Variant* find_variant(int key_bytes, bool vals, int block, int items);
-const Variant* default_variant(int key_bytes, bool vals);
+// The shape a sort of n keys takes when none is requested (typed: the key
+// mapping is compiled into the first shape of each key type only).
+const Variant* default_variant(int key_bytes, bool vals, size_t n, bool typed);
 
 rs_status radix_sort_impl(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
                           uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
