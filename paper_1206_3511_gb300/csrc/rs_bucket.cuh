@@ -89,6 +89,11 @@ struct BucketDigit {
     __device__ __forceinline__ uint32_t operator()(KeyT k) const {
         return (uint32_t)(bucket_of(bp, k) >> shift) & mask;
     }
+    // every key in [lo, hi] has one digit (the bucket id is monotone in the key)
+    template <typename KeyT>
+    __device__ __forceinline__ bool same_digit_range(KeyT lo, KeyT hi) const {
+        return (bucket_of(bp, lo) >> shift) == (bucket_of(bp, hi) >> shift);
+    }
 };
 
 // The same digit for the counting kernels (only pass q = 0 exists).

@@ -29,7 +29,40 @@ struct RadixDigit {
     __device__ __forceinline__ uint32_t operator()(KeyT k) const {
         return (uint32_t)(k >> shift) & mask;
     }
+    // every key in [lo, hi] has one digit: their bits from the digit up agree
+    template <typename KeyT>
+    __device__ __forceinline__ bool same_digit_range(KeyT lo, KeyT hi) const {
+        return (lo >> shift) == (hi >> shift);
+    }
 };
+
+template <typename T>
+__device__ __forceinline__ T warp_min(T x) {
+    if constexpr (sizeof(T) == 4) {
+        return __reduce_min_sync(0xffffffffu, x);
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = y < x ? y : x;
+        }
+        return x;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T x) {
+    if constexpr (sizeof(T) == 4) {
+        return __reduce_max_sync(0xffffffffu, x);
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = y > x ? y : x;
+        }
+        return x;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Digit counts of every pass in one read.
@@ -378,11 +411,38 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     const uint32_t lanebit = 1u << lane;
     const uint32_t gt = ~(lt | lanebit);
     uint32_t dr[ITEMS];
+    // A warp whose keys all carry one digit (a run of sorted keys) needs no
+    // ranking: a key's rank is its position in the warp, and the warp's
+    // count of that digit is all its keys.  This spares the 32 atomics on
+    // one table word that such a warp would make per item.  Full tiles only;
+    // screened by the warp's first and last keys, then decided on the
+    // warp's smallest and largest keys.
+    bool uniform = false;
+    if (FULL) {
+        const KeyT first = __shfl_sync(0xffffffffu, k[0], 0);
+        const KeyT last = __shfl_sync(0xffffffffu, k[ITEMS - 1], 31);
+        if (op.same_digit_range((KeyT)(first - c.key_lo), (KeyT)(last - c.key_lo))) {
+            KeyT lo = k[0], hi = k[0];
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const bool ok = FULL || (wofs + i * 32) < c.tile_n;
-        const uint32_t d = op((KeyT)(k[i] - c.key_lo));
-        dr[i] = (d << 16) | warp_rank<FULL>(tab, d, ok, lanebit, lt, gt);
+            for (int i = 1; i < ITEMS; ++i) {
+                lo = k[i] < lo ? k[i] : lo;
+                hi = k[i] > hi ? k[i] : hi;
+            }
+            uniform = op.same_digit_range((KeyT)(warp_min(lo) - c.key_lo), (KeyT)(warp_max(hi) - c.key_lo));
+        }
+    }
+    if (uniform) {
+        const uint32_t d0 = op((KeyT)(k[0] - c.key_lo));
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) dr[i] = (d0 << 16) | (uint32_t)(i * 32 + lane);
+        st_shared_v2_if(tab + 8u * d0, 0u, (uint32_t)(ITEMS * 32), lane == 0);
+    } else {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const bool ok = FULL || (wofs + i * 32) < c.tile_n;
+            const uint32_t d = op((KeyT)(k[i] - c.key_lo));
+            dr[i] = (d << 16) | warp_rank<FULL>(tab, d, ok, lanebit, lt, gt);
+        }
     }
     __syncthreads();
 

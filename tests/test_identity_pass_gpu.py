@@ -119,3 +119,66 @@ def test_counting_pass_on_a_constant_digit(rs, oracle):
     assert_same(wk, keys, "oracle: identity")
     assert_same(from_dev(ok, np.uint32), wk, "identity counting pass keys")
     assert_same(from_dev(ov, np.uint32), wv, "identity counting pass values")
+
+
+# Warps whose keys all carry one digit (runs of sorted keys) skip the ranking:
+# each key's rank is its position in the warp.  The cases below make such
+# warps in some passes but not others, with values so that order shows.
+
+def _runs_of_top_digit(n, seed, width=32):
+    """Keys grouped by their top byte in runs of about 600, random below it."""
+    top = (np.arange(n, dtype=np.uint64) // np.uint64(600)) % np.uint64(256)
+    if width == 32:
+        low = synth.u32(n, seed, 0) & np.uint32(0x00FFFFFF)
+        return ((top.astype(np.uint32) << np.uint32(24)) | low).astype(np.uint32)
+    low = synth.keys_u64(n, 56, seed=seed)
+    return (top << np.uint64(56)) | low
+
+
+@pytest.mark.parametrize("with_values", [False, True])
+def test_warp_uniform_digits_u32(rs, oracle, with_values):
+    n = 1_000_003
+    vals = synth.index_values(n) if with_values else None
+    _radix(rs, oracle, _runs_of_top_digit(n, 620), vals, what="runs of one top digit")
+    s = np.sort(synth.u32(n, 621, 0))
+    _radix(rs, oracle, s, vals, what="sorted keys")
+    dup = np.repeat(synth.u32(n // 700 + 1, 622, 0), 700)[:n]  # long runs of one key
+    _radix(rs, oracle, dup, vals, in_place=True, what="runs of one key, in place")
+    _radix(rs, oracle, s[::-1].copy(), vals, key_bits=32, what="reverse sorted keys")
+
+
+def test_warp_uniform_digits_u64_and_typed(rs, oracle):
+    import torch
+
+    n = 700_001
+    vals = synth.index_values(n)
+    _radix(rs, oracle, _runs_of_top_digit(n, 623, 64), vals, what="u64 runs of one top digit")
+    x = np.sort(synth.u32(n, 624, 0).view(np.int32))
+    kd = torch.from_numpy(x.copy()).cuda()
+    ok, ov = rs.sort_typed(kd, to_dev(vals), kind=1)
+    torch.cuda.synchronize()
+    wk, wv = oracle.sort_typed(x, vals, 1, False)
+    assert_same(ok.cpu().numpy().view(np.uint32), wk.view(np.uint32), "typed sorted int32 keys")
+    assert_same(ov.cpu().numpy().view(np.uint32), wv, "typed sorted int32 values")
+
+
+def test_warp_uniform_digits_segmented_and_bucket(rs, oracle):
+    import torch
+
+    sizes = synth.log_uniform_sizes(60, 5000, 300_000, seed=625)
+    n = int(sizes.sum())
+    keys = _runs_of_top_digit(n, 626)
+    vals = synth.index_values(n)
+    off = synth.segment_offsets(sizes)
+    kd, vd, od = to_dev(keys), to_dev(vals), to_dev(off.astype(np.uint64))
+    ok, ov = rs.segmented_sort(kd, od, vd)
+    torch.cuda.synchronize()
+    wk, wv = oracle.segmented_radix_sort(keys, off, vals, 32)
+    assert_same(from_dev(ok, np.uint32), wk, "segmented keys")
+    assert_same(from_dev(ov, np.uint32), wv, "segmented values")
+    s = np.sort(synth.u32(n, 627, 0))
+    ok, ov = rs.bucket_sort(to_dev(s), vd)
+    torch.cuda.synchronize()
+    wk, wv = oracle.bucket_sort(s, vals, int(s.min()), int(s.max()), max(1, n // 16))
+    assert_same(from_dev(ok, np.uint32), wk, "bucket sorted keys")
+    assert_same(from_dev(ov, np.uint32), wv, "bucket sorted values")
