@@ -550,7 +550,7 @@ def run_ours(args):
     # host memory into a device buffer, sorts them there and copies the sorted
     # keys (and values) back, all inside one library call.  Serial: one
     # stream, nothing overlaps.
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = max(3, min(args.steps, 20))
     if algo == "bucket":
         hbytes = rs.rs_host_sort_bytes(rs.RS_ALGO_BUCKET, kb, has_v, n, 0, nb)
         hfn = rs.bs_sort_host_u32 if kb == 4 else rs.bs_sort_host_u64
