@@ -322,7 +322,16 @@ rs_status counting_pass_impl(int key_bytes, const void* keys_in, void* keys_out,
     if (vals && ranges_overlap(vals_in, vb, vals_out, vb)) return RS_ERR_INVALID_ARG;
     if (((uintptr_t)keys_in | (uintptr_t)keys_out) % key_bytes) return RS_ERR_INVALID_ARG;
     if (!ws || ((uintptr_t)ws % 256)) return RS_ERR_WORKSPACE;
+    // the default shape, or the first that fits this digit width's tables
     const Variant* var = default_variant(key_bytes, vals, n, false);
+    if (var && var->smem_bytes(digit_bits) > kMaxSmemPerBlock) {
+        var = nullptr;
+        for (const Variant& v : kVariants)
+            if (v.key_bytes == key_bytes && v.vals == vals && v.smem_bytes(digit_bits) <= kMaxSmemPerBlock) {
+                var = &v;
+                break;
+            }
+    }
     if (!var) return RS_ERR_UNSUPPORTED;
     const RadixLayout L = radix_layout(key_bytes, vals, n, digit_bits, digit_bits, var->tile_keys, false);
     if (ws_bytes < L.total) return RS_ERR_WORKSPACE;
