@@ -333,9 +333,18 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
             bad |= seg.bits < 8 * sizeof(KeyT) && ((KeyT)(k - klo) >> seg.bits) != 0;
         }
         if (bad && lp.hdr) set_device_error(lp.hdr, RS_ERR_KEY_RANGE, si);
+        // keys already in nondecreasing order (a sorted run) are their own
+        // stable sort: nothing to rank or move.  On unsorted keys nearly every
+        // thread stops at its first pair.
+        __syncthreads();
+        bool in_order = true;
+        for (uint32_t i = threadIdx.x; i + 1 < m && in_order; i += BLOCK) in_order = !(kbuf[0][i + 1] < kbuf[0][i]);
+        const bool already_sorted = __syncthreads_and(in_order) != 0;
         int cur = 0;
-        bool by_keys = true;
-        if (bfn.active()) {
+        bool by_keys = !already_sorted;
+        if (already_sorted) {
+            // output straight from the loaded keys
+        } else if (bfn.active()) {
             const uint64_t b_lo = bfn.first_bucket(seg), span = bfn.bucket_span(seg);
             if (threadIdx.x == 0) *s_flag = 0u;
             __syncthreads();

@@ -182,3 +182,58 @@ def test_warp_uniform_digits_segmented_and_bucket(rs, oracle):
     wk, wv = oracle.bucket_sort(s, vals, int(s.min()), int(s.max()), max(1, n // 16))
     assert_same(from_dev(ok, np.uint32), wk, "bucket sorted keys")
     assert_same(from_dev(ov, np.uint32), wv, "bucket sorted values")
+
+
+# Segments sorted in shared memory (up to 4096 keys) whose keys are already in
+# nondecreasing order are written back as loaded.  The cases mix such segments
+# with near misses (one pair out of order at either end).
+
+@pytest.mark.parametrize("kb", [4, 8])
+def test_already_sorted_small_segments(rs, oracle, kb):
+    import torch
+
+    sizes = synth.log_uniform_sizes(400, 2, 4096, seed=631)
+    n = int(sizes.sum())
+    off = synth.segment_offsets(sizes)
+    keys = synth.u32(n, 630, 0) if kb == 4 else synth.keys_u64(n, 64, seed=630)
+    for s_ in range(len(sizes)):
+        a, b = int(off[s_]), int(off[s_ + 1])
+        seg = np.sort(keys[a:b])
+        mode = s_ % 5
+        if mode == 1 and b - a >= 2:
+            seg[-2], seg[-1] = seg[-1], seg[-2]   # one inversion at the end
+        elif mode == 2 and b - a >= 2:
+            seg[0], seg[1] = seg[1], seg[0]       # one inversion at the start
+        elif mode == 3:
+            seg[:] = seg[0]                       # all equal
+        elif mode == 4:
+            seg = seg[::-1].copy()                # descending
+        keys[a:b] = seg
+    vals = synth.index_values(n)
+    kd, vd, od = to_dev(keys), to_dev(vals), to_dev(off.astype(np.uint64))
+    ok, ov = rs.segmented_sort(kd, od, vd)
+    torch.cuda.synchronize()
+    wk, wv = oracle.segmented_radix_sort(keys, off, vals, 8 * kb)
+    assert_same(from_dev(ok, keys.dtype), wk, "sorted-run segments keys")
+    assert_same(from_dev(ov, np.uint32), wv, "sorted-run segments values")
+
+
+def test_already_sorted_single_block_sorts(rs, oracle):
+    import torch
+
+    for n, kind in ((4096, "sorted"), (4000, "equal"), (3000, "last pair swapped"), (1, "one key")):
+        keys = np.sort(synth.u32(n, 632, 0))
+        if kind == "equal":
+            keys[:] = 7
+        elif kind == "last pair swapped" and n >= 2:
+            keys[-2], keys[-1] = keys[-1], keys[-2]
+        _radix(rs, oracle, keys, synth.index_values(n), what=f"one block, {kind}")
+    # typed keys in order: floats with negatives, sorted by value
+    x = np.sort((synth.unit_doubles(3000, 633, 0) * 2 - 1).astype(np.float32))
+    vals = synth.index_values(3000)
+    kd = torch.from_numpy(x.view(np.int32).copy()).cuda()
+    ok, ov = rs.sort_typed(kd, to_dev(vals), kind=2)
+    torch.cuda.synchronize()
+    wk, wv = oracle.sort_typed(x, vals, 2, False)
+    assert_same(ok.cpu().numpy().view(np.uint32), wk.view(np.uint32), "typed floats in order")
+    assert_same(ov.cpu().numpy().view(np.uint32), wv, "typed floats in order, values")
