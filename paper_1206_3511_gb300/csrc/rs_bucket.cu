@@ -114,6 +114,10 @@ struct BucketCountDigits {
     __device__ __forceinline__ bool in_range(KeyT k) const {
         return (uint64_t)k >= bp.min && (uint64_t)k <= bp.max;
     }
+    template <typename KeyT>
+    __device__ __forceinline__ KeyT order(KeyT k) const {
+        return k;
+    }
 };
 
 // ceil(b * range / nb): how many key values lie below bucket b (exact).

@@ -32,7 +32,8 @@ struct WsHeader {
     // The whole header is zeroed at the start of every call.
     uint32_t status;        // first device error of the last call (RS_OK = none)
     uint32_t error_detail;  // tile or block index of that error, for debugging
-    uint32_t reserved0[6];
+    uint32_t unsorted;      // radix sort: nonzero once a key is found above its successor
+    uint32_t reserved0[5];
     uint32_t tile_ctr[kMaxPasses];  // dynamic tile counters, one per pass
     uint32_t done_ctr[8];           // "last block" counters
     uint32_t reserved1[64 - 8 - kMaxPasses - 8];

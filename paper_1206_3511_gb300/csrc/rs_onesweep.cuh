@@ -83,6 +83,11 @@ struct RadixDigits {
     __device__ __forceinline__ bool in_range(KeyT k) const {
         return key_bits >= (int)(8 * sizeof(KeyT)) || (k >> key_bits) == 0;
     }
+    // the order the sort produces: by the key itself
+    template <typename KeyT>
+    __device__ __forceinline__ KeyT order(KeyT k) const {
+        return k;
+    }
 };
 
 // RadixDigits of the ordered image of typed keys (signed, float, descending):
@@ -100,6 +105,11 @@ struct OrderedRadixDigits {
     __device__ __forceinline__ bool in_range(KeyT) const {
         return true;
     }
+    // the order the sort produces: by the ordered image
+    template <typename KeyT>
+    __device__ __forceinline__ KeyT order(KeyT k) const {
+        return xf.to_ordered(k);
+    }
 };
 
 struct CountParams {
@@ -112,6 +122,7 @@ struct CountParams {
     uint32_t* zero_ptr;  // words zeroed by the kernel (first pass's status words)
     size_t zero_words;
     WsHeader* hdr;
+    uint32_t* unsorted;  // nonnull: set nonzero if some key is above the next one (in dg's order)
 };
 
 constexpr int kCountBlock = 512;
@@ -148,10 +159,20 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Dig
     const size_t nvec = (p.n - head) / kPerVec;
     const size_t tail0 = head + nvec * kPerVec;
     bool bad = false;
+    // with p.unsorted: is every key at most the next one?  Each key is
+    // compared with its successor, wherever that is loaded.
+    const bool check = p.unsorted != nullptr;
+    bool inv = false;
     const size_t gthreads = (size_t)gridDim.x * kCountBlock;
     const size_t gtid = (size_t)blockIdx.x * kCountBlock + tid;
-    for (size_t i = gtid; i < head; i += gthreads) count_key<KeyT>(s_cnt, keys[i], dg, p.passes, bins, bad);
-    for (size_t i = tail0 + gtid; i < p.n; i += gthreads) count_key<KeyT>(s_cnt, keys[i], dg, p.passes, bins, bad);
+    for (size_t i = gtid; i < head; i += gthreads) {
+        count_key<KeyT>(s_cnt, keys[i], dg, p.passes, bins, bad);
+        if (check && i + 1 < p.n) inv |= dg.order(keys[i + 1]) < dg.order(keys[i]);
+    }
+    for (size_t i = tail0 + gtid; i < p.n; i += gthreads) {
+        count_key<KeyT>(s_cnt, keys[i], dg, p.passes, bins, bad);
+        if (check && i + 1 < p.n) inv |= dg.order(keys[i + 1]) < dg.order(keys[i]);
+    }
     const uint4* vec = reinterpret_cast<const uint4*>(keys + head);
     constexpr size_t kChunk = (size_t)kCountBlock * kCountVecIters;
     for (size_t base = (size_t)blockIdx.x * kChunk; base < nvec; base += (size_t)gridDim.x * kChunk) {
@@ -168,11 +189,17 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Dig
                 const KeyT* kk = reinterpret_cast<const KeyT*>(&v[j]);
 #pragma unroll
                 for (int e = 0; e < kPerVec; ++e) count_key<KeyT>(s_cnt, kk[e], dg, p.passes, bins, bad);
+                if (check) {
+#pragma unroll
+                    for (int e = 0; e + 1 < kPerVec; ++e) inv |= dg.order(kk[e + 1]) < dg.order(kk[e]);
+                    const size_t nxt = head + (idx + 1) * kPerVec;  // the key after this vector
+                    if (nxt < p.n) inv |= dg.order(keys[nxt]) < dg.order(kk[kPerVec - 1]);
+                }
             }
         }
     }
     if (bad) set_device_error(p.hdr, RS_ERR_KEY_RANGE, blockIdx.x);
-    __syncthreads();
+    if (__syncthreads_or(inv) && tid == 0) atomicOr(p.unsorted, 1u);
     for (int i = tid; i < ncnt; i += kCountBlock)
         if (s_cnt[i]) atomicAdd(&p.counts[i], s_cnt[i]);
 
@@ -228,6 +255,14 @@ struct PassParams {
     int stall_tile;              // test hook: this tile never publishes (-1 = off)
     KeyXform xf;                 // typed keys: map loaded keys to their ordered image (xf_in) and
     int xf_in, xf_out;           // stored keys back (xf_out); both 0 for unsigned keys
+    // Radix sorts: the count kernel's verdict on the sort's input (nullable).
+    // If no key is above its successor, the input is its own stable sort:
+    // every pass returns at once, except the last, which copies the input
+    // (sorted_keys, sorted_vals) to its output.
+    const uint32_t* unsorted;
+    const void* sorted_keys;
+    const uint32_t* sorted_vals;
+    int last_pass;
 };
 
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS>
@@ -538,6 +573,36 @@ __device__ __forceinline__ void identity_pass(const PassParams<DigitOp>& p, uint
     }
 }
 
+// The sort's input, already in order, copied unchanged to the last pass's
+// output (keys as given: typed keys are neither mapped nor mapped back).
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename DigitOp>
+__device__ __forceinline__ void copy_sorted_input(const PassParams<DigitOp>& p) {
+    constexpr uint32_t kTile = BLOCK * ITEMS;
+    const KeyT* kin = static_cast<const KeyT*>(p.sorted_keys);
+    KeyT* kout = static_cast<KeyT*>(p.keys_out);
+    if (kin == kout && (!VALS || p.sorted_vals == p.vals_out)) return;  // in place: already there
+    for (uint32_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+        const uint32_t base = tile * kTile;
+        const uint32_t m = min(kTile, p.n - base);
+        KeyT k[ITEMS];
+        uint32_t v[VALS ? ITEMS : 1];
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t idx = i * BLOCK + threadIdx.x;
+            k[i] = idx < m ? kin[base + idx] : (KeyT)0;
+            if (VALS) v[i] = idx < m ? p.sorted_vals[base + idx] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t idx = i * BLOCK + threadIdx.x;
+            if (idx < m) {
+                kout[base + idx] = k[i];
+                if (VALS) p.vals_out[base + idx] = v[i];
+            }
+        }
+    }
+}
+
 // Persistent: every block claims tiles from the pass's counter until none is
 // left.  A block holds one tile at a time and only waits on tiles claimed
 // earlier, whose blocks are running, so the waits always end.
@@ -551,16 +616,27 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p)
     DigitOp op = p.op;
     op.init();
     const int tid = threadIdx.x;
-    // every key carries the first key's digit iff that digit's exclusive
-    // prefix is 0 and the next digit's is n
+    // mode 2: the sort's input is already in order (see PassParams); mode 1:
+    // every key carries the first key's digit, which holds iff that digit's
+    // exclusive prefix is 0 and the next digit's is n; mode 0: rank and scatter
     if (tid == 0) {
-        KeyT k0 = static_cast<const KeyT*>(p.keys_in)[0];
-        if (XF && p.xf_in) k0 = p.xf.to_ordered(k0);
-        const uint32_t d0 = op(k0);
-        s_tile = p.digit_base[d0] == 0u && (d0 + 1u == bins || p.digit_base[d0 + 1u] == p.n);
+        uint32_t mode = 0;
+        if (p.unsorted && __ldcg(p.unsorted) == 0u) {
+            mode = 2;
+        } else {
+            KeyT k0 = static_cast<const KeyT*>(p.keys_in)[0];
+            if (XF && p.xf_in) k0 = p.xf.to_ordered(k0);
+            const uint32_t d0 = op(k0);
+            mode = p.digit_base[d0] == 0u && (d0 + 1u == bins || p.digit_base[d0 + 1u] == p.n) ? 1u : 0u;
+        }
+        s_tile = mode;
     }
     __syncthreads();
-    if (s_tile) {
+    if (s_tile == 2u) {
+        if (p.last_pass) copy_sorted_input<KeyT, VALS, BLOCK, ITEMS>(p);
+        return;
+    }
+    if (s_tile == 1u) {
         identity_pass<KeyT, VALS, BLOCK, ITEMS, DigitOp, XF>(p, bins);
         return;
     }

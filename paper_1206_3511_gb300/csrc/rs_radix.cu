@@ -174,8 +174,9 @@ rs_status resolve_config(int key_bytes, bool vals, size_t n, bool typed, const r
 // of `passes` digits starting at bit shift0.  counts must be zero already.
 rs_status enqueue_digit_counts(int key_bytes, const void* keys, size_t n, int shift0, int digit_bits, int passes,
                                int key_bits, uint32_t* counts, uint32_t* scan, uint32_t* zero_ptr,
-                               size_t zero_words, WsHeader* hdr, cudaStream_t stream) {
+                               size_t zero_words, WsHeader* hdr, cudaStream_t stream, uint32_t* unsorted) {
     CountParams cp{};
+    cp.unsorted = unsorted;
     cp.keys = keys;
     cp.n = n;
     cp.passes = passes;
@@ -263,18 +264,21 @@ rs_status radix_sort_xf(int key_bytes, const void* keys_in, void* keys_out, cons
         }
     }
     const size_t status_words = (size_t)L.tiles * L.bins;
+    uint32_t* unsorted = &hdr->unsorted;  // the count kernel checks whether the input is already in order
     if (xf.active()) {
-        CountParams cp{src_k, n, P, L.bins, counts, scan, status[0], status_words, hdr};
+        CountParams cp{src_k, n, P, L.bins, counts, scan, status[0], status_words, hdr, unsorted};
         const OrderedRadixDigits dg{RadixDigits{0, D, L.bins - 1u, key_bits}, xf};
         const cudaError_t e = key_bytes == 4 ? launch_counts<uint32_t>(cp, dg, count_grid(n), stream)
                                              : launch_counts<uint64_t>(cp, dg, count_grid(n), stream);
         if (e != cudaSuccess) return RS_ERR_CUDA;
     } else {
         st = enqueue_digit_counts(key_bytes, src_k, n, 0, D, P, key_bits, counts, scan, status[0], status_words, hdr,
-                                  stream);
+                                  stream, unsorted);
         if (st != RS_OK) return st;
     }
 
+    const void* sorted_k = src_k;  // the input of pass 0: the sort's result if already in order
+    const uint32_t* sorted_v = src_v;
     PassParams<RadixDigit> pp{};
     pp.n = (uint32_t)n;
     pp.num_tiles = L.tiles;
@@ -298,6 +302,10 @@ rs_status radix_sort_xf(int key_bytes, const void* keys_in, void* keys_out, cons
         pp.xf = xf;
         pp.xf_in = xf.active() && p == 0;
         pp.xf_out = xf.active() && p == P - 1;
+        pp.unsorted = unsorted;
+        pp.sorted_keys = sorted_k;
+        pp.sorted_vals = sorted_v;
+        pp.last_pass = p == P - 1;
         cudaError_t e = xf.active() ? var->launch_typed(pp, stream) : var->launch(pp, stream);
         if (e != cudaSuccess) return RS_ERR_CUDA;
         src_k = dst_k;

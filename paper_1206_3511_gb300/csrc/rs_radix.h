@@ -81,8 +81,10 @@ cudaError_t launch_counts(const CountParams& p, const Digits& dg, size_t grid, c
     return cudaGetLastError();
 }
 
+// unsorted (nullable): set nonzero if some key is above its successor.
 rs_status enqueue_digit_counts(int key_bytes, const void* keys, size_t n, int shift0, int digit_bits, int passes,
                                int key_bits, uint32_t* counts, uint32_t* scan, uint32_t* zero_ptr,
-                               size_t zero_words, WsHeader* hdr, cudaStream_t stream);
+                               size_t zero_words, WsHeader* hdr, cudaStream_t stream,
+                               uint32_t* unsorted = nullptr);
 
 }  // namespace rs

@@ -237,3 +237,57 @@ def test_already_sorted_single_block_sorts(rs, oracle):
     wk, wv = oracle.sort_typed(x, vals, 2, False)
     assert_same(ok.cpu().numpy().view(np.uint32), wk.view(np.uint32), "typed floats in order")
     assert_same(ov.cpu().numpy().view(np.uint32), wv, "typed floats in order, values")
+
+
+# A radix sort whose input is already in order (the count kernel checks every
+# key against its successor) returns the input: the passes return at once and
+# the last copies the input to the output.
+
+@pytest.mark.parametrize("with_values", [False, True])
+def test_radix_of_input_already_in_order(rs, oracle, with_values):
+    n = 1_000_003
+    vals = synth.index_values(n) if with_values else None
+    keys = np.sort(synth.u32(n, 640, 0) >> np.uint32(8))  # repeated keys, so order of equals shows
+    _radix(rs, oracle, keys, vals, what="in order")
+    _radix(rs, oracle, keys, vals, in_place=True, what="in order, in place (4 passes)")
+    _radix(rs, oracle, keys >> np.uint32(8), vals, key_bits=24, in_place=True, what="in order, in place (3 passes)")
+    miss = keys.copy()
+    miss[-1] = miss[-2] - np.uint32(1)                        # one pair out of order at the end
+    _radix(rs, oracle, miss, vals, what="out of order at the end")
+    miss = keys.copy()
+    miss[0] = miss[1] + np.uint32(1)                          # and at the start
+    _radix(rs, oracle, miss, vals, what="out of order at the start")
+    _radix(rs, oracle, np.sort(synth.keys_u64(n, 64, seed=641)), synth.index_values(n), what="u64 in order")
+
+
+def test_typed_input_already_in_order(rs, oracle):
+    import torch
+
+    n = 500_001
+    vals = synth.index_values(n)
+    x = np.sort((synth.unit_doubles(n, 642, 0) * 2e6 - 1e6).astype(np.float32))
+    for desc, arr in ((False, x), (True, x[::-1].copy())):   # in order for the requested direction
+        kd = torch.from_numpy(arr.view(np.int32).copy()).cuda()
+        ok, ov = rs.sort_typed(kd, to_dev(vals), kind=2, descending=desc)
+        torch.cuda.synchronize()
+        wk, wv = oracle.sort_typed(arr, vals, 2, desc)
+        assert_same(ok.cpu().numpy().view(np.uint32), wk.view(np.uint32), f"typed in order desc={desc}")
+        assert_same(ov.cpu().numpy().view(np.uint32), wv, f"typed in order desc={desc} values")
+
+
+def test_plan_replay_alternating_in_order_and_not(rs, oracle):
+    """The verdict is taken afresh on every call: a plan replayed on ordered
+    and then on unordered keys in the same buffer sorts both."""
+    import torch
+
+    n = 2_000_000
+    kd = to_dev(synth.u32(n, 643, 0))
+    ok = torch.empty_like(kd)
+    plan = rs.Plan(rs.RS_PLAN_RADIX, kd, ok)
+    for rep in range(2):
+        for keys in (np.sort(synth.u32(n, 644 + rep, 0)), synth.u32(n, 646 + rep, 0)):
+            kd.copy_(to_dev(keys))
+            plan.launch()
+            torch.cuda.synchronize()
+            assert_same(from_dev(ok, np.uint32), np.sort(keys), f"replay {rep}")
+    plan.close()
