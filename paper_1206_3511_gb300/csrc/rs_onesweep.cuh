@@ -165,13 +165,15 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Dig
     bool inv = false;
     const size_t gthreads = (size_t)gridDim.x * kCountBlock;
     const size_t gtid = (size_t)blockIdx.x * kCountBlock + tid;
+    // (a thread stops checking at its first inversion: on unordered keys
+    // that is its first few keys)
     for (size_t i = gtid; i < head; i += gthreads) {
         count_key<KeyT>(s_cnt, keys[i], dg, p.passes, bins, bad);
-        if (check && i + 1 < p.n) inv |= dg.order(keys[i + 1]) < dg.order(keys[i]);
+        if (check && !inv && i + 1 < p.n) inv = dg.order(keys[i + 1]) < dg.order(keys[i]);
     }
     for (size_t i = tail0 + gtid; i < p.n; i += gthreads) {
         count_key<KeyT>(s_cnt, keys[i], dg, p.passes, bins, bad);
-        if (check && i + 1 < p.n) inv |= dg.order(keys[i + 1]) < dg.order(keys[i]);
+        if (check && !inv && i + 1 < p.n) inv = dg.order(keys[i + 1]) < dg.order(keys[i]);
     }
     const uint4* vec = reinterpret_cast<const uint4*>(keys + head);
     constexpr size_t kChunk = (size_t)kCountBlock * kCountVecIters;
@@ -189,11 +191,11 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Dig
                 const KeyT* kk = reinterpret_cast<const KeyT*>(&v[j]);
 #pragma unroll
                 for (int e = 0; e < kPerVec; ++e) count_key<KeyT>(s_cnt, kk[e], dg, p.passes, bins, bad);
-                if (check) {
+                if (check && !inv) {
 #pragma unroll
                     for (int e = 0; e + 1 < kPerVec; ++e) inv |= dg.order(kk[e + 1]) < dg.order(kk[e]);
                     const size_t nxt = head + (idx + 1) * kPerVec;  // the key after this vector
-                    if (nxt < p.n) inv |= dg.order(keys[nxt]) < dg.order(kk[kPerVec - 1]);
+                    if (!inv && nxt < p.n) inv = dg.order(keys[nxt]) < dg.order(kk[kPerVec - 1]);
                 }
             }
         }
@@ -211,7 +213,18 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Dig
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // Keys already in order are their own stable sort.  Then every pass's
+    // prefixes are written as if all keys carried the first key's digit, so
+    // that every pass takes its copy path: the copies carry the input to the
+    // output unchanged (and the typed-key mapping there and back).
+    const bool in_order = p.unsorted && __ldcg(p.unsorted) == 0u;
+    const KeyT k0 = static_cast<const KeyT*>(p.keys)[0];
     for (int q = 0; q < p.passes; ++q) {
+        if (in_order) {
+            const uint32_t d0 = dg(k0, q);
+            for (uint32_t d = tid; d < bins; d += kCountBlock) p.scan[q * bins + d] = d <= d0 ? 0u : (uint32_t)p.n;
+            continue;
+        }
         for (uint32_t d = tid; d < bins; d += kCountBlock) s_cnt[d] = __ldcg(&p.counts[q * bins + d]);
         __syncthreads();
         block_exclusive_scan_smem<kCountBlock>(s_cnt, (int)bins, s_scan);
@@ -255,14 +268,6 @@ struct PassParams {
     int stall_tile;              // test hook: this tile never publishes (-1 = off)
     KeyXform xf;                 // typed keys: map loaded keys to their ordered image (xf_in) and
     int xf_in, xf_out;           // stored keys back (xf_out); both 0 for unsigned keys
-    // Radix sorts: the count kernel's verdict on the sort's input (nullable).
-    // If no key is above its successor, the input is its own stable sort:
-    // every pass returns at once, except the last, which copies the input
-    // (sorted_keys, sorted_vals) to its output.
-    const uint32_t* unsorted;
-    const void* sorted_keys;
-    const uint32_t* sorted_vals;
-    int last_pass;
 };
 
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS>
@@ -573,36 +578,6 @@ __device__ __forceinline__ void identity_pass(const PassParams<DigitOp>& p, uint
     }
 }
 
-// The sort's input, already in order, copied unchanged to the last pass's
-// output (keys as given: typed keys are neither mapped nor mapped back).
-template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename DigitOp>
-__device__ __forceinline__ void copy_sorted_input(const PassParams<DigitOp>& p) {
-    constexpr uint32_t kTile = BLOCK * ITEMS;
-    const KeyT* kin = static_cast<const KeyT*>(p.sorted_keys);
-    KeyT* kout = static_cast<KeyT*>(p.keys_out);
-    if (kin == kout && (!VALS || p.sorted_vals == p.vals_out)) return;  // in place: already there
-    for (uint32_t tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
-        const uint32_t base = tile * kTile;
-        const uint32_t m = min(kTile, p.n - base);
-        KeyT k[ITEMS];
-        uint32_t v[VALS ? ITEMS : 1];
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const uint32_t idx = i * BLOCK + threadIdx.x;
-            k[i] = idx < m ? kin[base + idx] : (KeyT)0;
-            if (VALS) v[i] = idx < m ? p.sorted_vals[base + idx] : 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < ITEMS; ++i) {
-            const uint32_t idx = i * BLOCK + threadIdx.x;
-            if (idx < m) {
-                kout[base + idx] = k[i];
-                if (VALS) p.vals_out[base + idx] = v[i];
-            }
-        }
-    }
-}
-
 // Persistent: every block claims tiles from the pass's counter until none is
 // left.  A block holds one tile at a time and only waits on tiles claimed
 // earlier, whose blocks are running, so the waits always end.
@@ -616,27 +591,16 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p)
     DigitOp op = p.op;
     op.init();
     const int tid = threadIdx.x;
-    // mode 2: the sort's input is already in order (see PassParams); mode 1:
-    // every key carries the first key's digit, which holds iff that digit's
-    // exclusive prefix is 0 and the next digit's is n; mode 0: rank and scatter
+    // every key carries the first key's digit iff that digit's exclusive
+    // prefix is 0 and the next digit's is n
     if (tid == 0) {
-        uint32_t mode = 0;
-        if (p.unsorted && __ldcg(p.unsorted) == 0u) {
-            mode = 2;
-        } else {
-            KeyT k0 = static_cast<const KeyT*>(p.keys_in)[0];
-            if (XF && p.xf_in) k0 = p.xf.to_ordered(k0);
-            const uint32_t d0 = op(k0);
-            mode = p.digit_base[d0] == 0u && (d0 + 1u == bins || p.digit_base[d0 + 1u] == p.n) ? 1u : 0u;
-        }
-        s_tile = mode;
+        KeyT k0 = static_cast<const KeyT*>(p.keys_in)[0];
+        if (XF && p.xf_in) k0 = p.xf.to_ordered(k0);
+        const uint32_t d0 = op(k0);
+        s_tile = p.digit_base[d0] == 0u && (d0 + 1u == bins || p.digit_base[d0 + 1u] == p.n);
     }
     __syncthreads();
-    if (s_tile == 2u) {
-        if (p.last_pass) copy_sorted_input<KeyT, VALS, BLOCK, ITEMS>(p);
-        return;
-    }
-    if (s_tile == 1u) {
+    if (s_tile) {
         identity_pass<KeyT, VALS, BLOCK, ITEMS, DigitOp, XF>(p, bins);
         return;
     }

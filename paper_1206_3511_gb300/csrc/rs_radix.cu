@@ -277,8 +277,6 @@ rs_status radix_sort_xf(int key_bytes, const void* keys_in, void* keys_out, cons
         if (st != RS_OK) return st;
     }
 
-    const void* sorted_k = src_k;  // the input of pass 0: the sort's result if already in order
-    const uint32_t* sorted_v = src_v;
     PassParams<RadixDigit> pp{};
     pp.n = (uint32_t)n;
     pp.num_tiles = L.tiles;
@@ -302,10 +300,6 @@ rs_status radix_sort_xf(int key_bytes, const void* keys_in, void* keys_out, cons
         pp.xf = xf;
         pp.xf_in = xf.active() && p == 0;
         pp.xf_out = xf.active() && p == P - 1;
-        pp.unsorted = unsorted;
-        pp.sorted_keys = sorted_k;
-        pp.sorted_vals = sorted_v;
-        pp.last_pass = p == P - 1;
         cudaError_t e = xf.active() ? var->launch_typed(pp, stream) : var->launch(pp, stream);
         if (e != cudaSuccess) return RS_ERR_CUDA;
         src_k = dst_k;
