@@ -70,6 +70,7 @@ __device__ __forceinline__ T warp_max(T x) {
 // Digit q of a key for the counting kernels: (x >> (shift0 + q*D)) & mask,
 // and the key-range check (every key must be below 2^key_bits).
 struct RadixDigits {
+    static constexpr bool kBytesCapable = true;
     int shift0;
     int digit_bits;
     uint32_t mask;
@@ -88,12 +89,15 @@ struct RadixDigits {
     __device__ __forceinline__ KeyT order(KeyT k) const {
         return k;
     }
+    // digit q is byte q of order(k) (8-bit digits from bit 0)
+    __host__ __device__ bool byte_digits() const { return shift0 == 0 && digit_bits == 8; }
 };
 
 // RadixDigits of the ordered image of typed keys (signed, float, descending):
 // every key is mapped by to_ordered before its digits are taken; all 2^w
 // images are valid, so there is no range check.
 struct OrderedRadixDigits {
+    static constexpr bool kBytesCapable = true;
     RadixDigits base;
     KeyXform xf;
     __device__ __forceinline__ void init() {}
@@ -110,6 +114,7 @@ struct OrderedRadixDigits {
     __device__ __forceinline__ KeyT order(KeyT k) const {
         return xf.to_ordered(k);
     }
+    __host__ __device__ bool byte_digits() const { return base.byte_digits(); }
 };
 
 struct CountParams {
@@ -128,14 +133,23 @@ struct CountParams {
 constexpr int kCountBlock = 512;
 constexpr int kCountVecIters = 8;  // 16-byte loads per thread per chunk
 
-template <typename KeyT, typename Digits>
+// BYTES: digit q is byte q of dg.order(k) (8-bit digits from bit 0, the
+// usual case): the key is mapped once and every digit is a fixed byte.
+template <typename KeyT, typename Digits, bool BYTES>
 __device__ __forceinline__ void count_key(uint32_t* s_cnt, KeyT k, const Digits& dg, int P, uint32_t bins,
                                           bool& bad) {
     bad |= !dg.in_range(k);
-    for (int q = 0; q < P; ++q) atomicAdd(&s_cnt[q * bins + dg(k, q)], 1u);
+    if (BYTES) {
+        const KeyT o = dg.order(k);
+#pragma unroll
+        for (int q = 0; q < (int)sizeof(KeyT); ++q)
+            if (q < P) atomicAdd(&s_cnt[q * 256 + (uint32_t)((o >> (8 * q)) & 0xffu)], 1u);
+    } else {
+        for (int q = 0; q < P; ++q) atomicAdd(&s_cnt[q * bins + dg(k, q)], 1u);
+    }
 }
 
-template <typename KeyT, typename Digits>
+template <typename KeyT, typename Digits, bool BYTES = false>
 __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Digits dg) {
     extern __shared__ uint32_t s_cnt[];  // [P][bins], then kCountBlock/32+1 scan words
     __shared__ uint32_t s_last;
@@ -168,11 +182,11 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Dig
     // (a thread stops checking at its first inversion: on unordered keys
     // that is its first few keys)
     for (size_t i = gtid; i < head; i += gthreads) {
-        count_key<KeyT>(s_cnt, keys[i], dg, p.passes, bins, bad);
+        count_key<KeyT, Digits, BYTES>(s_cnt, keys[i], dg, p.passes, bins, bad);
         if (check && !inv && i + 1 < p.n) inv = dg.order(keys[i + 1]) < dg.order(keys[i]);
     }
     for (size_t i = tail0 + gtid; i < p.n; i += gthreads) {
-        count_key<KeyT>(s_cnt, keys[i], dg, p.passes, bins, bad);
+        count_key<KeyT, Digits, BYTES>(s_cnt, keys[i], dg, p.passes, bins, bad);
         if (check && !inv && i + 1 < p.n) inv = dg.order(keys[i + 1]) < dg.order(keys[i]);
     }
     const uint4* vec = reinterpret_cast<const uint4*>(keys + head);
@@ -190,7 +204,7 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Dig
             if (idx < nvec) {
                 const KeyT* kk = reinterpret_cast<const KeyT*>(&v[j]);
 #pragma unroll
-                for (int e = 0; e < kPerVec; ++e) count_key<KeyT>(s_cnt, kk[e], dg, p.passes, bins, bad);
+                for (int e = 0; e < kPerVec; ++e) count_key<KeyT, Digits, BYTES>(s_cnt, kk[e], dg, p.passes, bins, bad);
                 if (check && !inv) {
 #pragma unroll
                     for (int e = 0; e + 1 < kPerVec; ++e) inv |= dg.order(kk[e + 1]) < dg.order(kk[e]);

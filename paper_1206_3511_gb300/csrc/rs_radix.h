@@ -66,9 +66,9 @@ rs_status radix_sort_xf(int key_bytes, const void* keys_in, void* keys_out, cons
 size_t count_grid(size_t n);
 
 // Launch the digit-count kernel with a digit functor.
-template <typename KeyT, typename Digits>
-cudaError_t launch_counts(const CountParams& p, const Digits& dg, size_t grid, cudaStream_t s) {
-    auto kern = k_digit_counts<KeyT, Digits>;
+template <typename KeyT, typename Digits, bool BYTES>
+cudaError_t launch_counts_as(const CountParams& p, const Digits& dg, size_t grid, cudaStream_t s) {
+    auto kern = k_digit_counts<KeyT, Digits, BYTES>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -79,6 +79,15 @@ cudaError_t launch_counts(const CountParams& p, const Digits& dg, size_t grid, c
     KernelScope scope("digit_counts", s);
     kern<<<(unsigned)grid, kCountBlock, (p.passes * p.bins + kCountBlock / 32 + 1) * 4, s>>>(p, dg);
     return cudaGetLastError();
+}
+
+// 8-bit digits from bit 0 take the kernel that reads them as bytes.
+template <typename KeyT, typename Digits>
+cudaError_t launch_counts(const CountParams& p, const Digits& dg, size_t grid, cudaStream_t s) {
+    if constexpr (Digits::kBytesCapable) {
+        if (dg.byte_digits()) return launch_counts_as<KeyT, Digits, true>(p, dg, grid, s);
+    }
+    return launch_counts_as<KeyT, Digits, false>(p, dg, grid, s);
 }
 
 // unsorted (nullable): set nonzero if some key is above its successor.
