@@ -4,6 +4,8 @@
 //    Algorithm 3) for every pass of the radix sort (Sec. 2.5, Algorithm 4) in
 //    one read of the keys; the last block turns the counts into exclusive
 //    prefixes, which are the counting sort's "number of smaller digits".
+//    For radix sorts it also checks whether the keys are already in order,
+//    and if so writes prefixes that send every pass down its copy path.
 //
 //  k_onesweep: one stable counting-sort pass (the placement loop of Algorithm
 //    3) done block-wise, in the manner of Onesweep (Adinets & Merrill,
@@ -13,7 +15,9 @@
 //    number of equal digits in all earlier tiles through a decoupled
 //    look-back over per-(tile, digit) status words, and writes each key to
 //    digit_base[d] + (earlier tiles' d) + (rank inside the tile).  The keys
-//    are read once and written once per pass.
+//    are read once and written once per pass.  A pass whose keys all carry
+//    one digit copies its input (identity_pass); a warp whose keys all carry
+//    one digit ranks them by position.
 #pragma once
 
 #include "rs_common.cuh"
