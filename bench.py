@@ -188,6 +188,23 @@ def cub_context(d_keys, n, stream, reps=20):
 E2E_REPEATS = 5
 
 
+def pass_bytes(n, key_bytes, has_values) -> int:
+    """Algorithmic HBM bytes of one scatter pass: every key (and value) read
+    once and written once."""
+    return 2 * n * (key_bytes + (4 if has_values else 0))
+
+
+def sort_bytes(algo, n, key_bytes, has_values, key_bits=0, digit_bits=8) -> int:
+    """Algorithmic HBM bytes of one whole sort.  Radix: one read of the keys
+    to count every digit, then one read and one write of keys (and values)
+    per pass.  Bucket: one read to count, then a read and a write to scatter
+    into buckets and another to sort the buckets."""
+    if algo == "bucket":
+        return n * key_bytes + 2 * pass_bytes(n, key_bytes, has_values)
+    passes = -(-(key_bits or 8 * key_bytes) // digit_bits)
+    return n * key_bytes + passes * pass_bytes(n, key_bytes, has_values)
+
+
 def host_link_rates(h_src, h_dst, d_a, d_b, reps=3) -> dict:
     """Copy rates of the host link on the step's own pinned buffers: host to
     device alone, device to host alone, and both at once on two streams
@@ -638,7 +655,6 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6800.0
-    w = kb + (4 if has_v else 0)
     # dominant kernel by time inside the timed region: its algorithmic bytes
     # per step over its device time per step (for a kernel launched once per
     # pass this is bytes per launch over the mean launch time)
@@ -648,9 +664,9 @@ def run_ours(args):
         nl, tot = kstats[top]
         per_step_launches = nl / prof_steps
         if top == "onesweep_pass":
-            step_bytes = 2 * n * w * per_step_launches
+            step_bytes = pass_bytes(n, kb, has_v) * per_step_launches
         elif top in SCATTER_KERNELS:
-            step_bytes = 2 * n * w  # the launches of one step move every key once
+            step_bytes = pass_bytes(n, kb, has_v)  # the launches of one step move every key once
         else:
             step_bytes = n * kb * per_step_launches
         step_s = tot / prof_steps / 1e3
@@ -661,14 +677,7 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": step_bytes / per_step_launches,
                     "avg_launch_ms": tot / nl, "launches": nl,
                     "timing": f"CUDA events around every launch over a repeat of the {prof_steps} timed steps"}
-    if algo == "bucket":
-        # one read to count, one read+write to scatter into buckets, one
-        # read+write to sort the buckets
-        whole_bytes = n * kb + 4 * n * w
-    else:
-        digit_bits = tuned[0] if tuned else 8
-        passes = -(-key_bits // digit_bits)
-        whole_bytes = n * kb + passes * 2 * n * w
+    whole_bytes = sort_bytes(algo, n, kb, has_v, key_bits, tuned[0] if (tuned and algo == "radix") else 8)
     step_s = ms / args.steps / 1e3
     whole = {"algorithmic_bytes_per_step": whole_bytes,
              "achieved_gbs": whole_bytes / step_s / 1e9,
@@ -1141,11 +1150,9 @@ def run_paper_cases(args):
 
 # ------------------------------------------------------------------ served workload
 def served_bytes(n, kind):
-    """Algorithmic HBM bytes of one radix request: one read to count, then
-    per pass a read and a write of keys (and values)."""
-    if kind == 0:
-        return n * 4 + 4 * 2 * n * 4
-    return n * 8 + 8 * 2 * n * 12
+    """Algorithmic HBM bytes of one radix request of the served mix: kind 0
+    is uint32 keys only, kind 1 uint64 keys with uint32 values."""
+    return sort_bytes("radix", n, 4, False) if kind == 0 else sort_bytes("radix", n, 8, True)
 
 
 def run_served(args):
@@ -1213,8 +1220,7 @@ def run_served(args):
             vout = abase + out_off[i] + 8 * n if kd == 1 else None
             if use_bucket[i]:
                 reqs.append(_lib.RsRequest(rs.RS_ALGO_BUCKET, kb, kin, kout, vin, vout, n, 0, lo, hi, 0))
-                w = kb + (4 if kd == 1 else 0)
-                nbytes += n * kb + 4 * n * w
+                nbytes += sort_bytes("bucket", n, kb, kd == 1)
             else:
                 reqs.append(_lib.RsRequest(rs.RS_ALGO_RADIX, kb, kin, kout, vin, vout, n, 8 * kb, 1, 0, 0))
                 nbytes += served_bytes(n, kd)
