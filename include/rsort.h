@@ -236,8 +236,12 @@ RS_API rs_status rs_counting_pass_u64(const uint64_t* keys_in, uint64_t* keys_ou
  * RS_MAX_KEYS - 1 keys.  Segments of up to 4096 keys are sorted inside one
  * thread block in shared memory, larger ones by segmented scatter passes; the
  * classification is done on the device, so the call never waits for the GPU.
- * An offsets table that decreases or has a segment above the limit is
- * reported as RS_ERR_INVALID_ARG by rs_get_status() (output unspecified).
+ * An offsets table that decreases, runs past n_total or has a segment above
+ * the limit is reported as RS_ERR_INVALID_ARG by rs_get_status(): such
+ * segments are dropped (their output is unspecified), every other segment is
+ * sorted, and nothing is written outside [0, n_total) of the arrays or the
+ * workspace.  A key with bits at or above key_bits is reported as
+ * RS_ERR_KEY_RANGE (that segment's output is unspecified).
  * Workspace: rs_segmented_workspace_bytes(key_bytes, has_values, n_total,
  * nseg, key_bits).  In place (keys_out == keys_in) is allowed.
  */
@@ -368,7 +372,13 @@ RS_API rs_status rs_server_submit(rs_server* s, const rs_request* req, uint64_t*
 /* Status of a request without waiting (RS_ERR_NOT_READY while not done). */
 RS_API rs_status rs_server_poll(rs_server* s, uint64_t ticket, rs_result* out);
 /* Wait up to timeout_ms (< 0: forever) for a request; its status, or
- * RS_ERR_NOT_READY on timeout. */
+ * RS_ERR_NOT_READY on timeout.  A finished request's status is the host-side
+ * result of launching it (argument or CUDA errors) or, when that succeeded,
+ * the device status word of its sort as rs_get_status() would read it
+ * (RS_ERR_KEY_RANGE for a key above key_bits or outside the declared bucket
+ * range, RS_ERR_DEVICE_TIMEOUT, ...).  A batched request shares the status
+ * word of its batch: a device error in one request of a batch is reported by
+ * every request of that batch. */
 RS_API rs_status rs_server_wait(rs_server* s, uint64_t ticket, int timeout_ms);
 /* Forget a finished request: its record (status and times) is freed and the
  * ticket becomes unknown (later calls on it return RS_ERR_INVALID_ARG).  A

@@ -53,6 +53,15 @@ rs_status scratch_for_current_device(void** out) {
     return RS_OK;
 }
 
+// Workspace of the largest call this entry point accepts: RS_NOALLOC_MAX_KEYS
+// keys with values, 32 key bits, the default kernel shape and digit width
+// (the ones a call without an explicit shape uses).
+size_t noalloc_scratch_needed() {
+    const Variant* v = default_variant(4, true, RS_NOALLOC_MAX_KEYS, false);
+    if (!v) return ~(size_t)0;
+    return radix_layout(4, true, RS_NOALLOC_MAX_KEYS, 32, kDefaultDigitBits, v->tile_keys, true).total;
+}
+
 }  // namespace
 }  // namespace rs
 
@@ -61,10 +70,12 @@ using namespace rs;
 extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
                                          uint32_t* vals_out, size_t n, int key_bits, rs_stream_t stream) {
     if (n > RS_NOALLOC_MAX_KEYS) return RS_ERR_INVALID_ARG;
-    if (n == 0) return RS_OK;
     void* scratch = nullptr;
     rs_status st = scratch_for_current_device(&scratch);
     if (st != RS_OK) return st;
+    // the array must hold the workspace of the largest sort accepted here,
+    // with values, under every kernel shape the sort may pick
+    if (noalloc_scratch_needed() > kNoAllocScratchBytes) return RS_ERR_UNSUPPORTED;
     // the sort clears the parts of the scratch that must start at zero (the
     // header, the digit counts and the first pass's status words) itself
     return radix_sort_impl(4, keys_in, keys_out, vals_in, vals_out, n, key_bits, scratch, kNoAllocScratchBytes,

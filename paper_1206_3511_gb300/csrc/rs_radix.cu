@@ -69,7 +69,6 @@ const Variant kVariants[] = {
     make_variant<uint64_t, true, 256, 8, 4>(),
     make_variant<uint64_t, true, 384, 8, 3>(),
 };
-constexpr int kDefaultDigitBits = 8;
 // digit widths offered to an autotuner for every kernel shape
 constexpr int kTuneDigitBits[] = {8, 4, 5, 6, 7, 9, 10, 11};
 

@@ -20,6 +20,9 @@ struct Variant {
     size_t (*smem_bytes)(int digit_bits);
 };
 
+// Digit width of a radix sort when no kernel shape is requested.
+constexpr int kDefaultDigitBits = 8;
+
 // Shared memory a block may use on sm_103a (opt-in maximum).
 constexpr size_t kMaxSmemPerBlock = 227 * 1024;
 

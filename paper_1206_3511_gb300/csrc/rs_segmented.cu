@@ -169,7 +169,8 @@ static rs_status large_passes_t(const void* src_k, const uint32_t* src_v, void* 
     RS_CUDA_TRY(cudaMemsetAsync(B.seg_rows, 0, B.max_segs * (size_t)passes * bins * 4, stream));
     RadixDigits dg{0, D, bins - 1u, 64};
     if (launch_seg_counts<KeyT>(static_cast<const KeyT*>(src_k), B.large, B.hdr, B.chunk_seg, B.max_chunks, dg, passes,
-                                bins, B.seg_rows, B.status[0], B.max_tiles * (size_t)bins, stream) != cudaSuccess)
+                                bins, B.seg_rows, B.status[0], B.max_tiles * (size_t)bins, stream,
+                                B.check_range ? B.ws_hdr : nullptr) != cudaSuccess)
         return RS_ERR_CUDA;
     {
         KernelScope scope("seg_scan", stream);
@@ -308,12 +309,14 @@ static rs_status segmented_impl(int key_bytes, const void* keys_in, void* keys_o
     SegBuffers B = carve_seg_buffers(ws, L);
     B.shape = shape;
     B.tile_keys = seg_shape_tile(key_bytes, vals, shape);
+    B.check_range = true;
     RS_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(WsHeader), stream));
     RS_CUDA_TRY(cudaMemsetAsync(B.hdr, 0, sizeof(SegPlanHdr), stream));
     {
         KernelScope scope("plan_segments", stream);
         k_plan_from_offsets<<<(unsigned)((nseg + 255) / 256), 256, 0, stream>>>(
-            d_offsets, nseg, kLocalCap, B.tile_keys, key_bits, B.large, B.small, B.tiny, B.hdr, B.ws_hdr);
+            d_offsets, nseg, (uint64_t)n_total, kLocalCap, B.tile_keys, key_bits, B.large, B.small, B.tiny, B.hdr,
+            B.ws_hdr);
         if (cudaGetLastError() != cudaSuccess) return RS_ERR_CUDA;
     }
     // large segments: scatter passes from keys_in (in place with an odd pass

@@ -52,14 +52,18 @@ constexpr uint32_t kTinyCap = 256;
 // Segments from an offset table: empty ones are dropped, those of at most
 // kTinyCap keys go to the warp list (when `tiny` is given), those of at most
 // `small_cap` keys to the shared-memory list, the others to the scatter
-// list.  One thread per segment.
-static __global__ void k_plan_from_offsets(const uint64_t* __restrict__ offsets, size_t nseg, uint32_t small_cap,
-                                    uint32_t tile_keys, int bits, SegDesc* large, SegDesc* small, SegDesc* tiny,
-                                    SegPlanHdr* hdr, WsHeader* ws_hdr) {
+// list.  One thread per segment.  A segment whose offsets decrease, that ends
+// past n_total keys, or that is above the single-sort limit is dropped and
+// reported as RS_ERR_INVALID_ARG: every segment kept lies inside the arrays,
+// so the tiles and chunks reserved for them stay within the workspace's
+// bounds (at most n_total / tile + nseg + 1 tiles).
+static __global__ void k_plan_from_offsets(const uint64_t* __restrict__ offsets, size_t nseg, uint64_t n_total,
+                                           uint32_t small_cap, uint32_t tile_keys, int bits, SegDesc* large,
+                                           SegDesc* small, SegDesc* tiny, SegPlanHdr* hdr, WsHeader* ws_hdr) {
     const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg) return;
     const uint64_t a = offsets[s], b = offsets[s + 1];
-    if (b < a || b - a >= ((uint64_t)1 << 30)) {  // decreasing offsets or a segment above the single-sort limit
+    if (b < a || b > n_total || b - a >= ((uint64_t)1 << 30)) {
         set_device_error(ws_hdr, RS_ERR_INVALID_ARG, (uint32_t)s);
         return;
     }
@@ -90,13 +94,15 @@ static __global__ void k_plan_maps(const SegDesc* __restrict__ large, const SegP
 
 // Per-segment digit counts of `passes` digits: seg_counts[li][q][d].  One
 // block per counting chunk of a large segment.  Also zeroes zero_words words
-// at zero_ptr (the first pass's look-back status).
+// at zero_ptr (the first pass's look-back status).  With range_hdr, a key
+// whose (key - key_lo) has bits at or above the segment's `bits` is reported
+// there as RS_ERR_KEY_RANGE.
 template <typename KeyT, typename Digits>
 __global__ void __launch_bounds__(512) k_seg_counts(const KeyT* __restrict__ keys, const SegDesc* __restrict__ large,
                                                     const SegPlanHdr* __restrict__ hdr,
                                                     const uint32_t* __restrict__ chunk_seg, Digits dg, int passes,
                                                     uint32_t bins, uint32_t* seg_counts, uint32_t* zero_ptr,
-                                                    size_t zero_words) {
+                                                    size_t zero_words, WsHeader* range_hdr) {
     extern __shared__ uint32_t s_cnt[];  // [passes][bins]
     const int tid = threadIdx.x;
     const size_t used_words = (size_t)hdr->total_tiles * bins;  // only the rows of tiles that exist
@@ -115,10 +121,14 @@ __global__ void __launch_bounds__(512) k_seg_counts(const KeyT* __restrict__ key
         __syncthreads();
         const KeyT* kp = keys + d.start;
         const KeyT klo = (KeyT)d.key_lo;
+        const bool check = range_hdr && d.bits < 8 * sizeof(KeyT);
+        bool bad = false;
         for (uint32_t i = lo + tid; i < hi; i += blockDim.x) {
             const KeyT x = (KeyT)(__ldcs(kp + i) - klo);
+            bad |= check && (x >> (check ? d.bits : 0)) != 0;
             for (int q = 0; q < passes; ++q) atomicAdd(&s_cnt[q * bins + dg(x, q)], 1u);
         }
+        if (bad) set_device_error(range_hdr, RS_ERR_KEY_RANGE, li);
         __syncthreads();
         uint32_t* out = seg_counts + (size_t)li * ncnt;
         for (int i = tid; i < ncnt; i += blockDim.x)

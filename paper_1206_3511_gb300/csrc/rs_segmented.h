@@ -79,7 +79,7 @@ uint32_t seg_min_tile(int key_bytes, bool vals);
 template <typename KeyT, typename Digits>
 cudaError_t launch_seg_counts(const KeyT* keys, const SegDesc* segs, const SegPlanHdr* hdr, const uint32_t* chunk_seg,
                               size_t max_chunks, const Digits& dg, int passes, uint32_t bins, uint32_t* rows,
-                              uint32_t* zero_ptr, size_t zero_words, cudaStream_t s) {
+                              uint32_t* zero_ptr, size_t zero_words, cudaStream_t s, WsHeader* range_hdr = nullptr) {
     auto kern = k_seg_counts<KeyT, Digits>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
@@ -91,7 +91,8 @@ cudaError_t launch_seg_counts(const KeyT* keys, const SegDesc* segs, const SegPl
     const size_t grid = std::min<size_t>(max_chunks, (size_t)device_sm_count() * 4);
     KernelScope scope("seg_counts", s);
     kern<<<(unsigned)(grid ? grid : 1), 512, (size_t)passes * bins * 4, s>>>(keys, segs, hdr, chunk_seg, dg, passes,
-                                                                            bins, rows, zero_ptr, zero_words);
+                                                                            bins, rows, zero_ptr, zero_words,
+                                                                            range_hdr);
     return cudaGetLastError();
 }
 
@@ -112,6 +113,7 @@ struct SegBuffers {
     int max_passes, max_bins;
     int shape;             // segmented pass shape (index into the compiled shapes; 0 = default)
     uint32_t tile_keys;    // keys per tile of that shape (0: the default shape's)
+    bool check_range;      // report keys with bits at or above a segment's `bits` in ws_hdr
 };
 
 // Workspace layout of a segmented sort: sizes for every region, the offsets

@@ -97,6 +97,7 @@ struct Slot {  // one launch in flight
     std::vector<void*> pool_blocks;
     size_t footprint = 0;
     uint64_t* h_offsets = nullptr;  // pinned, max_batch + 1 entries
+    uint32_t* h_status = nullptr;   // pinned: the device status word of the launch's workspace
 };
 
 size_t request_ws_bytes(const rs_request& r) {
@@ -129,8 +130,13 @@ struct ServerImpl {
     void finish_slot(Slot& s, rs_status st);
 };
 
+// Completes every request of a slot.  A launch that ran reports the status
+// word of its workspace (copied to h_status behind the sort), so errors found
+// on the device (a key outside the declared range, a bounded wait that gave
+// up) reach the request instead of an RS_OK with unspecified output.
 void ServerImpl::finish_slot(Slot& s, rs_status st) {
     const double t = now_ms();
+    if (st == RS_OK && s.h_status && *s.h_status != 0u) st = static_cast<rs_status>(*s.h_status);
     for (uint64_t tk : s.tickets) {
         auto it = reqs.find(tk);
         if (it == reqs.end()) continue;
@@ -152,6 +158,7 @@ bool ServerImpl::launch_single(Slot& s, Request& r) {
     const size_t wsb = request_ws_bytes(q);
     void* ws = pool.alloc(wsb);
     if (!ws) return false;
+    *s.h_status = 0u;  // the slot is free: no copy into it is in flight
     rs_status st;
     const bool u32 = q.key_bytes == 4;
     if (q.algo == RS_ALGO_BUCKET)
@@ -171,7 +178,12 @@ bool ServerImpl::launch_single(Slot& s, Request& r) {
     in_use += r.footprint;
     max_in_use = std::max(max_in_use, in_use);
     r.t_start = now_ms();
+    if (st == RS_OK && cudaMemcpyAsync(s.h_status, ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, s.stream) != cudaSuccess)
+        st = RS_ERR_CUDA;
     if (st != RS_OK || cudaEventRecord(s.done, s.stream) != cudaSuccess) {
+        // work already enqueued on the stream may still use the pool blocks:
+        // let it end before they are handed out again
+        cudaStreamSynchronize(s.stream);
         finish_slot(s, st != RS_OK ? st : RS_ERR_CUDA);
         return true;
     }
@@ -199,6 +211,7 @@ bool ServerImpl::launch_batch(Slot& s, std::vector<Request*>& batch, size_t foot
         for (void* p : {ws, kin, kout, vin, vout, doff}) pool.release(p);
         return false;
     }
+    *s.h_status = 0u;
     s.pool_blocks = {ws, kin, kout, doff};
     if (vals) {
         s.pool_blocks.push_back(vin);
@@ -239,12 +252,16 @@ bool ServerImpl::launch_batch(Slot& s, std::vector<Request*>& batch, size_t foot
             ok &= cudaMemcpyAsync(q.vals_out, static_cast<uint32_t*>(vout) + o, q.n * 4, cudaMemcpyDeviceToDevice,
                                   s.stream) == cudaSuccess;
     }
+    // one status word for the whole batch: every request of it reports it
+    if (ok && st == RS_OK)
+        ok &= cudaMemcpyAsync(s.h_status, ws, sizeof(uint32_t), cudaMemcpyDeviceToHost, s.stream) == cudaSuccess;
     s.footprint = footprint;
     in_use += footprint;
     max_in_use = std::max(max_in_use, in_use);
     ++batches;
     batched_requests += batch.size();
     if (!ok || st != RS_OK || cudaEventRecord(s.done, s.stream) != cudaSuccess) {
+        cudaStreamSynchronize(s.stream);  // enqueued copies and kernels still use the pool blocks
         finish_slot(s, st != RS_OK ? st : RS_ERR_CUDA);
         return true;
     }
@@ -372,11 +389,13 @@ rs_status rs_server_create(const rs_server_config* cfg, rs_server** out) {
     for (Slot& sl : m.slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMallocHost(&sl.h_offsets, ((size_t)cfg->max_batch + 1) * 8) != cudaSuccess) {
+            cudaMallocHost(&sl.h_offsets, ((size_t)cfg->max_batch + 1) * 8) != cudaSuccess ||
+            cudaMallocHost(&sl.h_status, sizeof(uint32_t)) != cudaSuccess) {
             for (Slot& t : m.slots) {
                 if (t.stream) cudaStreamDestroy(t.stream);
                 if (t.done) cudaEventDestroy(t.done);
                 if (t.h_offsets) cudaFreeHost(t.h_offsets);
+                if (t.h_status) cudaFreeHost(t.h_status);
             }
             delete s;
             return RS_ERR_CUDA;
@@ -499,6 +518,7 @@ rs_status rs_server_destroy(rs_server* s, int cancel_pending) {
         cudaStreamDestroy(t.stream);
         cudaEventDestroy(t.done);
         cudaFreeHost(t.h_offsets);
+        cudaFreeHost(t.h_status);
     }
     delete s;
     return RS_OK;

@@ -99,6 +99,51 @@ def test_bad_offsets_are_reported(rs):
     assert rs.get_status(ws) == 1  # RS_ERR_INVALID_ARG recorded on the device
 
 
+@pytest.mark.parametrize("past", [1, 5000])
+def test_offsets_past_n_total_are_reported_and_nothing_is_written_outside(rs, oracle, past):
+    """An offsets table that ends past n_total: the segment that runs past it
+    is dropped and reported as RS_ERR_INVALID_ARG, the segments inside are
+    still sorted, and guard words around the output and after the workspace
+    are unchanged (no write outside the arrays)."""
+    import torch
+
+    sizes = [3000, 70_000, 100]
+    n = sum(sizes)
+    keys = synth.u32(n, 48, 0)
+    off = synth.segment_offsets(sizes).astype(np.uint64)
+    off[-1] = n + past  # the last segment ends past n_total
+    G = 1 << 16
+    guard = -0x21524111  # 0xdeadbeef as int32
+    kd = to_dev(keys)
+    out = torch.full((n + 2 * G,), guard, dtype=torch.int32, device="cuda")
+    wsb = rs.rs_segmented_workspace_bytes(4, 0, n, 3, 32)
+    wsbuf = torch.full((wsb + G,), 0x5A, dtype=torch.uint8, device="cuda")
+    ws = wsbuf[:wsb]
+    assert rs.rs_sort_segmented_u32(kd, out[G:G + n], None, None, to_dev(off), 3, n, 32, ws, wsb) == 0
+    assert rs.get_status(ws) == 1  # RS_ERR_INVALID_ARG
+    o = out.cpu().numpy()
+    assert np.all(o[:G] == guard) and np.all(o[G + n:] == guard)
+    assert np.all(wsbuf[wsb:].cpu().numpy() == 0x5A)
+    got = o[G:G + n].view(np.uint32)
+    for a, b in [(0, 3000), (3000, 73_000)]:  # the segments inside n_total are sorted
+        assert_same(got[a:b], oracle.radix_sort(keys[a:b]), f"segment [{a},{b})")
+
+
+def test_key_above_key_bits_in_a_large_segment_is_reported(rs):
+    import torch
+
+    sizes = [100, 20_000, 300]
+    n = sum(sizes)
+    keys = synth.u32(n, 49, 0) >> np.uint32(20)  # 12-bit keys
+    keys[5_000] = 1 << 12  # inside the scatter-pass segment
+    kd = to_dev(keys)
+    off = to_dev(synth.segment_offsets(sizes))
+    ws = rs.workspace(rs.rs_segmented_workspace_bytes(4, 0, n, 3, 12))
+    out = torch.empty_like(kd)
+    assert rs.rs_sort_segmented_u32(kd, out, None, None, off, 3, n, 12, ws, ws.numel()) == 0
+    assert rs.get_status(ws) == 3  # RS_ERR_KEY_RANGE
+
+
 def test_key_above_key_bits_in_a_small_segment_is_reported(rs):
     import torch
 
@@ -123,10 +168,14 @@ def test_full_batched_workload_sampled_against_oracle(rs, oracle):
     """The batched workload at full size, in the launch configuration the
     benchmark times (a segmented-sort plan replayed from a CUDA graph):
     20,000 uint32 arrays with sizes log-uniform in [256, 2,000,000], about
-    4.5e9 keys, so offsets pass 2^32.  Sampled arrays (including the last,
-    past 2^32) are compared with the oracle; every array is checked on the
-    device to be nondecreasing with its key sum and sum of squares (mod
-    2^64) unchanged."""
+    4.5e9 keys, so offsets pass 2^32.  Every 100th array, every array above
+    1M keys (about 1,500 of them, half the keys) and the edge arrays
+    (including the last, past 2^32) are compared element by element with the
+    oracle; every array is also checked on the device to be nondecreasing
+    with its key sum and sum of squares (mod 2^64) unchanged."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
     import torch
 
     sizes = synth.log_uniform_sizes(20_000, 256, 2_000_000, seed=0)
@@ -141,10 +190,23 @@ def test_full_batched_workload_sampled_against_oracle(rs, oracle):
     plan.launch()
     torch.cuda.synchronize()
     assert rs.get_status(plan.ws) == 0
-    for i in [0, 1, 777, 5000, 10_000, 15_000, 19_998, 19_999, int(np.argmax(sizes)), int(np.argmin(sizes))]:
+    sample = set(range(0, sizes.size, 100)) | set(np.flatnonzero(sizes > 1_000_000).tolist())
+    sample |= {1, 777, 19_998, 19_999, int(np.argmax(sizes)), int(np.argmin(sizes))}
+    sample = sorted(sample)
+    assert len(sample) > 1000
+
+    def compare(i):
+        # the oracle's C routine runs without the GIL, so arrays are checked
+        # on several host threads at once
         a, b = int(off[i]), int(off[i + 1])
         keys = kd[a:b].cpu().numpy().view(np.uint32)
-        assert_same(out[a:b].cpu().numpy().view(np.uint32), oracle.radix_sort(keys, None, 32), f"array {i}")
+        got = out[a:b].cpu().numpy().view(np.uint32)
+        assert_same(got, oracle.radix_sort(keys, None, 32), f"array {i}")
+        return b - a
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        checked = sum(ex.map(compare, sample))
+    assert checked > n // 3
     # properties of every array, in chunks of whole arrays
     starts = torch.from_numpy(off[:-1].view(np.int64)).cuda()
     i0 = 0

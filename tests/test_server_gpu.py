@@ -169,3 +169,72 @@ def test_released_requests_are_forgotten(rs):
         assert srv.release(t) == 1  # RS_ERR_INVALID_ARG: unknown ticket now
         rc, _ = srv.result(t)
         assert rc == 1
+
+
+def test_large_unbatched_requests_in_the_mix_equal_results_alone(rs, oracle):
+    """Requests above batch_max_keys run as single sorts beside the batched
+    small ones: 12M and 10M u32 keys (radix; bucket over declared bounds),
+    10M and 3M u64 keys with index values (radix; bucket over computed
+    bounds), mixed with 24 small requests, each result compared with the
+    oracle."""
+    big = [
+        (synth.keys_u32(12_000_000, 0, seed=201), None, 0, {}),
+        (synth.keys_u32(10_000_000, 6, seed=202), None, 1, dict(zip(("min_key", "max_key"),
+                                                                    synth.DECLARED_BOUNDS[6]))),
+        (synth.keys_u64(10_000_000, 64, seed=203), synth.index_values(10_000_000), 0, {}),
+        (synth.keys_u64(3_000_000, 40, seed=204), synth.index_values(3_000_000), 1, {}),
+    ]
+    small = [(synth.keys_u32(5000 + 311 * i, i % 7, seed=210 + i), None, 0, {}) for i in range(24)]
+    reqs = big[:2] + small[:12] + big[2:] + small[12:]
+    import torch
+
+    with rs.Server(pool_bytes=8 << 30, num_streams=4, max_batch=16, batch_max_keys=1 << 18) as srv:
+        handles = []
+        for keys, vals, algo, bounds in reqs:
+            kd = to_dev(keys)
+            vd = to_dev(vals) if vals is not None else None
+            ko = torch.empty_like(kd)
+            vo = torch.empty_like(vd) if vd is not None else None
+            torch.cuda.synchronize()
+            handles.append((srv.submit(kd, ko, vd, vo, algo=algo, **bounds), ko, vo))
+        for (t, ko, vo), (keys, vals, algo, _) in zip(handles, reqs):
+            assert srv.wait(t, 120_000) == 0
+            gk = from_dev(ko, keys.dtype)
+            if vals is None:
+                assert_same(gk, oracle.radix_sort(keys), f"ticket {t} n={keys.size}")
+            else:
+                wk, wv = oracle.radix_sort(keys, vals)
+                assert_same(gk, wk, f"ticket {t} keys n={keys.size}")
+                assert_same(from_dev(vo, np.uint32), wv, f"ticket {t} values n={keys.size}")
+        assert srv.stats().completed == len(reqs)
+
+
+@pytest.mark.parametrize("algo,n", [(0, 300_000), (0, 2000), (1, 300_000)])
+def test_device_errors_reach_the_request(rs, algo, n):
+    """A key above 2^key_bits (radix) or outside the declared bounds (bucket)
+    is found on the device; the request must end with RS_ERR_KEY_RANGE, not
+    RS_OK.  The 2,000-key radix request is sent with two good ones of the
+    same type, so it may be batched; if it is, its batch reports the error
+    too, and a good request that was not batched with it ends RS_OK."""
+    import torch
+
+    keys = synth.u32(n, 220 + n % 7, 0) >> np.uint32(8)  # 24-bit keys
+    keys[n // 2] = 1 << 24 if algo == 0 else (1 << 24) + 5
+    good = [synth.u32(n, 230 + j, 0) >> np.uint32(8) for j in range(2)]
+    bounds = {} if algo == 0 else {"min_key": 0, "max_key": (1 << 24) - 1}
+    with rs.Server(pool_bytes=1 << 30, num_streams=2, max_batch=8) as srv:
+        outs, tickets = [], []
+        for k in [keys] + good:
+            kd = to_dev(k)
+            ko = torch.empty_like(kd)
+            torch.cuda.synchronize()
+            tickets.append(srv.submit(kd, ko, algo=algo, key_bits=24 if algo == 0 else 0, **bounds))
+            outs.append((k, ko))
+        codes = [srv.wait(t, 60_000) for t in tickets]
+        assert codes[0] == 3  # RS_ERR_KEY_RANGE
+        batched = srv.stats().batches > 0
+        for (k, ko), c in zip(outs[1:], codes[1:]):
+            if c == 0:
+                assert_same(from_dev(ko, np.uint32), np.sort(k), "good request")
+            else:
+                assert batched and c == 3
