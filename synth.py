@@ -241,6 +241,91 @@ def paper_case_keys(n: int, case: int, seed: int = 0) -> np.ndarray:
     raise ValueError(f"no paper case {case}")
 
 
+def _srl_t(z, k: int):
+    """Logical right shift of an int64 torch tensor holding uint64 bits."""
+    return (z >> k) & ((1 << (64 - k)) - 1)
+
+
+def _hi32_t(n: int, seed: int, dist_id: int, stream: int, device, start: int = 0):
+    """The 32-bit draws of u32() (counters start+1 .. start+n) as non-negative
+    int64 values on `device`."""
+    return _srl_t(u64_torch_range(start, start + n, seed, dist_id, stream, device), 32)
+
+
+def _uniform_below_t(n: int, R: int, seed: int, dist_id: int, stream: int, device):
+    """uniform_below() on `device` as int64 values (same numbers)."""
+    d = _hi32_t(n, seed, dist_id, stream, device)
+    return d if R == 2**32 else _srl_t(d * R, 32)
+
+
+def _sorted_spread_t(n: int, seed: int, dist_id: int, hi: int, device):
+    import torch
+
+    i = torch.arange(n, dtype=torch.int64, device=device)
+    width = max(1, hi // n)
+    base = torch.div(i * hi, n, rounding_mode="floor")
+    off = _srl_t(_hi32_t(n, seed, dist_id, 1, device) * width, 32)
+    return torch.clamp(base + off, max=hi - 1)
+
+
+def _as_u32_bits_t(v):
+    """int64 values in [0, 2^32) -> int32 tensor with the same 32 bits."""
+    import torch
+
+    return torch.where(v >= 2**31, v - 2**32, v).to(torch.int32)
+
+
+def keys_u32_torch(n: int, dist: int, seed: int = 0, device="cpu", chunk: int = 1 << 26):
+    """keys_u32(n, dist, seed) built on `device` with torch (distributions
+    0-6), the same bits as the numpy form, as an int32 tensor: for inputs
+    too large to build on the host in good time."""
+    import torch
+
+    dist = int(dist)
+    if dist in (0, 2):
+        return u32_torch(n, seed, dist, device=device)
+    if dist == 1:
+        return _as_u32_bits_t(_uniform_below_t(n, 1000, seed, 1, 0, device))
+    if dist in (3, 4, 5):
+        a = _sorted_spread_t(n, seed, 3, 2**32, device)
+        if dist == 4:
+            a = torch.flip(a, dims=[0])
+        elif dist == 5 and n // 100:
+            # the swaps run one after another, as in the numpy form: replay
+            # them on the host over the positions they touch
+            m = n // 100
+            xs = uniform_below(m, n, seed, 5, 2).astype(np.int64)
+            ys = uniform_below(m, n, seed, 5, 3).astype(np.int64)
+            pos = np.unique(np.concatenate([xs, ys]))
+            vals = a[torch.from_numpy(pos).to(device)].cpu().numpy().tolist()
+            where = {int(p): j for j, p in enumerate(pos.tolist())}
+            for x, y in zip(xs.tolist(), ys.tolist()):
+                jx, jy = where[x], where[y]
+                vals[jx], vals[jy] = vals[jy], vals[jx]
+            a[torch.from_numpy(pos).to(device)] = torch.tensor(vals, dtype=torch.int64, device=device)
+        return _as_u32_bits_t(a)
+    if dist == 6:
+        out = torch.empty(n, dtype=torch.int32, device=device)
+        for a0 in range(0, n, chunk):
+            b0 = min(n, a0 + chunk)
+            s = torch.zeros(b0 - a0, dtype=torch.int64, device=device)
+            for j in range(6):
+                d = u64_torch_range(a0, b0, seed, 6, 10 + j, device)
+                s += _srl_t(d, 32)
+                s += d & 0xFFFFFFFF
+            v = 2**31 + ((s - 6 * 2**32) >> 12)
+            out[a0:b0] = _as_u32_bits_t(torch.clamp(v, 0, 2**32 - 1))
+        return out
+    raise ValueError(f"no device form of distribution {dist}")
+
+
+def keys_u64_shaped_torch(n: int, dist: int, seed: int = 0, device="cpu"):
+    """keys_u64_shaped(n, dist, seed) built on `device` (int64 tensor, same
+    bits)."""
+    hi = keys_u32_torch(n, dist, seed, device).to(__import__("torch").int64) & 0xFFFFFFFF
+    return (hi << 32) | _hi32_t(n, seed, 44, dist, device)
+
+
 def keys_u64(n: int, key_bits: int = 64, seed: int = 0, dist_id: int = 20) -> np.ndarray:
     """n uint64 keys uniform over [0, 2^key_bits)."""
     d = u64(n, seed, dist_id)

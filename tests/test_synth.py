@@ -57,3 +57,17 @@ def test_log_uniform_sizes():
     # the mean of a log-uniform law on [a, b] is (b - a) / ln(b / a)
     want = (2_000_000 - 256) / np.log(2_000_000 / 256)
     assert abs(sz.mean() / want - 1) < 0.03
+
+
+@pytest.mark.parametrize("dist", [0, 1, 2, 3, 4, 5, 6])
+def test_device_form_of_the_distributions_equals_numpy_form(dist):
+    """keys_u32_torch / keys_u64_shaped_torch (the benchmark builds its large
+    inputs with them on the GPU) give the numpy forms' bits; run here on the
+    CPU device."""
+    n = 30_011
+    a = synth.keys_u32(n, dist, seed=3)
+    b = synth.keys_u32_torch(n, dist, seed=3, chunk=7_001).numpy().view(np.uint32)
+    assert np.array_equal(a, b)
+    a64 = synth.keys_u64_shaped(n, dist, seed=4)
+    b64 = synth.keys_u64_shaped_torch(n, dist, seed=4).numpy().view(np.uint64)
+    assert np.array_equal(a64, b64)
