@@ -109,6 +109,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="radix: pick the kernel shape with the autotuner")
     ap.add_argument("--no-context", action="store_true", help="skip the torch.sort context timing")
+    ap.add_argument("--no-batched-served", dest="batched_served", action="store_false",
+                    help="default workload: skip the batched and served comparisons added to the line")
     ap.add_argument("--rates", default="", help="served: comma-separated arrival rates per second")
     ap.add_argument("--no-bucket-sweep", dest="bucket_sweep", action="store_false",
                     help="served: skip the second sweep with half the requests bucket sorts")
@@ -718,6 +720,17 @@ def run_ours(args):
                "sample": f"one oracle sort of {n_sample} keys of the same workload ({secs:.1f} s), "
                          f"single thread of {os.cpu_count()} host cores"}
 
+    # the metric's second half: batched and served sorts against plain ones
+    # (one GPU; every rank would measure the same thing again)
+    batched = served = None
+    if args.batched_served and wl == "radix_u32_100m" and world == 1 and not args.n:
+        del ws, hbufs, houts, houtv, d_keys, d_out, d_vals, d_outv
+        torch.cuda.empty_cache()
+        batched = batched_summary(dev, steps=max(3, min(args.steps, 5)), warmup=3)
+        torch.cuda.empty_cache()
+        served = served_summary(dev, rates=SUMMARY_RATES, count=1000)
+        torch.cuda.empty_cache()
+
     line = {
         "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -738,11 +751,245 @@ def run_ours(args):
                 "link": dict(link, bound_value=link_bound(n, h2d, d2h, ms / args.steps, link),
                              note="bound_value: the pipelined ceiling set by the sort time and the host link's "
                                   "measured copy rates on these pinned buffers")},
-        "cpu_baseline": cpu, "context": lib,
+        "cpu_baseline": cpu, "context": lib, "batched": batched, "served": served,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------ batched and served, for the default line
+SUMMARY_RATES = (2_000, 5_000, 20_000)
+
+
+def batched_summary(dev, steps=5, warmup=3):
+    """The batched workload (20,000 uint32 arrays, sizes log-uniform in
+    [256, 2,000,000], seed 0, ~4.4e9 keys) sorted by one CUDA-graph launch of
+    the segmented sort (autotuned pass shape) against one rs_sort_u32 call
+    per array on the same stream.  Latency of an array: from the moment all
+    arrays are handed over to its completion (plain: the event after its own
+    sort; batched: the end of the graph)."""
+    import numpy as np
+    import torch
+
+    import paper_1206_3511_gb300 as rs
+
+    count = WORKLOADS["batched_u32_20k"][3]
+    sizes, off, d_keys = batched_inputs(count, 0, dev)
+    n_total = int(off[-1])
+    d_out = torch.empty_like(d_keys)
+    d_off = torch.from_numpy(off.view(np.int64)).to(dev)
+    stream = torch.cuda.current_stream()
+    plan = rs.Plan(rs.RS_PLAN_SEGMENTED, d_keys, d_out, seg_offsets=d_off, autotune=True)
+    seg_shape, graph_kernels, _ = plan.info()
+    for _ in range(warmup):
+        plan.launch(stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.launch(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / steps
+    if rs.get_status(plan.ws):
+        raise rs.SortError(rs.get_status(plan.ws), "batched device status")
+    for i in (0, count // 2, count - 1):  # spot check (the tests hold the oracle checks)
+        a, b = int(off[i]), int(off[i + 1])
+        assert np.array_equal(d_out[a:b].cpu().numpy().view(np.uint32),
+                              np.sort(d_keys[a:b].cpu().numpy().view(np.uint32))), f"batched array {i} wrong"
+    ws_plain = rs.workspace(rs.rs_workspace_bytes(rs.RS_ALGO_RADIX, 4, False, int(sizes.max()), 32, 0, 0), dev)
+    kp, op = d_keys.data_ptr(), d_out.data_ptr()
+    offs = [int(x) for x in off]
+
+    def plain_step(events=None):
+        for i in range(count):
+            a, b = offs[i], offs[i + 1]
+            rc = rs.rs_sort_u32(kp + 4 * a, op + 4 * a, None, None, b - a, 32, ws_plain, ws_plain.numel(), stream)
+            if rc:
+                raise rs.SortError(rc, "plain sort")
+            if events is not None:
+                events[i].record(stream)
+
+    plain_step()
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(count)]
+    plain_ms = []
+    for _ in range(2):
+        s0 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        plain_step(evs)
+        torch.cuda.synchronize()
+        plain_ms.append(s0.elapsed_time(evs[-1]))
+    plain_lat = [s0.elapsed_time(e) for e in evs]
+    clocks = sampler.stop()
+    plan.close()
+    del plan, d_keys, d_out, ws_plain
+    plain_t = float(np.median(plain_ms))
+    return {
+        "workload": WORKLOADS["batched_u32_20k"][6], "arrays": count, "keys": n_total,
+        "graph": {"gkeys_s": n_total / (graph_ms / 1e3) / 1e9, "ms_per_batch": graph_ms, "steps": steps,
+                  "p50_ms": graph_ms, "p99_ms": graph_ms, "kernel_nodes": graph_kernels,
+                  "pass_shape": {"block_threads": seg_shape[1], "items_per_thread": seg_shape[2]}},
+        "plain": {"gkeys_s": n_total / (plain_t / 1e3) / 1e9, "ms_per_batch": plain_t, "steps": len(plain_ms),
+                  "p50_ms": _pct(plain_lat, 50), "p99_ms": _pct(plain_lat, 99),
+                  "note": "one rs_sort_u32 call per array, in order, one stream, one workspace"},
+        "speedup": plain_t / graph_ms, "clocks": clocks,
+        "timing": "CUDA events on the launch stream; inputs (17.5 GB) larger than L2, no flush",
+    }
+
+
+def served_summary(dev, rates=SUMMARY_RATES, count=1000):
+    """The served mix (Poisson arrivals; sizes log-uniform in [1e3, 5e7]
+    keys; 70% uint32 keys only, 30% uint64 keys + uint32 values;
+    distributions 0-6 drawn per request; radix requests) through the sort
+    server (4 streams, continuous batching) against a plain loop that calls
+    rs_sort_u32/u64 once per request at its arrival, on one stream.  Latency:
+    scheduled arrival to completion seen on the host (the server's
+    completion record; for the plain loop, a host thread that waits on each
+    request's event in order).  Inputs are resident on the device before the
+    clock starts; the served keys per run are ~4.6e9."""
+    import numpy as np
+    import torch
+
+    import paper_1206_3511_gb300 as rs
+    import synth
+    from paper_1206_3511_gb300 import _lib
+
+    sizes, kinds, dists = synth.served_mix(count, SERVED_LO, SERVED_HI, seed=0)
+    big = int(sizes.max())
+    src_k = {}
+    for d in sorted(set(dists.tolist())):
+        if np.any((dists == d) & (kinds == 0)):
+            src_k[(0, d)] = synth.keys_u32_torch(big, d, seed=0, device=dev)
+        if np.any((dists == d) & (kinds == 1)):
+            src_k[(1, d)] = synth.keys_u64_shaped_torch(big, d, seed=0, device=dev)
+    src_v = torch.arange(big, dtype=torch.int32, device=dev)
+    ARENA = 60 * 10**9
+    arena = torch.empty(ARENA, dtype=torch.uint8, device=dev)
+    abase = arena.data_ptr()
+    out_off, out_end, lap = [], [], []
+    head, cur_lap = 0, 0
+    for i in range(count):
+        nb_out = (int(sizes[i]) * (4 if kinds[i] == 0 else 12) + 255) // 256 * 256
+        if head + nb_out > ARENA:
+            head, cur_lap = 0, cur_lap + 1
+        out_off.append(head)
+        out_end.append(head + nb_out)
+        lap.append(cur_lap)
+        head += nb_out
+    reqs = []
+    for i in range(count):
+        n, kd, d = int(sizes[i]), int(kinds[i]), int(dists[i])
+        kb = 4 if kd == 0 else 8
+        kin, kout = src_k[(kd, d)].data_ptr(), abase + out_off[i]
+        vin = src_v.data_ptr() if kd == 1 else None
+        vout = abase + out_off[i] + 8 * n if kd == 1 else None
+        reqs.append(_lib.RsRequest(rs.RS_ALGO_RADIX, kb, kin, kout, vin, vout, n, 8 * kb, 1, 0, 0))
+    total_keys = int(sizes.sum())
+
+    def must_wait_for(j, i):  # request j's output region is reused by request i
+        return lap[j] < lap[i] - 1 or (lap[j] == lap[i] - 1 and out_off[j] < out_end[i])
+
+    def run_server(rate, seed):
+        srv = rs.Server(SERVED_BUDGET, SERVED_BUDGET, num_streams=4, max_batch=64, device=dev)
+        arr = synth.poisson_arrivals(count, rate, seed=seed) * 1e3
+        tickets, oldest = [0] * count, 0
+        t0 = time.monotonic() * 1e3 + 2.0
+        for i in range(count):
+            while oldest < i and must_wait_for(oldest, i):
+                srv.wait(tickets[oldest])
+                oldest += 1
+            while time.monotonic() * 1e3 < t0 + arr[i]:
+                pass
+            rc, tickets[i] = _lib.rs_server_submit(srv.handle, reqs[i])
+            if rc:
+                raise rs.SortError(rc, "submit")
+        lat, done = [], []
+        for i in range(count):
+            rc = srv.wait(tickets[i])
+            if rc:
+                raise rs.SortError(rc, f"served request {i}")
+            _, r = srv.result(tickets[i])
+            done.append(r.t_done_ms)
+            lat.append(r.t_done_ms - (t0 + arr[i]))
+            srv.release(tickets[i])
+        st = srv.stats()
+        srv.close()
+        span = max(done) - t0
+        return {"p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "gkeys_s": total_keys / (span / 1e3) / 1e9,
+                "batches": int(st.batches), "batched_requests": int(st.batched_requests),
+                "max_queued": int(st.max_queued)}
+
+    ws_bytes = max(rs.rs_workspace_bytes(rs.RS_ALGO_RADIX, 4, False, big, 32, 0, 0),
+                   rs.rs_workspace_bytes(rs.RS_ALGO_RADIX, 8, True, big, 64, 0, 0))
+    ws = rs.workspace(ws_bytes, dev)
+    pstream = torch.cuda.Stream(device=dev)
+
+    def run_plain(rate, seed):
+        """One rs_sort_* call per request at its arrival, in order, on one
+        stream with one workspace; a host thread stamps each completion."""
+        arr = synth.poisson_arrivals(count, rate, seed=seed) * 1e3
+        evs = [torch.cuda.Event() for _ in range(count)]
+        issued = [threading.Event() for _ in range(count)]
+        done = [0.0] * count
+
+        def poll():
+            for i in range(count):
+                issued[i].wait()
+                while not evs[i].query():
+                    time.sleep(20e-6)
+                done[i] = time.monotonic() * 1e3
+
+        th = threading.Thread(target=poll)
+        th.start()
+        t0 = time.monotonic() * 1e3 + 2.0
+        for i in range(count):
+            q = reqs[i]
+            while time.monotonic() * 1e3 < t0 + arr[i]:
+                pass
+            fn = rs.rs_sort_u32 if q.key_bytes == 4 else rs.rs_sort_u64
+            rc = fn(q.keys_in, q.keys_out, q.vals_in, q.vals_out, q.n, q.key_bits, ws, ws_bytes, pstream)
+            if rc:
+                raise rs.SortError(rc, f"plain request {i}")
+            evs[i].record(pstream)
+            issued[i].set()
+        th.join()
+        lat = [done[i] - (t0 + arr[i]) for i in range(count)]
+        span = max(done) - t0
+        return {"p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "gkeys_s": total_keys / (span / 1e3) / 1e9}
+
+    run_server(1e6, 99)  # warm-up
+    run_plain(1e6, 99)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    rows = []
+    for j, rate in enumerate(rates):
+        rows.append({"rate_per_s": rate, "server": run_server(rate, j), "plain": run_plain(rate, j)})
+    clocks = sampler.stop()
+    if rs.get_status(ws):
+        raise rs.SortError(rs.get_status(ws), "plain served device status")
+    # spot check: the last uint32 request below 2M keys whose region is not reused
+    for i in range(count - 1, -1, -1):
+        n, kd, d = int(sizes[i]), int(kinds[i]), int(dists[i])
+        if kd != 0 or n > 2_000_000 or any(out_off[j] < out_end[i] and out_off[i] < out_end[j]
+                                           for j in range(i + 1, count)):
+            continue
+        got = arena[out_off[i]: out_off[i] + 4 * n].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, np.sort(src_k[(0, d)][:n].cpu().numpy().view(np.uint32))), "served output wrong"
+        break
+    del arena, src_k, src_v, ws
+    return {
+        "workload": WORKLOADS["served_mix"][6].replace("vs a FIFO of one sort per request on one stream",
+                                                        "radix requests"),
+        "requests_per_rate": count, "keys_per_run": total_keys, "budget_bytes": SERVED_BUDGET,
+        "server": "rs_server: 4 streams, continuous batching of up to 64 requests of <= 262,144 keys",
+        "plain": "one rs_sort_u32/u64 call per request at its arrival, one stream, one workspace",
+        "rates": rows, "clocks": clocks,
+    }
 
 
 # ------------------------------------------------------------------ batched (segmented) workload

@@ -253,6 +253,38 @@ RS_API rs_status rs_sort_segmented_u32(const uint32_t* keys_in, uint32_t* keys_o
 RS_API rs_status rs_sort_segmented_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
                                        uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg,
                                        size_t n_total, int key_bits, void* ws, size_t ws_bytes, rs_stream_t stream);
+/* Segmented bucket sort: each segment [d_seg_offsets[s], d_seg_offsets[s+1])
+ * of the arrays is bucket-sorted on its own, as bs_sort_u32/u64 would sort it
+ * alone (Sec. 2.3, Algorithm 2, per segment; stable).  Segment s of n_s keys
+ * gets max(1, floor(n_s / keys_per_bucket)) buckets (keys_per_bucket 0 =
+ * 16, the n/16 rule of bs_sort_*; 1 gives the paper's n buckets) over the
+ * range [min_key, max_key] when min_key <= max_key (every key of every
+ * segment must lie in it; a key outside is reported as RS_ERR_KEY_RANGE), or
+ * over that segment's own smallest and largest key when min_key > max_key
+ * (found on the device).  Segments of up to 4096 keys are bucket-sorted whole
+ * inside one thread block; larger ones are partitioned by their bucket ids in
+ * two segmented one-sweep levels, every partition of up to 4096 keys is then
+ * sorted bucket by bucket in shared memory, and a partition still larger when
+ * the bucket bits run out (skewed keys) is radix-sorted on the key bits its
+ * buckets span.  Offsets follow rs_sort_segmented_u32's rules (DEVICE array
+ * of nseg+1 offsets, d_seg_offsets[nseg] <= n_total, errors reported on the
+ * device as RS_ERR_INVALID_ARG, no write outside the arrays).  The
+ * classification is done on the device: the call never waits for the GPU.
+ * Workspace: bs_segmented_workspace_bytes(key_bytes, has_values, n_total,
+ * nseg, keys_per_bucket), valid for any bounds.  In place is allowed.
+ * RS_ERR_INVALID_ARG (synchronous): mismatched value pointers, misaligned or
+ * overlapping arrays, keys_per_bucket > 2^30, a u32 max_key above 2^32 - 1.
+ */
+RS_API size_t bs_segmented_workspace_bytes(int key_bytes, int has_values, size_t n_total, size_t nseg,
+                                           size_t keys_per_bucket);
+RS_API rs_status bs_sort_segmented_u32(const uint32_t* keys_in, uint32_t* keys_out, const uint32_t* vals_in,
+                                       uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg,
+                                       size_t n_total, uint32_t min_key, uint32_t max_key, size_t keys_per_bucket,
+                                       void* ws, size_t ws_bytes, rs_stream_t stream);
+RS_API rs_status bs_sort_segmented_u64(const uint64_t* keys_in, uint64_t* keys_out, const uint32_t* vals_in,
+                                       uint32_t* vals_out, const uint64_t* d_seg_offsets, size_t nseg,
+                                       size_t n_total, uint64_t min_key, uint64_t max_key, size_t keys_per_bucket,
+                                       void* ws, size_t ws_bytes, rs_stream_t stream);
 /* Same with an explicit kernel shape for the scatter passes of the large
  * segments (NULL = default).  Every shape rs_config_get lists is compiled for
  * segmented passes at digit_bits = 8; another digit width or shape gives

@@ -14,7 +14,8 @@ bits are sorted as unsigned).  Values are 32-bit (uint32 or int32).
 from __future__ import annotations
 
 from . import _lib
-from ._lib import (rs_sort_segmented_u32_ex, rs_sort_segmented_u64_ex, rs_server_release, bs_bucket_counts_u32, bs_bucket_counts_u64, RS_KEY_FLOAT, RS_KEY_INT, RS_KEY_UINT, rs_sort_typed, RS_PLAN_BUCKET, RS_PLAN_RADIX, RS_PLAN_SEGMENTED, RsPlanDesc, rs_plan_create, rs_plan_destroy,
+from ._lib import (bs_segmented_workspace_bytes, bs_sort_segmented_u32, bs_sort_segmented_u64,
+                   rs_sort_segmented_u32_ex, rs_sort_segmented_u64_ex, rs_server_release, bs_bucket_counts_u32, bs_bucket_counts_u64, RS_KEY_FLOAT, RS_KEY_INT, RS_KEY_UINT, rs_sort_typed, RS_PLAN_BUCKET, RS_PLAN_RADIX, RS_PLAN_SEGMENTED, RsPlanDesc, rs_plan_create, rs_plan_destroy,
                    rs_plan_info, rs_plan_launch, RsRequest, RsResult, RsServerConfig, RsServerStats, rs_server_create, rs_server_destroy,
                    rs_server_get_stats, rs_server_poll, rs_server_submit, rs_server_wait, bs_sort_u32, bs_sort_u64, rs_segmented_workspace_bytes, rs_sort_segmented_u32, rs_sort_segmented_u64,
                    RS_ALGO_BUCKET, RS_ALGO_RADIX, STATUS, RsConfig, load, rs_config_count, rs_config_get,
@@ -40,7 +41,8 @@ __all__ = [
     "rs_server_poll", "rs_server_submit", "rs_server_wait", "rs_server_release", "rs_sort_segmented_u32_ex",
     "rs_sort_segmented_u64_ex", "rs_host_sort_bytes", "rs_sort_host_u32", "rs_sort_host_u64", "sort_host",
     "bs_sort_host_u32", "bs_sort_host_u64", "rs_segmented_host_bytes", "rs_sort_segmented_host_u32",
-    "rs_sort_segmented_host_u64",
+    "rs_sort_segmented_host_u64", "bs_segmented_workspace_bytes", "bs_sort_segmented_u32", "bs_sort_segmented_u64",
+    "segmented_bucket_sort",
 ]
 
 
@@ -229,6 +231,32 @@ def segmented_sort(keys, offsets, values=None, key_bits: int = 0, out=None, out_
         ws = workspace(rs_segmented_workspace_bytes(kb, values is not None, n, max(nseg, 1), key_bits), keys.device)
     fn = rs_sort_segmented_u32 if kb == 4 else rs_sort_segmented_u64
     check(fn(keys, out, values, out_values, offsets, nseg, n, key_bits, ws, ws.numel(), stream), "rs_sort_segmented")
+    return out, out_values
+
+
+def segmented_bucket_sort(keys, offsets, values=None, min_key=None, max_key=None, keys_per_bucket: int = 0, out=None,
+                          out_values=None, ws=None, stream=None):
+    """Bucket-sort every segment [offsets[s], offsets[s+1]) of a 1-D CUDA
+    tensor on its own (bs_sort_segmented_u32/u64).  min_key/max_key: bounds
+    declared for every segment (both None: each segment's own, found on the
+    device).  keys_per_bucket 0 means 16.  Returns (keys, values or None)."""
+    import torch
+
+    _check_tensor(keys, "keys")
+    _check_tensor(offsets, "offsets")
+    kb = key_bytes_of(keys)
+    n = keys.numel()
+    nseg = offsets.numel() - 1
+    out = torch.empty_like(keys) if out is None else out
+    if values is not None and out_values is None:
+        out_values = torch.empty_like(values)
+    if ws is None:
+        ws = workspace(bs_segmented_workspace_bytes(kb, values is not None, n, max(nseg, 1), keys_per_bucket),
+                       keys.device)
+    lo, hi = (1, 0) if min_key is None else (min_key, max_key)
+    fn = bs_sort_segmented_u32 if kb == 4 else bs_sort_segmented_u64
+    check(fn(keys, out, values, out_values, offsets, nseg, n, lo, hi, keys_per_bucket, ws, ws.numel(), stream),
+          "bs_sort_segmented")
     return out, out_values
 
 

@@ -91,6 +91,9 @@ SIGNATURES: dict[str, tuple] = {
     "rs_sort_segmented_u64": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P]),
     "rs_sort_segmented_u32_ex": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P, _c.POINTER(RsConfig)]),
     "rs_sort_segmented_u64_ex": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _I, _P, _SZ, _P, _c.POINTER(RsConfig)]),
+    "bs_segmented_workspace_bytes": (_SZ, [_I, _I, _SZ, _SZ, _SZ]),
+    "bs_sort_segmented_u32": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _U32, _U32, _SZ, _P, _SZ, _P]),
+    "bs_sort_segmented_u64": (_I, [_P, _P, _P, _P, _P, _SZ, _SZ, _U64, _U64, _SZ, _P, _SZ, _P]),
     "rs_sort_typed": (_I, [_I, _I, _I, _P, _P, _P, _P, _SZ, _P, _SZ, _P]),
     "bs_bucket_counts_u32": (_I, [_P, _SZ, _c.c_uint32, _c.c_uint32, _SZ, _P, _P, _SZ, _P]),
     "bs_bucket_counts_u64": (_I, [_P, _SZ, _c.c_uint64, _c.c_uint64, _SZ, _P, _P, _SZ, _P]),
@@ -288,6 +291,24 @@ def rs_sort_segmented_u64(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, n
                           stream=None) -> int:
     return _call("rs_sort_segmented_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out),
                  ptr(d_seg_offsets), nseg, n_total, key_bits, ptr(ws), ws_bytes, stream_handle(stream))
+
+
+def bs_segmented_workspace_bytes(key_bytes, has_values, n_total, nseg, keys_per_bucket) -> int:
+    return _call("bs_segmented_workspace_bytes", key_bytes, int(bool(has_values)), n_total, nseg, keys_per_bucket)
+
+
+def bs_sort_segmented_u32(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, min_key, max_key,
+                          keys_per_bucket, ws, ws_bytes, stream=None) -> int:
+    return _call("bs_sort_segmented_u32", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out),
+                 ptr(d_seg_offsets), nseg, n_total, min_key, max_key, keys_per_bucket, ptr(ws), ws_bytes,
+                 stream_handle(stream))
+
+
+def bs_sort_segmented_u64(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, min_key, max_key,
+                          keys_per_bucket, ws, ws_bytes, stream=None) -> int:
+    return _call("bs_sort_segmented_u64", ptr(keys_in), ptr(keys_out), ptr(vals_in), ptr(vals_out),
+                 ptr(d_seg_offsets), nseg, n_total, min_key, max_key, keys_per_bucket, ptr(ws), ws_bytes,
+                 stream_handle(stream))
 
 
 def rs_sort_segmented_u32_ex(keys_in, keys_out, vals_in, vals_out, d_seg_offsets, nseg, n_total, key_bits, ws,

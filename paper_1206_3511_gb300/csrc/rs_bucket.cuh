@@ -78,13 +78,44 @@ __device__ __forceinline__ BucketParams load_bucket_params(const BucketParams* p
     return b;
 }
 
-// Digit of the bucket id for a scatter pass: (b(k) >> shift) & mask.
+// Position (shift) and width (bits) of the bucket-id digit that partition
+// level 1 or 2 sorts by, for a bucket id of bbits bits: level 1 takes the top
+// min(8, bbits) bits, level 2 the next min(8, what is left) bits.
+__host__ __device__ __forceinline__ void bucket_level_digit(uint32_t bbits, int level, int* shift, int* bits) {
+    const int d1 = bbits < 8u ? (int)bbits : 8;
+    const int s1 = (int)bbits - d1;
+    if (level <= 1) {
+        *shift = s1;
+        *bits = d1;
+    } else {
+        const int d2 = s1 < 8 ? s1 : 8;
+        *shift = s1 - d2;
+        *bits = d2;
+    }
+}
+
+// Digit of the bucket id for a scatter pass: (b(k) >> shift) & mask.  With a
+// table (the segmented bucket sort), every segment has its own parameters
+// (table[SegDesc::grp]) and the digit is that of partition level `level` for
+// the segment's bucket-id width; for_segment selects them per tile.
 struct BucketDigit {
     const BucketParams* src;
     int shift;
     uint32_t mask;
     BucketParams bp;
-    __device__ __forceinline__ void init() { bp = load_bucket_params(src); }
+    const BucketParams* table = nullptr;
+    int level = 0;
+    __device__ __forceinline__ void init() {
+        if (!table) bp = load_bucket_params(src);
+    }
+    template <typename Seg>
+    __device__ __forceinline__ void for_segment(const Seg& s) {
+        if (!table) return;
+        bp = load_bucket_params(table + s.grp);
+        int bits;
+        bucket_level_digit(bp.bbits, level, &shift, &bits);
+        mask = (1u << bits) - 1u;
+    }
     template <typename KeyT>
     __device__ __forceinline__ uint32_t operator()(KeyT k) const {
         return (uint32_t)(bucket_of(bp, k) >> shift) & mask;
@@ -96,27 +127,59 @@ struct BucketDigit {
     }
 };
 
-// The same digit for the counting kernels (only pass q = 0 exists).
+// The same digit for the counting kernels (only pass q = 0 exists).  With
+// check_range, keys outside the segment's [min, max] are reported (declared
+// bounds of the segmented bucket sort).
 struct BucketDigits {
     const BucketParams* src;
     int shift;
     uint32_t mask;
     BucketParams bp;
-    __device__ __forceinline__ void init() { bp = load_bucket_params(src); }
+    const BucketParams* table = nullptr;
+    int level = 0;
+    int check_range = 0;
+    __device__ __forceinline__ void init() {
+        if (!table) bp = load_bucket_params(src);
+    }
+    template <typename Seg>
+    __device__ __forceinline__ void for_segment(const Seg& s) {
+        if (!table) return;
+        bp = load_bucket_params(table + s.grp);
+        int bits;
+        bucket_level_digit(bp.bbits, level, &shift, &bits);
+        mask = (1u << bits) - 1u;
+    }
     template <typename KeyT>
     __device__ __forceinline__ uint32_t operator()(KeyT k, int) const {
         return (uint32_t)(bucket_of(bp, k) >> shift) & mask;
+    }
+    template <typename KeyT>
+    __device__ __forceinline__ bool in_range(KeyT k) const {
+        return !check_range || ((uint64_t)k >= bp.min && (uint64_t)k <= bp.max);
     }
 };
 
 // Bucket view for the shared-memory sort of one partition: the partition's
 // first bucket is kept in SegDesc::aux and the number of buckets it spans in
 // SegDesc::chunk0 (unused for shared-memory segments).
+// With a table (the segmented bucket sort), each segment's parameters are
+// table[SegDesc::grp], and with check_range its keys must lie in [min, max].
 struct SegBucketFn {
     const BucketParams* src;
     BucketParams bp;
-    __device__ __forceinline__ bool active() const { return src != nullptr; }
-    __device__ __forceinline__ void init() { bp = load_bucket_params(src); }
+    const BucketParams* table = nullptr;
+    int check_range = 0;
+    __device__ __forceinline__ bool active() const { return src != nullptr || table != nullptr; }
+    __device__ __forceinline__ void init() {
+        if (!table) bp = load_bucket_params(src);
+    }
+    __device__ __forceinline__ void for_segment(const SegDesc& s) {
+        if (table) bp = load_bucket_params(table + s.grp);
+    }
+    template <typename KeyT>
+    __device__ __forceinline__ bool in_range(KeyT k) const {
+        return !check_range || ((uint64_t)k >= bp.min && (uint64_t)k <= bp.max);
+    }
     __device__ __forceinline__ uint64_t first_bucket(const SegDesc& s) const { return s.aux; }
     __device__ __forceinline__ uint64_t bucket_span(const SegDesc& s) const { return s.chunk0; }
     template <typename KeyT>

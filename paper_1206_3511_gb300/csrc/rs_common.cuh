@@ -82,6 +82,12 @@ __device__ __forceinline__ void st_shared_v2_if(uint32_t addr, uint32_t x, uint3
         : "memory");
 }
 
+__device__ __forceinline__ void st_shared_u32_if(uint32_t addr, uint32_t v, bool pred) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.u32 p, %2, 0; @p st.shared.u32 [%0], %1; }" ::"r"(addr), "r"(v), "r"((uint32_t)pred)
+        : "memory");
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -10,8 +10,9 @@
 //  k_onesweep: one stable counting-sort pass (the placement loop of Algorithm
 //    3) done block-wise, in the manner of Onesweep (Adinets & Merrill,
 //    arXiv:2206.01784): each block takes the next tile (dynamic tile id),
-//    ranks its keys stably by digit inside each warp (lane masks built with
-//    shared-memory atomic OR in a per-warp table, see warp_rank), obtains the
+//    ranks its keys stably by digit inside each half-warp (lane masks built
+//    with shared-memory atomic OR in a per-half-warp table of packed mask and
+//    count words, see subwarp_rank), obtains the
 //    number of equal digits in all earlier tiles through a decoupled
 //    look-back over per-(tile, digit) status words, and writes each key to
 //    digit_base[d] + (earlier tiles' d) + (rank inside the tile).  The keys
@@ -29,6 +30,8 @@ struct RadixDigit {
     int shift;
     uint32_t mask;
     __device__ __forceinline__ void init() {}
+    template <typename Seg>
+    __device__ __forceinline__ void for_segment(const Seg&) {}
     template <typename KeyT>
     __device__ __forceinline__ uint32_t operator()(KeyT k) const {
         return (uint32_t)(k >> shift) & mask;
@@ -80,6 +83,8 @@ struct RadixDigits {
     uint32_t mask;
     int key_bits;
     __device__ __forceinline__ void init() {}
+    template <typename Seg>
+    __device__ __forceinline__ void for_segment(const Seg&) {}
     template <typename KeyT>
     __device__ __forceinline__ uint32_t operator()(KeyT x, int q) const {
         return (uint32_t)(x >> (shift0 + q * digit_bits)) & mask;
@@ -288,14 +293,20 @@ struct PassParams {
     int xf_in, xf_out;           // stored keys back (xf_out); both 0 for unsigned keys
 };
 
+// Rank tables of a scatter-pass block: one per half-warp ("sub"), each of
+// bins + kSubPad 32-bit words (the pad staggers the tables across banks).
+constexpr uint32_t kSubPad = 4;
+
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS>
 struct OnesweepShape {
     static constexpr int kWarps = BLOCK / 32;
+    static constexpr int kSubs = BLOCK / 16;
     static constexpr int kTile = BLOCK * ITEMS;
     static_assert(kTile < 65536, "tile offsets are 16-bit");
+    static_assert(16 * ITEMS < 65536, "a half-warp's digit count is 16-bit");
     static size_t smem_bytes(int digit_bits) {
         const size_t bins = (size_t)1 << digit_bits;
-        size_t b = (size_t)kWarps * bins * 8;  // per-warp rank table (64-bit entries)
+        size_t b = (size_t)kSubs * (bins + kSubPad) * 4;  // per-half-warp rank tables
         b += (size_t)kTile * sizeof(KeyT);     // staged keys
         if (VALS) b += (size_t)kTile * 4;      // staged values
         b += bins * 4 * 2;                     // local starts, scatter deltas
@@ -303,6 +314,33 @@ struct OnesweepShape {
         return b;
     }
 };
+
+// Stable rank of one key among the keys of its half-warp that carry the
+// same digit, in the half-warp's order (items in order, lanes in order within
+// an item).  Entry d of the half-warp's table (one 32-bit word at tab + 4d):
+// low 16 bits = peer mask of the item being ranked, one bit per lane of the
+// half-warp (built with shared atomic OR, so the mask does not depend on the
+// order in which the hardware applies the ORs), high 16 bits = number of keys
+// with digit d in the half-warp's earlier items.  The highest lane of each
+// peer group advances the count and clears the mask with one store.  One
+// word per entry spreads the 32 lanes' accesses over all 32 banks, and the
+// count comes with the mask in the same load.
+template <bool ALL>
+__device__ __forceinline__ uint32_t subwarp_rank(uint32_t tab, uint32_t d, bool ok, uint32_t hbit, uint32_t hlt,
+                                                 uint32_t hgt) {
+    const uint32_t addr = tab + 4u * d;
+    if (ALL)
+        asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(addr), "r"(hbit) : "memory");
+    else
+        red_or_shared_if(addr, hbit, ok);
+    __syncwarp();
+    const uint32_t e = ld_shared_u32(addr);
+    __syncwarp();
+    const uint32_t peers = (ALL || ok) ? (e & 0xffffu) : 0u;
+    st_shared_u32_if(addr, ((e >> 16) + __popc(peers)) << 16, (ALL || ok) && (peers & hgt) == 0);
+    __syncwarp();
+    return (e >> 16) + __popc(peers & hlt);
+}
 
 // Stable rank of one key among the keys of its warp that carry the same
 // digit, in warp order (items in order, lanes in order within an item).
@@ -379,7 +417,8 @@ __device__ __forceinline__ uint32_t lookback_digit(const uint32_t* status, uint3
 // Shared-memory layout of one scatter-pass block.
 template <typename KeyT>
 struct PassSmem {
-    unsigned long long* tab;  // [warps][bins] rank table, later warp offsets (low words)
+    uint32_t* tab;            // [subs][bins + kSubPad] rank tables, later each sub's offset per digit
+    uint32_t tab_stride;      // words per sub table
     KeyT* keys;               // [tile] staged keys
     uint32_t* vals;           // [tile] staged values
     uint32_t* local;          // [bins] start of each digit inside the staged tile
@@ -390,8 +429,9 @@ struct PassSmem {
 template <typename KeyT, bool VALS, int BLOCK>
 __device__ __forceinline__ PassSmem<KeyT> carve_pass_smem(unsigned char* smem, uint32_t bins, int tile_keys) {
     PassSmem<KeyT> sm;
-    sm.tab = reinterpret_cast<unsigned long long*>(smem);
-    sm.keys = reinterpret_cast<KeyT*>(sm.tab + (size_t)(BLOCK / 32) * bins);
+    sm.tab = reinterpret_cast<uint32_t*>(smem);
+    sm.tab_stride = bins + kSubPad;
+    sm.keys = reinterpret_cast<KeyT*>(sm.tab + (size_t)(BLOCK / 16) * sm.tab_stride);
     sm.vals = reinterpret_cast<uint32_t*>(sm.keys + tile_keys);
     sm.local = sm.vals + (VALS ? tile_keys : 0);
     sm.delta = sm.local + bins;
@@ -441,19 +481,22 @@ template <typename KeyT, bool VALS, int BLOCK, int ITEMS, bool FULL, typename Di
 __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, const DigitOp& op,
                                               const PassSmem<KeyT>& sm, const TileCtx<KeyT>& c, uint32_t bins,
                                               bool publish) {
-    constexpr int kWarps = BLOCK / 32;
+    constexpr int kSubs = BLOCK / 16;
     constexpr int kTile = BLOCK * ITEMS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int half = lane >> 4, hl = lane & 15;
     const bool first = c.tile == c.first_tile;
 
-    // load: warp w owns keys [w*ITEMS*32, (w+1)*ITEMS*32) of the tile, lane l
-    // holds item i = key w*ITEMS*32 + i*32 + l (warp-striped, coalesced)
-    const uint32_t wofs = (uint32_t)warp * (ITEMS * 32) + lane;
+    // load: half-warp h of warp w (sub 2w + h) owns the 16*ITEMS keys from
+    // (2w + h)*16*ITEMS of the tile; its lane l holds item i = key
+    // (2w + h)*16*ITEMS + i*16 + l.  Every load instruction of a warp reads
+    // two runs of 16 consecutive keys, one per half.
+    const uint32_t hofs = (uint32_t)warp * (ITEMS * 32) + (uint32_t)half * (ITEMS * 16) + hl;
     KeyT k[ITEMS];
     uint32_t v[VALS ? ITEMS : 1];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t idx = wofs + i * 32;
+        const uint32_t idx = hofs + i * 16;
         const bool ok = FULL || idx < c.tile_n;
         k[i] = ok ? c.kin[idx] : c.key_lo;
         if (VALS) v[i] = ok ? c.vin[idx] : 0u;
@@ -463,18 +506,19 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
         for (int i = 0; i < ITEMS; ++i) k[i] = p.xf.to_ordered(k[i]);
     }
 
-    // rank every key inside its warp; keep (digit << 16 | rank) per item
-    const uint32_t tab = smem_addr(sm.tab + (size_t)warp * bins);
-    const uint32_t lt = lanemask_lt();
-    const uint32_t lanebit = 1u << lane;
-    const uint32_t gt = ~(lt | lanebit);
+    // rank every key inside its half-warp; keep (digit << 16 | rank) per item
+    const uint32_t tab = smem_addr(sm.tab + (size_t)(2 * warp + half) * sm.tab_stride);
+    const uint32_t hbit = 1u << hl;
+    const uint32_t hlt = hbit - 1u;
+    const uint32_t hgt = 0xffffu & ~(hlt | hbit);
     uint32_t dr[ITEMS];
     // A warp whose keys all carry one digit (a run of sorted keys) needs no
-    // ranking: a key's rank is its position in the warp, and the warp's
-    // count of that digit is all its keys.  This spares the 32 atomics on
-    // one table word that such a warp would make per item.  Full tiles only;
-    // screened by the warp's first and last keys, then decided on the
-    // warp's smallest and largest keys.
+    // ranking: a key's rank is its position in its half-warp, and each
+    // half-warp's count of that digit is all its keys.  This spares the
+    // atomics on one table word that such a warp would make per item.  Full
+    // tiles only; screened by the warp's first and last keys (lane 0's first
+    // item and lane 31's last), then decided on the warp's smallest and
+    // largest keys.
     bool uniform = false;
     if (FULL) {
         const KeyT first = __shfl_sync(0xffffffffu, k[0], 0);
@@ -492,14 +536,14 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     if (uniform) {
         const uint32_t d0 = op((KeyT)(k[0] - c.key_lo));
 #pragma unroll
-        for (int i = 0; i < ITEMS; ++i) dr[i] = (d0 << 16) | (uint32_t)(i * 32 + lane);
-        st_shared_v2_if(tab + 8u * d0, 0u, (uint32_t)(ITEMS * 32), lane == 0);
+        for (int i = 0; i < ITEMS; ++i) dr[i] = (d0 << 16) | (uint32_t)(i * 16 + hl);
+        st_shared_u32_if(tab + 4u * d0, (uint32_t)(ITEMS * 16) << 16, hl == 0);
     } else {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
-            const bool ok = FULL || (wofs + i * 32) < c.tile_n;
+            const bool ok = FULL || (hofs + i * 16) < c.tile_n;
             const uint32_t d = op((KeyT)(k[i] - c.key_lo));
-            dr[i] = (d << 16) | warp_rank<FULL>(tab, d, ok, lanebit, lt, gt);
+            dr[i] = (d << 16) | subwarp_rank<FULL>(tab, d, ok, hbit, hlt, hgt);
         }
     }
     __syncthreads();
@@ -510,7 +554,7 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     for (uint32_t d = tid; d < bins; d += BLOCK) {
         uint32_t sum = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) sum += (uint32_t)(sm.tab[(size_t)w * bins + d] >> 32);
+        for (int s = 0; s < kSubs; ++s) sum += sm.tab[(size_t)s * sm.tab_stride + d] >> 16;
         sm.local[d] = sum;
         if (publish) st_relaxed(srow + d, (first ? kFlagPrefix : kFlagAggregate) | sum);
     }
@@ -522,17 +566,17 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     }
     __syncthreads();
 
-    // each digit's start inside the staged tile, and each warp's offset
-    // inside that digit (kept in the low word of the rank table)
+    // each digit's start inside the staged tile, and each half-warp's offset
+    // inside that digit (it replaces the rank-table entry)
     block_exclusive_scan_smem<BLOCK>(sm.local, (int)bins, sm.scan);
     for (uint32_t d = tid; d < bins; d += BLOCK) {
         uint32_t run = sm.local[d];
         sm.delta[d] -= run;
-        uint32_t* low = reinterpret_cast<uint32_t*>(sm.tab + d);
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t cnt = low[2 * (size_t)w * bins + 1];
-            low[2 * (size_t)w * bins] = run;
+        for (int s = 0; s < kSubs; ++s) {
+            uint32_t* e = sm.tab + (size_t)s * sm.tab_stride + d;
+            const uint32_t cnt = *e >> 16;
+            *e = run;
             run += cnt;
         }
     }
@@ -541,9 +585,9 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     // stage the tile in shared memory in digit order
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const bool ok = FULL || (wofs + i * 32) < c.tile_n;
+        const bool ok = FULL || (hofs + i * 16) < c.tile_n;
         if (ok) {
-            const uint32_t pos = ld_shared_u32(tab + 8u * (dr[i] >> 16)) + (dr[i] & 0xffffu);
+            const uint32_t pos = ld_shared_u32(tab + 4u * (dr[i] >> 16)) + (dr[i] & 0xffffu);
             if (pos < (uint32_t)kTile) {
                 sm.keys[pos] = k[i];
                 if (VALS) sm.vals[pos] = v[i];
@@ -624,7 +668,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p)
     }
     __syncthreads();  // s_tile is reused for the tile ids below
     while (true) {
-        for (uint32_t i = tid; i < (uint32_t)(BLOCK / 32) * bins; i += BLOCK) sm.tab[i] = 0ull;
+        for (uint32_t i = tid; i < (uint32_t)(BLOCK / 16) * sm.tab_stride; i += BLOCK) sm.tab[i] = 0u;
         if (tid == 0) s_tile = atomicAdd(p.tile_ctr, 1u);
         __syncthreads();
         const uint32_t tile = s_tile;

@@ -49,15 +49,21 @@ constexpr Variant make_variant() {
 }
 
 // Compiled kernel shapes.  The first entry of each (key width, values) group
-// is the default (the fastest measured on GB300 at 100M keys); only the
-// defaults are also compiled for typed keys.
+// is the default (the fastest measured on GB300 at 100M keys with the
+// half-warp rank tables: u32 keys only 256 x 22, 1.84 ms per sort against
+// 1.93 for 256 x 20 and 1.96 for 384 x 16; u32 with values 256 x 15, 2.78 ms
+// against 3.05 for 256 x 12); only the defaults are also compiled for typed
+// keys.
 const Variant kVariants[] = {
-    make_variant<uint32_t, false, 384, 16, 3, true>(),
+    make_variant<uint32_t, false, 256, 22, 4, true>(),
+    make_variant<uint32_t, false, 384, 16, 3>(),
+    make_variant<uint32_t, false, 256, 20, 4>(),
+    make_variant<uint32_t, false, 256, 24, 4>(),
     make_variant<uint32_t, false, 256, 18, 4>(),
     make_variant<uint32_t, false, 256, 15, 4>(),
     make_variant<uint32_t, false, 512, 15, 2>(),
-    make_variant<uint32_t, true, 256, 12, 4, true>(),
-    make_variant<uint32_t, true, 256, 15, 3>(),
+    make_variant<uint32_t, true, 256, 15, 3, true>(),
+    make_variant<uint32_t, true, 256, 12, 4>(),
     // u64 defaults: 384 x 12 keys only (5.59 ms at 100M 64-bit keys against
     // 5.77 for 256 x 12), 384 x 10 with values (7.35 ms against 8.02)
     make_variant<uint64_t, false, 384, 12, 3, true>(),

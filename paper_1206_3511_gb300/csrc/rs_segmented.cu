@@ -54,7 +54,9 @@ constexpr SegVariant seg_variant() {
 
 // The first entry of each (key width, values) group is SegShape's.
 const SegVariant kSegVariants[] = {
-    seg_variant<uint32_t, false, 384, 16, 3>(), seg_variant<uint32_t, false, 256, 18, 4>(),
+    seg_variant<uint32_t, false, 384, 16, 3>(), seg_variant<uint32_t, false, 256, 22, 4>(),
+    seg_variant<uint32_t, false, 256, 20, 4>(), seg_variant<uint32_t, false, 256, 24, 4>(),
+    seg_variant<uint32_t, false, 256, 18, 4>(),
     seg_variant<uint32_t, false, 256, 15, 4>(), seg_variant<uint32_t, false, 512, 15, 2>(),
     seg_variant<uint32_t, true, 256, 12, 4>(),  seg_variant<uint32_t, true, 256, 15, 3>(),
     seg_variant<uint64_t, false, 256, 12, 4>(), seg_variant<uint64_t, false, 256, 9, 4>(),
@@ -235,12 +237,15 @@ rs_status enqueue_large_passes(int key_bytes, bool vals, const void* src_k, cons
 
 rs_status enqueue_local_sorts(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,
                               uint32_t* out_v, const SegDesc* segs, const uint32_t* count, size_t max_count,
-                              const void* bucket, WsHeader* range_hdr, cudaStream_t stream) {
-    LocalParams lp{src_k, out_k, src_v, out_v, segs, count, bucket, SegDesc{}, range_hdr, KeyXform{}};
+                              const void* bucket, WsHeader* range_hdr, cudaStream_t stream, const void* bucket_table,
+                              int check_range) {
+    LocalParams lp{src_k, out_k, src_v, out_v, segs, count, bucket ? bucket : bucket_table, SegDesc{}, range_hdr,
+                   KeyXform{}};
     const size_t grid = max_count ? max_count : 1;
     cudaError_t e;
-    if (bucket) {
-        SegBucketFn f{static_cast<const BucketParams*>(bucket), {}};
+    if (bucket || bucket_table) {
+        SegBucketFn f{static_cast<const BucketParams*>(bucket), {}, static_cast<const BucketParams*>(bucket_table),
+                      check_range};
         if (key_bytes == 4)
             e = vals ? launch_local<uint32_t, true>(lp, f, grid, stream)
                      : launch_local<uint32_t, false>(lp, f, grid, stream);

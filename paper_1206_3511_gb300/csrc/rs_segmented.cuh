@@ -19,8 +19,10 @@ struct SegDesc {
     uint32_t chunk0;  // first counting chunk
     uint32_t bits;    // key bits to sort on
     uint64_t aux;     // planner data (bucket range of bucket-sort partitions)
+    uint32_t grp;     // input segment the descriptor belongs to (segmented bucket sort: its bucket parameters)
+    uint32_t pad;
 };
-static_assert(sizeof(SegDesc) == 40, "SegDesc layout");
+static_assert(sizeof(SegDesc) == 48, "SegDesc layout");
 
 // Device-side totals of a plan (zeroed before planning).
 struct SegPlanHdr {
@@ -122,13 +124,30 @@ __global__ void __launch_bounds__(512) k_seg_counts(const KeyT* __restrict__ key
         const KeyT* kp = keys + d.start;
         const KeyT klo = (KeyT)d.key_lo;
         const bool check = range_hdr && d.bits < 8 * sizeof(KeyT);
+        dg.for_segment(d);
         bool bad = false;
-        for (uint32_t i = lo + tid; i < hi; i += blockDim.x) {
+        // eight keys per thread per step are loaded before any is counted, so
+        // that enough loads are in flight to cover the memory latency
+        constexpr uint32_t kU = 8;
+        uint32_t i = lo + tid;
+        for (; i + (kU - 1) * blockDim.x < hi; i += kU * blockDim.x) {
+            KeyT x[kU];
+#pragma unroll
+            for (uint32_t u = 0; u < kU; ++u) x[u] = (KeyT)(__ldcs(kp + i + u * blockDim.x) - klo);
+#pragma unroll
+            for (uint32_t u = 0; u < kU; ++u) {
+                bad |= check && (x[u] >> (check ? d.bits : 0)) != 0;
+                bad |= !dg.in_range(x[u]);
+                for (int q = 0; q < passes; ++q) atomicAdd(&s_cnt[q * bins + dg(x[u], q)], 1u);
+            }
+        }
+        for (; i < hi; i += blockDim.x) {
             const KeyT x = (KeyT)(__ldcs(kp + i) - klo);
             bad |= check && (x >> (check ? d.bits : 0)) != 0;
+            bad |= !dg.in_range(x);
             for (int q = 0; q < passes; ++q) atomicAdd(&s_cnt[q * bins + dg(x, q)], 1u);
         }
-        if (bad) set_device_error(range_hdr, RS_ERR_KEY_RANGE, li);
+        if (bad && range_hdr) set_device_error(range_hdr, RS_ERR_KEY_RANGE, li);
         __syncthreads();
         uint32_t* out = seg_counts + (size_t)li * ncnt;
         for (int i = tid; i < ncnt; i += blockDim.x)
@@ -176,7 +195,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep_seg(SegPassParams<Digi
     op.init();
     const int tid = threadIdx.x;
     while (true) {
-        for (uint32_t i = tid; i < (uint32_t)(BLOCK / 32) * bins; i += BLOCK) sm.tab[i] = 0ull;
+        for (uint32_t i = tid; i < (uint32_t)(BLOCK / 16) * sm.tab_stride; i += BLOCK) sm.tab[i] = 0u;
         if (tid == 0) s_tile = atomicAdd(p.tile_ctr, 1u);
         __syncthreads();
         const uint32_t g = s_tile;
@@ -185,6 +204,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep_seg(SegPassParams<Digi
             for (uint32_t d = tid; d < bins; d += BLOCK) p.status_next[(size_t)g * bins + d] = 0u;
         const uint32_t li = sp.tile_seg[g];
         const SegDesc seg = sp.segs[li];
+        op.for_segment(seg);  // digit parameters of this segment, if they differ per segment
         const uint32_t base = (g - seg.tile0) * (uint32_t)kTile;
         TileCtx<KeyT> c;
         c.kin = static_cast<const KeyT*>(p.keys_in) + seg.start + base;
@@ -332,6 +352,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
         const SegDesc seg = lp.count ? lp.segs[si] : lp.one;
         const uint32_t m = seg.n;
         const KeyT klo = (KeyT)seg.key_lo;
+        bfn.for_segment(seg);
         __syncthreads();
         const KeyT* kin = static_cast<const KeyT*>(lp.keys_in) + seg.start;
         bool bad = false;
@@ -341,6 +362,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
             kbuf[0][i] = k;
             if (VALS) vbuf[0][i] = lp.vals_in[seg.start + i];
             bad |= seg.bits < 8 * sizeof(KeyT) && ((KeyT)(k - klo) >> seg.bits) != 0;
+            bad |= !bfn.in_range(k);
         }
         if (bad && lp.hdr) set_device_error(lp.hdr, RS_ERR_KEY_RANGE, si);
         // keys already in nondecreasing order (a sorted run) are their own
@@ -593,6 +615,11 @@ __global__ void __launch_bounds__(256) k_tiny_sort(const KeyT* __restrict__ keys
 struct NoBucket {
     __device__ __forceinline__ bool active() const { return false; }
     __device__ __forceinline__ void init() {}
+    __device__ __forceinline__ void for_segment(const SegDesc&) {}
+    template <typename KeyT>
+    __device__ __forceinline__ bool in_range(KeyT) const {
+        return true;
+    }
     __device__ __forceinline__ uint64_t first_bucket(const SegDesc&) const { return 0; }
     __device__ __forceinline__ uint64_t bucket_span(const SegDesc&) const { return 0; }
     template <typename KeyT>

@@ -148,11 +148,15 @@ rs_status enqueue_large_passes_at(int key_bytes, bool vals, const void* src_k, c
 size_t bucket_workspace_bytes(int key_bytes, bool vals, size_t n, size_t nb);
 
 // Shared-memory sorts of a device list of segments (count on the device).
-// bucket: device BucketParams for bucket mode, or null.  range_hdr: non-null
-// to report keys at or above 2^bits (relative to the segment's key_lo).
+// bucket: device BucketParams for bucket mode, or null.  bucket_table: per
+// segment BucketParams indexed by SegDesc::grp (segmented bucket sort; takes
+// the place of bucket), with check_range keys outside each segment's [min,
+// max] reported.  range_hdr: non-null to report keys at or above 2^bits
+// (relative to the segment's key_lo) and, in bucket mode, keys out of range.
 rs_status enqueue_local_sorts(int key_bytes, bool vals, const void* src_k, const uint32_t* src_v, void* out_k,
                               uint32_t* out_v, const SegDesc* segs, const uint32_t* count, size_t max_count,
-                              const void* bucket, WsHeader* range_hdr, cudaStream_t stream);
+                              const void* bucket, WsHeader* range_hdr, cudaStream_t stream,
+                              const void* bucket_table = nullptr, int check_range = 0);
 
 // One array of at most kLocalCap keys sorted in shared memory by a single
 // block (a whole radix sort in one launch); keys >= 2^key_bits are reported
