@@ -348,10 +348,15 @@ RS_API void rs_plan_destroy(rs_plan* plan);
  * host thread; a dispatcher thread admits them, oldest first, while the
  * memory they need fits under budget_bytes, and keeps up to num_streams
  * launches in flight on separate streams so their work overlaps on the GPU.
- * Waiting radix requests of at most batch_max_keys keys with the same key
- * type, value presence and key_bits are packed, up to max_batch at a time,
- * into one segmented sort (their keys are gathered into the pool, sorted per
- * segment and copied back); other requests run as single sorts.  Each
+ * Waiting requests of at most batch_max_keys keys are packed, up to
+ * max_batch at a time, into one segmented sort (their keys are gathered into
+ * the pool, sorted per segment and copied back): radix requests with the same
+ * key type, value presence and key_bits through rs_sort_segmented_*, bucket
+ * requests with the same key type and value presence, the default bucket
+ * count (num_buckets 0 or max(1, n/16)) and the same declared bounds (or
+ * bounds computed for each) through bs_sort_segmented_*; other requests run
+ * as single sorts.  A bucket request of 4-byte keys with max_key above
+ * 2^32 - 1 (and min_key <= max_key) is refused with RS_ERR_INVALID_ARG.  Each
  * request's output is exactly what rs_sort_* / bs_sort_* would produce for
  * it alone.
  *

@@ -22,6 +22,7 @@ namespace rs {
 
 size_t segmented_workspace_bytes(int key_bytes, bool vals, size_t n_total, size_t nseg, int key_bits);
 size_t bucket_workspace_bytes(int key_bytes, bool vals, size_t n, size_t nb);
+size_t seg_bucket_workspace_bytes(int key_bytes, bool vals, size_t n_total, size_t nseg, size_t keys_per_bucket);
 
 namespace {
 
@@ -99,6 +100,30 @@ struct Slot {  // one launch in flight
     uint64_t* h_offsets = nullptr;  // pinned, max_batch + 1 entries
     uint32_t* h_status = nullptr;   // pinned: the device status word of the launch's workspace
 };
+
+// Bucket requests are batched when they use the default bucket count
+// (max(1, n / 16), what the segmented bucket sort gives every segment).
+bool default_buckets(const rs_request& r) {
+    return r.num_buckets == 0 || r.num_buckets == std::max<size_t>(1, r.n / 16);
+}
+
+// Requests that one segmented call can sort together: same algorithm, key
+// width, value presence, and key_bits (radix) or declared bounds (bucket:
+// the same [min, max], or bounds computed for each).
+bool batch_compatible(const rs_request& a, const rs_request& b) {
+    if (a.algo != b.algo || a.key_bytes != b.key_bytes || (a.vals_in != nullptr) != (b.vals_in != nullptr))
+        return false;
+    if (a.algo == RS_ALGO_RADIX) return a.key_bits == b.key_bits;
+    const bool ca = a.min_key > a.max_key, cb = b.min_key > b.max_key;
+    return default_buckets(a) && default_buckets(b) && (ca ? cb : (!cb && a.min_key == b.min_key &&
+                                                                   a.max_key == b.max_key));
+}
+
+size_t batch_ws_bytes(const rs_request& q0, size_t keys, size_t count) {
+    const bool vals = q0.vals_in != nullptr;
+    return q0.algo == RS_ALGO_BUCKET ? seg_bucket_workspace_bytes(q0.key_bytes, vals, keys, count, 16)
+                                     : segmented_workspace_bytes(q0.key_bytes, vals, keys, count, q0.key_bits);
+}
 
 size_t request_ws_bytes(const rs_request& r) {
     const bool vals = r.vals_in != nullptr;
@@ -191,15 +216,16 @@ bool ServerImpl::launch_single(Slot& s, Request& r) {
     return true;
 }
 
-// Small radix requests of one key type: keys (and values) are gathered into
-// one array, sorted by one segmented call and scattered back.
+// Small compatible requests (batch_compatible): keys (and values) are
+// gathered into one array, sorted by one segmented radix or bucket call and
+// scattered back.
 bool ServerImpl::launch_batch(Slot& s, std::vector<Request*>& batch, size_t footprint) {
     const rs_request& q0 = batch[0]->req;
     const int kb = q0.key_bytes;
     const bool vals = q0.vals_in != nullptr;
     size_t total = 0;
     for (Request* r : batch) total += r->req.n;
-    const size_t wsb = segmented_workspace_bytes(kb, vals, total, batch.size(), q0.key_bits);
+    const size_t wsb = batch_ws_bytes(q0, total, batch.size());
     const size_t kbytes = total * kb, vbytes = vals ? total * 4 : 0;
     void* ws = pool.alloc(wsb);
     void* kin = pool.alloc(kbytes);
@@ -234,7 +260,16 @@ bool ServerImpl::launch_batch(Slot& s, std::vector<Request*>& batch, size_t foot
     s.h_offsets[batch.size()] = off;
     ok &= cudaMemcpyAsync(doff, s.h_offsets, (batch.size() + 1) * 8, cudaMemcpyHostToDevice, s.stream) == cudaSuccess;
     rs_status st = RS_OK;
-    if (ok)
+    if (ok && q0.algo == RS_ALGO_BUCKET)
+        st = kb == 4 ? bs_sort_segmented_u32(static_cast<const uint32_t*>(kin), static_cast<uint32_t*>(kout),
+                                             static_cast<const uint32_t*>(vin), static_cast<uint32_t*>(vout),
+                                             static_cast<const uint64_t*>(doff), batch.size(), total,
+                                             (uint32_t)q0.min_key, (uint32_t)q0.max_key, 16, ws, wsb, s.stream)
+                     : bs_sort_segmented_u64(static_cast<const uint64_t*>(kin), static_cast<uint64_t*>(kout),
+                                             static_cast<const uint32_t*>(vin), static_cast<uint32_t*>(vout),
+                                             static_cast<const uint64_t*>(doff), batch.size(), total, q0.min_key,
+                                             q0.max_key, 16, ws, wsb, s.stream);
+    else if (ok)
         st = kb == 4 ? rs_sort_segmented_u32(static_cast<const uint32_t*>(kin), static_cast<uint32_t*>(kout),
                                              static_cast<const uint32_t*>(vin), static_cast<uint32_t*>(vout),
                                              static_cast<const uint64_t*>(doff), batch.size(), total, q0.key_bits,
@@ -271,10 +306,10 @@ bool ServerImpl::launch_batch(Slot& s, std::vector<Request*>& batch, size_t foot
 
 // Footprint of a batch: the requests' own inputs and outputs, the gathered
 // copies (input and output) and the segmented workspace.
-size_t batch_footprint(const std::vector<Request*>& batch, size_t own, size_t keys, int kb, bool vals, int key_bits) {
-    const size_t per_key = (size_t)kb + (vals ? 4 : 0);
-    return own + 2 * keys * per_key + segmented_workspace_bytes(kb, vals, keys, batch.size(), key_bits) +
-           (batch.size() + 1) * 8;
+size_t batch_footprint(const std::vector<Request*>& batch, size_t own, size_t keys) {
+    const rs_request& q0 = batch[0]->req;
+    const size_t per_key = (size_t)q0.key_bytes + (q0.vals_in != nullptr ? 4 : 0);
+    return own + 2 * keys * per_key + batch_ws_bytes(q0, keys, batch.size()) + (batch.size() + 1) * 8;
 }
 
 void ServerImpl::run() {
@@ -310,17 +345,15 @@ void ServerImpl::run() {
             const bool vals = q.vals_in != nullptr;
             std::vector<Request*> batch;
             size_t own = 0, keys = 0, bfp = 0;
-            if (q.algo == RS_ALGO_RADIX && q.n <= cfg.batch_max_keys && cfg.max_batch > 1) {
-                // gather waiting small requests of the same type, oldest first
+            if (q.n <= cfg.batch_max_keys && cfg.max_batch > 1 && batch_compatible(q, q)) {
+                // gather waiting small requests of the same kind, oldest first
                 for (auto it = pending.begin(); it != pending.end() && (int)batch.size() < cfg.max_batch; ++it) {
                     Request& r = reqs[*it];
                     const rs_request& x = r.req;
-                    if (x.algo != RS_ALGO_RADIX || x.n > cfg.batch_max_keys || x.key_bytes != q.key_bytes ||
-                        (x.vals_in != nullptr) != vals || x.key_bits != q.key_bits)
-                        continue;
+                    if (x.n > cfg.batch_max_keys || !batch_compatible(q, x)) continue;
                     const size_t own2 = own + 2 * x.n * ((size_t)x.key_bytes + (vals ? 4 : 0));
                     batch.push_back(&r);
-                    const size_t fp2 = batch_footprint(batch, own2, keys + x.n, q.key_bytes, vals, q.key_bits);
+                    const size_t fp2 = batch_footprint(batch, own2, keys + x.n);
                     if (in_use + fp2 > cfg.budget_bytes) {
                         batch.pop_back();
                         continue;
@@ -421,6 +454,12 @@ rs_status rs_server_submit(rs_server* s, const rs_request* req, uint64_t* ticket
         if (r.req.key_bits < 1 || r.req.key_bits > 8 * q.key_bytes) return RS_ERR_INVALID_ARG;
     } else {
         r.req.key_bits = 8 * q.key_bytes;
+        if (r.req.min_key > r.req.max_key) {  // bounds computed on the device: one marker for every key width
+            r.req.min_key = 1;
+            r.req.max_key = 0;
+        } else if (q.key_bytes == 4 && r.req.max_key > 0xffffffffull) {
+            return RS_ERR_INVALID_ARG;
+        }
     }
     const size_t ws = request_ws_bytes(r.req);
     if (ws == 0) return RS_ERR_INVALID_ARG;

@@ -238,3 +238,39 @@ def test_device_errors_reach_the_request(rs, algo, n):
                 assert_same(from_dev(ko, np.uint32), np.sort(k), "good request")
             else:
                 assert batched and c == 3
+
+
+def test_bucket_requests_are_batched(rs, oracle):
+    """Small bucket requests with the default bucket count are packed into
+    segmented bucket sorts (bs_sort_segmented_*): u32 keys with bounds found
+    on the device and u64 keys with values and declared bounds.  With one
+    stream, the requests that wait behind the first launch form batches.
+    Every result equals the oracle's bucket sort of the request alone."""
+    import torch
+
+    reqs = []
+    for i in range(40):
+        n = 2000 + 1777 * i
+        reqs.append((synth.keys_u32(n, i % 7, seed=300 + i), None, {}))
+    for i in range(12):
+        n = 3000 + 2500 * i
+        keys = synth.keys_u64(n, 40, seed=350 + i)
+        reqs.append((keys, synth.index_values(n), {"min_key": 0, "max_key": 2**40 - 1}))
+    with rs.Server(pool_bytes=2 << 30, num_streams=1, max_batch=16) as srv:
+        staged = []
+        for keys, vals, bounds in reqs:
+            kd = to_dev(keys)
+            vd = to_dev(vals) if vals is not None else None
+            staged.append((kd, torch.empty_like(kd), vd, torch.empty_like(vd) if vd is not None else None, bounds))
+        torch.cuda.synchronize()
+        handles = [(srv.submit(kd, ko, vd, vo, algo=rs.RS_ALGO_BUCKET, **b), ko, vo) for kd, ko, vd, vo, b in staged]
+        for (t, ko, vo), (keys, vals, bounds) in zip(handles, reqs):
+            assert srv.wait(t, 60_000) == 0
+            want = oracle.bucket_sort(keys, vals, bounds.get("min_key"), bounds.get("max_key"))
+            if vals is None:
+                assert_same(from_dev(ko, keys.dtype), want, f"bucket ticket {t}")
+            else:
+                assert_same(from_dev(ko, keys.dtype), want[0], f"bucket ticket {t} keys")
+                assert_same(from_dev(vo, np.uint32), want[1], f"bucket ticket {t} values")
+        st = srv.stats()
+        assert st.batches >= 2 and st.batched_requests >= 10
