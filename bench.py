@@ -53,6 +53,9 @@ for _d in range(7):
     WORKLOADS[f"bucket_u32_{_name}_100m"] = ("bucket", 4, False, 100_000_000, 32, _d,
                                             f"bucket sort, 100M uint32 keys, distribution {_d}, declared bounds, "
                                             f"n/16 buckets")
+WORKLOADS["bucket_u64_uniform_100m"] = ("bucket", 8, False, 100_000_000, 64, 20,
+                                        "bucket sort, 100M uint64 keys uniform [0,2^64), bounds computed on the "
+                                        "device (min and max of the keys), n/16 buckets")
 WORKLOADS["bucket_u32_1m"] = ("bucket", 4, False, 1_000_000, 31, 10,
                               "bucket sort, 1M uint32 keys uniform [0,2^31), 62,500 buckets over [0,2^31-1]")
 WORKLOADS["radix_u32_1m"] = ("radix", 4, False, 1_000_000, 32, 10,
@@ -196,13 +199,14 @@ def pass_bytes(n, key_bytes, has_values) -> int:
     return 2 * n * (key_bytes + (4 if has_values else 0))
 
 
-def sort_bytes(algo, n, key_bytes, has_values, key_bits=0, digit_bits=8) -> int:
+def sort_bytes(algo, n, key_bytes, has_values, key_bits=0, digit_bits=8, bounds_computed=False) -> int:
     """Algorithmic HBM bytes of one whole sort.  Radix: one read of the keys
     to count every digit, then one read and one write of keys (and values)
     per pass.  Bucket: one read to count, then a read and a write to scatter
-    into buckets and another to sort the buckets."""
+    into buckets and another to sort the buckets, plus one read of the keys
+    for their min and max when the bounds are not declared."""
     if algo == "bucket":
-        return n * key_bytes + 2 * pass_bytes(n, key_bytes, has_values)
+        return (2 if bounds_computed else 1) * n * key_bytes + 2 * pass_bytes(n, key_bytes, has_values)
     passes = -(-(key_bits or 8 * key_bytes) // digit_bits)
     return n * key_bytes + passes * pass_bytes(n, key_bytes, has_values)
 
@@ -388,9 +392,12 @@ def make_keys(wl, n, seed=0):
 
 
 def bucket_bounds(wl):
+    """Declared (min, max) of a bucket workload; (1, 0) = computed on the device."""
     import synth
 
-    dist = WORKLOADS[wl][5]
+    kb, dist = WORKLOADS[wl][1], WORKLOADS[wl][5]
+    if kb == 8:
+        return 1, 0
     if dist == 10:
         return 0, 2**31 - 1
     return synth.DECLARED_BOUNDS[dist]
@@ -407,6 +414,8 @@ def cpu_oracle_rate(wl, n_sample, keys=None, vals=None) -> tuple[float, float]:
     t0 = time.perf_counter()
     if algo == "bucket":
         lo, hi = bucket_bounds(wl)
+        if lo > hi:  # bounds computed from the keys
+            lo = hi = None
         oracle.bucket_sort(keys, vals, lo, hi, max(1, keys.size // 16))
     else:
         oracle.radix_sort(keys, vals, key_bits, 8)
@@ -679,7 +688,8 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": step_bytes / per_step_launches,
                     "avg_launch_ms": tot / nl, "launches": nl,
                     "timing": f"CUDA events around every launch over a repeat of the {prof_steps} timed steps"}
-    whole_bytes = sort_bytes(algo, n, kb, has_v, key_bits, tuned[0] if (tuned and algo == "radix") else 8)
+    whole_bytes = sort_bytes(algo, n, kb, has_v, key_bits, tuned[0] if (tuned and algo == "radix") else 8,
+                             bounds_computed=algo == "bucket" and lo > hi)
     step_s = ms / args.steps / 1e3
     whole = {"algorithmic_bytes_per_step": whole_bytes,
              "achieved_gbs": whole_bytes / step_s / 1e9,

@@ -70,8 +70,8 @@ __device__ __forceinline__ BucketParams make_bucket_params(uint64_t lo, uint64_t
     p.max = hi;
     p.nb = nb;
     p.range = range;
-    p.recip = (key_bytes == 4 && range != 0) ? (~0ull / range) : 0ull;
-    p.mul_ok = (key_bytes == 4 && range != 0 && nb < range) ? 1u : 0u;
+    p.recip = (range != 0 && range <= 0x100000000ull) ? (~0ull / range) : 0ull;
+    p.mul_ok = (range != 0 && nb < range) ? 1u : 0u;
     p.mul = p.mul_ok ? (uint64_t)(((unsigned __int128)nb << 64) / range) : 0ull;
     p.bbits = nb > 1 ? 64u - __clzll(nb - 1) : 0u;
     p.valid = 1u;

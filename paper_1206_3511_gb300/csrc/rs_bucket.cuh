@@ -19,7 +19,7 @@ struct BucketParams {
     uint64_t nb;     // number of buckets
     uint64_t range;  // max - min + 1; 0 stands for 2^64
     uint64_t recip;  // floor((2^64 - 1) / range) when range <= 2^32
-    uint64_t mul;    // floor(2^64 * nb / range) for 32-bit keys when nb < range (mul_ok)
+    uint64_t mul;    // floor(2^64 * nb / range) when nb < range (mul_ok)
     uint32_t bbits;  // bit length of nb - 1 (0 when nb == 1)
     uint32_t valid;  // 1 once the parameters are set
     uint32_t mul_ok;
@@ -31,8 +31,13 @@ struct BucketParams {
 //   q = mulhi(x, floor((2^64-1)/range)) is at most 2 below the quotient
 //   (division by an invariant integer through a precomputed reciprocal,
 //   Granlund & Montgomery 1994), and the remainder test corrects it.
-//   64-bit keys: 128-bit product divided exactly; range 2^64 is a plain
-//   high product.
+//   64-bit keys with nb < range: the same estimate with 64-bit words,
+//   m = floor(2^64 nb / range) and e = floor(u m / 2^64) (a 64 x 64 high
+//   product), is the quotient or one below it for the same reason, and the
+//   exact comparison (e + 1) * range <= u * nb is made on 128-bit products
+//   (multiplications only; no division per key).  64-bit keys with
+//   nb >= range have range <= 2^32 and u * nb < 2^64, so they take the
+//   32-bit keys' reciprocal path; range 2^64 is a plain high product.
 //   32-bit keys with nb < range take a cheaper estimate first: with
 //   m = floor(2^64 nb / range), e = floor(t m / 2^64) (t = k - min, a 32 x 64
 //   bit high product) is the quotient or one below it (m is short of
@@ -59,8 +64,22 @@ __device__ __forceinline__ uint64_t bucket_of(const BucketParams& bp, uint32_t k
 __device__ __forceinline__ uint64_t bucket_of(const BucketParams& bp, uint64_t k) {
     const uint64_t u = k - bp.min;
     if (bp.range == 0) return __umul64hi(u, bp.nb);
-    const unsigned __int128 x = (unsigned __int128)u * bp.nb;
-    return (uint64_t)(x / bp.range);
+    if (bp.mul_ok) {
+        const uint64_t e = __umul64hi(u, bp.mul);
+        const unsigned __int128 lhs = (unsigned __int128)(e + 1) * bp.range;
+        const unsigned __int128 rhs = (unsigned __int128)u * bp.nb;
+        return e + (uint64_t)(lhs <= rhs);
+    }
+    const uint64_t x = u * bp.nb;  // < 2^64: range <= 2^32 here
+    uint64_t q = __umul64hi(x, bp.recip);
+    uint64_t r = x - q * bp.range;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        if (r >= bp.range) {
+            ++q;
+            r -= bp.range;
+        }
+    return q;
 }
 
 __device__ __forceinline__ BucketParams load_bucket_params(const BucketParams* p) {
