@@ -66,7 +66,8 @@ typedef enum rs_status {
     RS_ERR_DEVICE_TIMEOUT = 6, /* device: a bounded inter-block wait gave up */
     RS_ERR_NOT_READY = 7,      /* server: request still running */
     RS_ERR_SHUTDOWN = 8,       /* server: request cancelled by shutdown */
-    RS_ERR_UNSUPPORTED = 9     /* configuration not compiled into this build */
+    RS_ERR_UNSUPPORTED = 9,    /* configuration not compiled into this build */
+    RS_ERR_CHECK_FAILED = 10   /* device, checked mode (RS_CHECKED=1): an output was not in order */
 } rs_status;
 
 /* Largest n for one (unsegmented) sort: per-block digit counts travel in the
@@ -342,6 +343,35 @@ RS_API rs_status rs_plan_launch(rs_plan* plan, rs_stream_t stream);
  * tuned in this call). */
 RS_API rs_status rs_plan_info(const rs_plan* plan, rs_config* cfg, size_t* kernel_nodes, float* tuned_ms);
 RS_API void rs_plan_destroy(rs_plan* plan);
+
+/* Autotuning results, kept across processes (no counterpart in the paper:
+ * the digit base of Sec. 2.5 is left open, and the autotuner picks it per
+ * GPU).  A plan's autotuner caches the shape it picks per (GPU name,
+ * algorithm, key width, values, key_bits, floor(log2 n)).  The cache can be
+ * written to and merged from a file of one JSON object per line, e.g.
+ *   {"gpu": "NVIDIA GB300", "algo": 0, "key_bytes": 4, "values": 0,
+ *    "key_bits": 32, "log2n": 26, "digit_bits": 8, "block_threads": 256,
+ *    "items_per_thread": 22}
+ * Lines that do not parse, or name a shape this build does not compile, are
+ * skipped.  With the environment variable RS_TUNE_CACHE set to a path, plans
+ * merge that file before their first tuning and rewrite it (through a
+ * temporary file and a rename) after each new result.
+ *   rs_tune_cache_load: entries merged from path, or -1 if it cannot be read.
+ *   rs_tune_cache_save: entries written to path, or -1 on an I/O error.
+ *   rs_tune_cache_size: entries in the process's cache.
+ *   rs_tune_cache_clear: forget every entry (files are not touched).
+ * Thread-safe; no GPU needed.
+ *
+ * Other environment switches (read once per process): RS_DIGIT_BITS (4..11)
+ * sets the digit width of radix sorts that name no kernel shape (default 8);
+ * RS_SPIN_LIMIT sets the poll limit of the bounded inter-block waits unless
+ * rs_set_debug has set one; RS_CHECKED=1 makes rs_sort_*, rs_sort_typed and
+ * bs_sort_* verify on the device that their output is in order, recording
+ * RS_ERR_CHECK_FAILED in the status word if it is not. */
+RS_API int rs_tune_cache_load(const char* path);
+RS_API int rs_tune_cache_save(const char* path);
+RS_API int rs_tune_cache_size(void);
+RS_API void rs_tune_cache_clear(void);
 
 /* ---------------------------------------------------------------------------
  * Sort server (continuous batching).  Requests arrive at any time from any

@@ -122,12 +122,17 @@ SIGNATURES: dict[str, tuple] = {
     "rs_profile_enable": (None, [_I]),
     "rs_profile_read": (_I, [_c.POINTER(RsKernelStat), _I]),
     "rs_launch_count": (_U64, []),
+    "rs_tune_cache_load": (_I, [_c.c_char_p]),
+    "rs_tune_cache_save": (_I, [_c.c_char_p]),
+    "rs_tune_cache_size": (_I, []),
+    "rs_tune_cache_clear": (None, []),
 }
 
 STATUS = {
     0: "RS_OK", 1: "RS_ERR_INVALID_ARG", 2: "RS_ERR_WORKSPACE", 3: "RS_ERR_KEY_RANGE", 4: "RS_ERR_BUDGET",
     5: "RS_ERR_CUDA", 6: "RS_ERR_DEVICE_TIMEOUT", 7: "RS_ERR_NOT_READY", 8: "RS_ERR_SHUTDOWN",
     9: "RS_ERR_UNSUPPORTED",
+    10: "RS_ERR_CHECK_FAILED",
 }
 RS_ALGO_RADIX = 0
 RS_ALGO_BUCKET = 1
@@ -473,6 +478,22 @@ def rs_sort_segmented_host_u64(h_keys_in, h_keys_out, h_vals_in, h_vals_out, h_s
     return _call("rs_sort_segmented_host_u64", ptr(h_keys_in), ptr(h_keys_out), ptr(h_vals_in), ptr(h_vals_out),
                  ptr(h_seg_offsets), nseg, n_total, key_bits, ptr(dev_buf), dev_buf_bytes, stream_handle(stream),
                  _c.byref(c) if c is not None else None)
+
+
+def rs_tune_cache_load(path: str) -> int:
+    return _call("rs_tune_cache_load", os.fsencode(path))
+
+
+def rs_tune_cache_save(path: str) -> int:
+    return _call("rs_tune_cache_save", os.fsencode(path))
+
+
+def rs_tune_cache_size() -> int:
+    return _call("rs_tune_cache_size")
+
+
+def rs_tune_cache_clear() -> None:
+    _call("rs_tune_cache_clear")
 
 
 def rs_get_status(ws, stream=None) -> int:

@@ -1,7 +1,9 @@
 // rs_api.cu -- library-wide C entry points: status strings, version,
 // workspace sizing, the device status word, the debug hooks and the sorts of
 // arrays held in host memory.
+#include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -19,9 +21,34 @@ std::atomic<int> g_stall_tile{-1};
 constexpr uint32_t kDefaultSpinLimit = 1u << 21;  // polls; about a second with the back-off
 }  // namespace
 
+namespace {
+// A positive integer from the environment, or `fallback` (read once by callers).
+long env_long(const char* name, long fallback) {
+    const char* v = std::getenv(name);
+    if (!v || !*v) return fallback;
+    char* end = nullptr;
+    const long x = std::strtol(v, &end, 10);
+    return (end && *end == '\0' && x > 0) ? x : fallback;
+}
+}  // namespace
+
 uint32_t debug_spin_limit() {
+    static const uint32_t env = (uint32_t)std::min<long>(env_long("RS_SPIN_LIMIT", kDefaultSpinLimit), 0x7fffffffL);
     uint32_t v = g_spin_limit.load(std::memory_order_relaxed);
-    return v ? v : kDefaultSpinLimit;
+    return v ? v : env;
+}
+
+int default_digit_bits() {
+    static const int d = [] {
+        const long x = env_long("RS_DIGIT_BITS", 8);
+        return (x >= kMinDigitBits && x <= kMaxDigitBits) ? (int)x : 8;
+    }();
+    return d;
+}
+
+bool checked_mode() {
+    static const bool on = env_long("RS_CHECKED", 0) == 1;
+    return on;
 }
 
 int debug_stall_tile() { return g_stall_tile.load(std::memory_order_relaxed); }
@@ -49,7 +76,7 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
-KernelScope::KernelScope(const char* name, cudaStream_t stream) : slot_(-1), stream_(stream) {
+KernelScope::KernelScope(const char* name, cudaStream_t stream) : range_(name), slot_(-1), stream_(stream) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_profile.load(std::memory_order_relaxed)) return;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -334,6 +361,7 @@ const char* rs_status_string(rs_status s) {
         case RS_ERR_NOT_READY: return "RS_ERR_NOT_READY: request still running";
         case RS_ERR_SHUTDOWN: return "RS_ERR_SHUTDOWN: request cancelled by shutdown";
         case RS_ERR_UNSUPPORTED: return "RS_ERR_UNSUPPORTED: configuration not compiled";
+        case RS_ERR_CHECK_FAILED: return "RS_ERR_CHECK_FAILED: checked mode found an output out of order";
     }
     return "unknown rs_status";
 }

@@ -829,9 +829,24 @@ static rs_status bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const uint32
     return RS_OK;
 }
 
+static rs_status bucket_impl_body(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                                  uint32_t* vals_out, size_t n, uint64_t min_key, uint64_t max_key, size_t nb,
+                                  void* ws, size_t ws_bytes, cudaStream_t stream);
+
 static rs_status bucket_impl(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
                              uint32_t* vals_out, size_t n, uint64_t min_key, uint64_t max_key, size_t nb, void* ws,
                              size_t ws_bytes, cudaStream_t stream) {
+    NvtxRange range(key_bytes == 4 ? "bs_sort_u32" : "bs_sort_u64");
+    rs_status st = bucket_impl_body(key_bytes, keys_in, keys_out, vals_in, vals_out, n, min_key, max_key, nb, ws,
+                                    ws_bytes, stream);
+    if (st == RS_OK && n > 1 && checked_mode())
+        st = enqueue_order_check(key_bytes, keys_out, n, KeyXform{}, static_cast<WsHeader*>(ws), stream);
+    return st;
+}
+
+static rs_status bucket_impl_body(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                                  uint32_t* vals_out, size_t n, uint64_t min_key, uint64_t max_key, size_t nb,
+                                  void* ws, size_t ws_bytes, cudaStream_t stream) {
     if ((vals_in == nullptr) != (vals_out == nullptr)) return RS_ERR_INVALID_ARG;
     if (n > RS_MAX_KEYS) return RS_ERR_INVALID_ARG;
     if (n == 0) return RS_OK;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -202,10 +203,30 @@ inline bool ranges_overlap(const void* a, size_t abytes, const void* b, size_t b
     return x < y + bbytes && y < x + abytes;
 }
 
-// Library-wide debug knobs (rs_set_debug).
+// Library-wide debug knobs (rs_set_debug; the environment variable
+// RS_SPIN_LIMIT sets the spin limit when rs_set_debug has not).
 uint32_t debug_spin_limit();
 int debug_stall_tile();
 int device_sm_count();
+
+// Digit width of radix sorts that name no kernel shape: 8, or the
+// environment variable RS_DIGIT_BITS (4 .. 11) read once.
+int default_digit_bits();
+
+// Checked mode (environment variable RS_CHECKED=1, read once): rs_sort_*,
+// rs_sort_typed and bs_sort_* verify on the device that their output is in
+// nondecreasing order and record RS_ERR_CHECK_FAILED otherwise.
+bool checked_mode();
+
+// A named NVTX range on the host timeline (nvtxRangePush / Pop) for as long
+// as the object lives; without a profiler attached it costs one test.
+class NvtxRange {
+  public:
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Wraps one kernel launch: counts it and, while rs_profile_enable(1) is in
 // force, records CUDA events around it on its stream.
@@ -217,6 +238,7 @@ class KernelScope {
     KernelScope& operator=(const KernelScope&) = delete;
 
   private:
+    NvtxRange range_;
     long slot_;
     cudaStream_t stream_;
 };

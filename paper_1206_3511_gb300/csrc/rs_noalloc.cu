@@ -59,7 +59,7 @@ rs_status scratch_for_current_device(void** out) {
 size_t noalloc_scratch_needed() {
     const Variant* v = default_variant(4, true, RS_NOALLOC_MAX_KEYS, false);
     if (!v) return ~(size_t)0;
-    return radix_layout(4, true, RS_NOALLOC_MAX_KEYS, 32, kDefaultDigitBits, v->tile_keys, true).total;
+    return radix_layout(4, true, RS_NOALLOC_MAX_KEYS, 32, default_digit_bits(), v->tile_keys, true).total;
 }
 
 }  // namespace

@@ -696,6 +696,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p)
     }
 }
 
+// Checked mode: every key of a sort's output is at most the next one in the
+// sort's order (typed keys compared by their ordered image); the first pair
+// out of order is recorded as RS_ERR_CHECK_FAILED.
+template <typename KeyT>
+__global__ void __launch_bounds__(256) k_check_order(const KeyT* __restrict__ keys, size_t n, KeyXform xf,
+                                                     WsHeader* hdr) {
+    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i + 1 < n; i += (size_t)gridDim.x * 256) {
+        if (xf.to_ordered(keys[i + 1]) < xf.to_ordered(keys[i])) {
+            set_device_error(hdr, RS_ERR_CHECK_FAILED, (uint32_t)i);
+            return;
+        }
+    }
+}
+
 // Blocks of a kernel that fit on the GPU at once (the grid of a persistent
 // launch); at least 1.  The occupancy query is cached per (kernel, shared
 // memory, device): it costs host time on every launch otherwise.

@@ -6,6 +6,10 @@
 // the speed.  Tuning results are cached per (GPU, key width, values, key
 // bits, log2 n).
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
 #include <map>
 #include <mutex>
 #include <string>
@@ -61,6 +65,120 @@ TuneKey tune_key(const rs_plan_desc& d) {
                    d.n ? (int)std::floor(std::log2((double)d.n)) : 0);
 }
 
+// ---------------------------------------------------------------- persisted tuning results
+// A tuning cache file holds one JSON object per line:
+//   {"gpu": "NVIDIA GB300", "algo": 0, "key_bytes": 4, "values": 0,
+//    "key_bits": 32, "log2n": 26, "digit_bits": 8, "block_threads": 256,
+//    "items_per_thread": 22}
+// Lines that do not parse, or name a shape this build does not compile, are
+// skipped.  The environment variable RS_TUNE_CACHE names a file that plans
+// read before their first tuning and rewrite after every new result.
+
+// The value after "name": in a line (a string without quotes, or a number).
+bool json_field(const std::string& line, const char* name, std::string* out) {
+    const std::string key = std::string("\"") + name + "\"";
+    size_t p = line.find(key);
+    if (p == std::string::npos) return false;
+    p = line.find(':', p + key.size());
+    if (p == std::string::npos) return false;
+    ++p;
+    while (p < line.size() && line[p] == ' ') ++p;
+    if (p < line.size() && line[p] == '"') {
+        const size_t q = line.find('"', p + 1);
+        if (q == std::string::npos) return false;
+        *out = line.substr(p + 1, q - p - 1);
+        return true;
+    }
+    size_t q = p;
+    while (q < line.size() && (line[q] == '-' || (line[q] >= '0' && line[q] <= '9'))) ++q;
+    if (q == p) return false;
+    *out = line.substr(p, q - p);
+    return true;
+}
+
+bool json_int(const std::string& line, const char* name, int* out) {
+    std::string v;
+    if (!json_field(line, name, &v)) return false;
+    char* end = nullptr;
+    const long x = std::strtol(v.c_str(), &end, 10);
+    if (!end || *end != '\0' || x < -1000000 || x > 1000000) return false;
+    *out = (int)x;
+    return true;
+}
+
+// A shape is usable for a key if this build compiles it for that algorithm.
+bool shape_compiled(int algo, int key_bytes, bool vals, const rs_config& c) {
+    if (algo == RS_PLAN_SEGMENTED)
+        return c.digit_bits == kSegDigitBits && seg_shape_find(key_bytes, vals, c.block_threads, c.items_per_thread) >= 0;
+    if (algo != RS_PLAN_RADIX || c.digit_bits < kMinDigitBits || c.digit_bits > kMaxDigitBits) return false;
+    const Variant* v = find_variant(key_bytes, vals, c.block_threads, c.items_per_thread);
+    return v && v->smem_bytes(c.digit_bits) <= kMaxSmemPerBlock;
+}
+
+bool parse_tune_line(const std::string& line, TuneKey* key, rs_config* cfg) {
+    std::string gpu;
+    int algo, kb, vals, kbits, l2n;
+    if (!json_field(line, "gpu", &gpu) || !json_int(line, "algo", &algo) || !json_int(line, "key_bytes", &kb) ||
+        !json_int(line, "values", &vals) || !json_int(line, "key_bits", &kbits) || !json_int(line, "log2n", &l2n) ||
+        !json_int(line, "digit_bits", &cfg->digit_bits) || !json_int(line, "block_threads", &cfg->block_threads) ||
+        !json_int(line, "items_per_thread", &cfg->items_per_thread))
+        return false;
+    if ((kb != 4 && kb != 8) || (vals != 0 && vals != 1) || kbits < 1 || kbits > 8 * kb || l2n < 0 || l2n > 40)
+        return false;
+    if (!shape_compiled(algo, kb, vals != 0, *cfg)) return false;
+    *key = TuneKey(gpu, algo, kb, vals, kbits, l2n);
+    return true;
+}
+
+std::string tune_line(const TuneKey& k, const rs_config& c) {
+    std::string gpu = std::get<0>(k);
+    for (char& ch : gpu)
+        if (ch == '"' || ch == '\\' || (unsigned char)ch < 0x20) ch = '_';
+    char buf[512];
+    std::snprintf(buf, sizeof buf,
+                  "{\"gpu\": \"%s\", \"algo\": %d, \"key_bytes\": %d, \"values\": %d, \"key_bits\": %d, "
+                  "\"log2n\": %d, \"digit_bits\": %d, \"block_threads\": %d, \"items_per_thread\": %d}",
+                  gpu.c_str(), std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k),
+                  c.digit_bits, c.block_threads, c.items_per_thread);
+    return buf;
+}
+
+// Merge a cache file into the in-process cache: entries read, or -1.
+int tune_cache_load_locked(const char* path) {
+    std::ifstream f(path);
+    if (!f) return -1;
+    int got = 0;
+    std::string line;
+    while (std::getline(f, line)) {
+        TuneKey k;
+        rs_config c{};
+        if (parse_tune_line(line, &k, &c)) {
+            g_tune_cache[k] = c;
+            ++got;
+        }
+    }
+    return got;
+}
+
+// Write the in-process cache (through a temporary file renamed over the
+// target, so a reader never sees half a file): entries written, or -1.
+int tune_cache_save_locked(const char* path) {
+    const std::string tmp = std::string(path) + ".tmp";
+    {
+        std::ofstream f(tmp, std::ios::trunc);
+        if (!f) return -1;
+        for (const auto& e : g_tune_cache) f << tune_line(e.first, e.second) << "\n";
+        if (!f) return -1;
+    }
+    if (std::rename(tmp.c_str(), path) != 0) return -1;
+    return (int)g_tune_cache.size();
+}
+
+const char* env_tune_cache() {
+    const char* p = std::getenv("RS_TUNE_CACHE");
+    return (p && *p) ? p : nullptr;
+}
+
 // Time one shape: mean of `reps` runs after one warm-up run.
 float time_config(const rs_plan_desc& d, const rs_config& cfg, cudaStream_t s, cudaEvent_t a, cudaEvent_t b,
                   int reps) {
@@ -92,6 +210,11 @@ rs_status autotune(const rs_plan_desc& d, cudaStream_t s, rs_config* best, float
     const TuneKey key = tune_key(d);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        static bool env_loaded = false;
+        if (!env_loaded) {
+            env_loaded = true;
+            if (const char* p = env_tune_cache()) tune_cache_load_locked(p);
+        }
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             *best = it->second;
@@ -129,6 +252,7 @@ rs_status autotune(const rs_plan_desc& d, cudaStream_t s, rs_config* best, float
     *best_ms = found;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = *best;
+    if (const char* p = env_tune_cache()) tune_cache_save_locked(p);  // best effort: tuning stands regardless
     return RS_OK;
 }
 
@@ -149,6 +273,28 @@ struct rs_plan {
 };
 
 extern "C" {
+
+int rs_tune_cache_load(const char* path) {
+    if (!path) return -1;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return tune_cache_load_locked(path);
+}
+
+int rs_tune_cache_save(const char* path) {
+    if (!path) return -1;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return tune_cache_save_locked(path);
+}
+
+int rs_tune_cache_size(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (int)g_tune_cache.size();
+}
+
+void rs_tune_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.clear();
+}
 
 rs_status rs_plan_create(const rs_plan_desc* desc, rs_plan** out) {
     if (!desc || !out) return RS_ERR_INVALID_ARG;

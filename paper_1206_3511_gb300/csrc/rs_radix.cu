@@ -147,7 +147,7 @@ size_t radix_workspace_bytes(int key_bytes, bool vals, size_t n, int key_bits) {
     size_t best = 0;
     for (const Variant& v : kVariants) {
         if (v.key_bytes != key_bytes || v.vals != vals) continue;
-        for (int D = kMinDigitBits; D <= kDefaultDigitBits; ++D) {
+        for (int D = kMinDigitBits; D <= std::max(kDefaultDigitBits, default_digit_bits()); ++D) {
             size_t t = radix_layout(key_bytes, vals, n, key_bits, D, v.tile_keys, true).total;
             if (t > best) best = t;
         }
@@ -165,8 +165,26 @@ rs_status resolve_config(int key_bytes, bool vals, size_t n, bool typed, const r
                          int* digit_bits) {
     if (!cfg) {
         *var = default_variant(key_bytes, vals, n, typed);
-        *digit_bits = kDefaultDigitBits;
-        return *var ? RS_OK : RS_ERR_UNSUPPORTED;
+        if (!*var) return RS_ERR_UNSUPPORTED;
+        // RS_DIGIT_BITS may ask for wider digits than the default shape's
+        // tables allow: then the first compiled shape that holds them (plain
+        // keys), else 8-bit digits
+        int D = default_digit_bits();
+        if ((*var)->smem_bytes(D) > kMaxSmemPerBlock) {
+            const Variant* fit = nullptr;
+            if (!typed)
+                for (const Variant& v : kVariants)
+                    if (v.key_bytes == key_bytes && v.vals == vals && v.smem_bytes(D) <= kMaxSmemPerBlock) {
+                        fit = &v;
+                        break;
+                    }
+            if (fit)
+                *var = fit;
+            else
+                D = kDefaultDigitBits;
+        }
+        *digit_bits = D;
+        return RS_OK;
     }
     if (cfg->digit_bits < kMinDigitBits || cfg->digit_bits > kMaxDigitBits) return RS_ERR_INVALID_ARG;
     *var = find_variant(key_bytes, vals, cfg->block_threads, cfg->items_per_thread);
@@ -205,9 +223,36 @@ rs_status radix_sort_impl(int key_bytes, const void* keys_in, void* keys_out, co
                          KeyXform{});
 }
 
+rs_status enqueue_order_check(int key_bytes, const void* keys, size_t n, const KeyXform& xf, WsHeader* hdr,
+                              cudaStream_t stream) {
+    if (n < 2) return RS_OK;
+    const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, (size_t)device_sm_count() * 8);
+    KernelScope scope("check_order", stream);
+    if (key_bytes == 4)
+        k_check_order<uint32_t><<<grid, 256, 0, stream>>>(static_cast<const uint32_t*>(keys), n, xf, hdr);
+    else
+        k_check_order<uint64_t><<<grid, 256, 0, stream>>>(static_cast<const uint64_t*>(keys), n, xf, hdr);
+    return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
+static rs_status radix_sort_xf_body(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                                    uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
+                                    cudaStream_t stream, const rs_config* cfg, const KeyXform& xf);
+
 rs_status radix_sort_xf(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
                         uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes, cudaStream_t stream,
                         const rs_config* cfg, const KeyXform& xf) {
+    NvtxRange range(key_bytes == 4 ? "rs_sort_u32" : "rs_sort_u64");
+    rs_status st = radix_sort_xf_body(key_bytes, keys_in, keys_out, vals_in, vals_out, n, key_bits, ws, ws_bytes,
+                                      stream, cfg, xf);
+    if (st == RS_OK && n > 1 && checked_mode())
+        st = enqueue_order_check(key_bytes, keys_out, n, xf, static_cast<WsHeader*>(ws), stream);
+    return st;
+}
+
+static rs_status radix_sort_xf_body(int key_bytes, const void* keys_in, void* keys_out, const uint32_t* vals_in,
+                                    uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes,
+                                    cudaStream_t stream, const rs_config* cfg, const KeyXform& xf) {
     const int width = 8 * key_bytes;
     if (key_bits == 0) key_bits = width;
     if (key_bits < 1 || key_bits > width) return RS_ERR_INVALID_ARG;
@@ -453,9 +498,10 @@ rs_status rs_counting_pass_u64(const uint64_t* keys_in, uint64_t* keys_out, cons
 
 rs_status rs_default_config(int key_bytes, int has_values, size_t n, rs_config* out) {
     if ((key_bytes != 4 && key_bytes != 8) || !out) return RS_ERR_INVALID_ARG;
-    const Variant* v = default_variant(key_bytes, has_values != 0, n, false);
-    if (!v) return RS_ERR_UNSUPPORTED;
-    out->digit_bits = kDefaultDigitBits;
+    const Variant* v = nullptr;
+    int D = 0;
+    if (resolve_config(key_bytes, has_values != 0, n, false, nullptr, &v, &D) != RS_OK) return RS_ERR_UNSUPPORTED;
+    out->digit_bits = D;
     out->block_threads = v->block;
     out->items_per_thread = v->items;
     return RS_OK;

@@ -65,6 +65,11 @@ rs_status radix_sort_xf(int key_bytes, const void* keys_in, void* keys_out, cons
                         uint32_t* vals_out, size_t n, int key_bits, void* ws, size_t ws_bytes, cudaStream_t stream,
                         const rs_config* cfg, const KeyXform& xf);
 
+// Checked mode: enqueue the order check of a sort's output (n keys of
+// key_bytes bytes at keys) into the status word of hdr.
+rs_status enqueue_order_check(int key_bytes, const void* keys, size_t n, const KeyXform& xf, WsHeader* hdr,
+                              cudaStream_t stream);
+
 // Grid of the digit-count kernel for n keys.
 size_t count_grid(size_t n);
 

@@ -54,7 +54,7 @@ constexpr SegVariant seg_variant() {
 
 // The first entry of each (key width, values) group is SegShape's.
 const SegVariant kSegVariants[] = {
-    seg_variant<uint32_t, false, 384, 16, 3>(), seg_variant<uint32_t, false, 256, 22, 4>(),
+    seg_variant<uint32_t, false, 256, 22, 4>(), seg_variant<uint32_t, false, 384, 16, 3>(),
     seg_variant<uint32_t, false, 256, 20, 4>(), seg_variant<uint32_t, false, 256, 24, 4>(),
     seg_variant<uint32_t, false, 256, 18, 4>(),
     seg_variant<uint32_t, false, 256, 15, 4>(), seg_variant<uint32_t, false, 512, 15, 2>(),

@@ -244,7 +244,7 @@ template <typename KeyT, bool VALS, int BLOCK>
 struct LocalSmem {
     static constexpr int kWarps = BLOCK / 32;
     static size_t bytes(int cap) {
-        size_t b = (size_t)kWarps * 256 * 8;          // rank table
+        size_t b = (size_t)(BLOCK / 16) * (256 + kSubPad) * 4;  // rank tables (one per half-warp)
         b += 2 * (size_t)cap * sizeof(KeyT);          // key buffers
         if (VALS) b += 2 * (size_t)cap * 4;           // value buffers
         b += 256 * 4 * 2 + (kWarps + 1 + 3) * 4 + 16; // starts, counts, scan scratch, flags
@@ -253,37 +253,43 @@ struct LocalSmem {
     }
 };
 
+// Rank tables of the shared-memory sort: one per half-warp, 256 + kSubPad
+// 32-bit words each (as in the scatter pass).
+constexpr uint32_t kLocalTabStride = 256 + kSubPad;
+
 // One stable pass of the shared-memory sort: keys (and values) move from
-// (ka, va) to (kb, vb) ordered by digit dfun(key) < 256.
+// (ka, va) to (kb, vb) ordered by digit dfun(key) < 256.  Each half-warp owns
+// a contiguous run of keys and ranks them with subwarp_rank.
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename DFun>
 __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, KeyT* kb, uint32_t* vb, uint32_t m,
-                                           unsigned long long* s_tab, uint32_t* s_start, uint32_t* s_cnt,
-                                           uint32_t* s_scan, DFun dfun, uint8_t* s_dig = nullptr) {
-    constexpr int kWarps = BLOCK / 32;
+                                           uint32_t* s_tab, uint32_t* s_start, uint32_t* s_cnt, uint32_t* s_scan,
+                                           DFun dfun, uint8_t* s_dig = nullptr) {
+    constexpr int kSubs = BLOCK / 16;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (uint32_t i = tid; i < (uint32_t)kWarps * 256; i += BLOCK) s_tab[i] = 0ull;
+    const int half = lane >> 4, hl = lane & 15;
+    for (uint32_t i = tid; i < (uint32_t)kSubs * kLocalTabStride; i += BLOCK) s_tab[i] = 0u;
     __syncthreads();
-    const uint32_t tab = smem_addr(s_tab + (size_t)warp * 256);
-    const uint32_t lt = lanemask_lt(), lanebit = 1u << lane, gt = ~(lt | lanebit);
-    // each warp owns a contiguous run of `used` items of 32 keys, just enough
-    // to cover the m keys of the segment
+    const uint32_t tab = smem_addr(s_tab + (size_t)(2 * warp + half) * kLocalTabStride);
+    const uint32_t hbit = 1u << hl, hlt = hbit - 1u, hgt = 0xffffu & ~(hlt | hbit);
+    // each half-warp owns a contiguous run of `used` items of 16 keys, just
+    // enough to cover the m keys of the segment
     const uint32_t used = (m + BLOCK - 1) / BLOCK;
-    const uint32_t wofs = (uint32_t)warp * (used * 32) + lane;
+    const uint32_t hofs = (uint32_t)(2 * warp + half) * (used * 16) + hl;
     uint32_t dr[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         if ((uint32_t)i < used) {
-            const uint32_t idx = wofs + i * 32;
+            const uint32_t idx = hofs + i * 16;
             const bool ok = idx < m;
             const uint32_t d = ok ? dfun(ka[idx]) : 0u;
-            dr[i] = (d << 16) | warp_rank<false>(tab, d, ok, lanebit, lt, gt);
+            dr[i] = (d << 16) | subwarp_rank<false>(tab, d, ok, hbit, hlt, hgt);
         }
     }
     __syncthreads();
     for (uint32_t d = tid; d < 256; d += BLOCK) {
         uint32_t sum = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) sum += (uint32_t)(s_tab[(size_t)w * 256 + d] >> 32);
+        for (int s = 0; s < kSubs; ++s) sum += s_tab[(size_t)s * kLocalTabStride + d] >> 16;
         s_cnt[d] = sum;
         s_start[d] = sum;
     }
@@ -291,20 +297,20 @@ __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, K
     block_exclusive_scan_smem<BLOCK>(s_start, 256, s_scan);
     for (uint32_t d = tid; d < 256; d += BLOCK) {
         uint32_t run = s_start[d];
-        uint32_t* low = reinterpret_cast<uint32_t*>(s_tab + d);
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t cnt = low[2 * (size_t)w * 256 + 1];
-            low[2 * (size_t)w * 256] = run;
+        for (int s = 0; s < kSubs; ++s) {
+            uint32_t* e = s_tab + (size_t)s * kLocalTabStride + d;
+            const uint32_t cnt = *e >> 16;
+            *e = run;
             run += cnt;
         }
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t idx = wofs + i * 32;
+        const uint32_t idx = hofs + i * 16;
         if ((uint32_t)i < used && idx < m) {
-            const uint32_t pos = ld_shared_u32(tab + 8u * (dr[i] >> 16)) + (dr[i] & 0xffffu);
+            const uint32_t pos = ld_shared_u32(tab + 4u * (dr[i] >> 16)) + (dr[i] & 0xffffu);
             if (pos < m) {
                 kb[pos] = ka[idx];
                 if (VALS) vb[pos] = va[idx];
@@ -333,9 +339,9 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
     constexpr int kCap = BLOCK * ITEMS;
     constexpr int kWarps = BLOCK / 32;
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned long long* s_tab = reinterpret_cast<unsigned long long*>(smem);
+    uint32_t* s_tab = reinterpret_cast<uint32_t*>(smem);
     KeyT* kbuf[2];
-    kbuf[0] = reinterpret_cast<KeyT*>(s_tab + kWarps * 256);
+    kbuf[0] = reinterpret_cast<KeyT*>(s_tab + (size_t)(BLOCK / 16) * kLocalTabStride);
     kbuf[1] = kbuf[0] + kCap;
     uint32_t* vbuf[2];
     vbuf[0] = reinterpret_cast<uint32_t*>(kbuf[1] + kCap);

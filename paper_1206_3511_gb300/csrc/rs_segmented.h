@@ -23,7 +23,7 @@ template <typename KeyT, bool VALS>
 struct SegShape;
 template <>
 struct SegShape<uint32_t, false> {
-    static constexpr int kBlock = 384, kItems = 16, kMinB = 3, kTile = kBlock * kItems;
+    static constexpr int kBlock = 256, kItems = 22, kMinB = 4, kTile = kBlock * kItems;
 };
 template <>
 struct SegShape<uint32_t, true> {
