@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) k_bucket_counts(const KeyT* __restrict__ 
     bool bad = false;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const KeyT k = keys[i];
-        if ((uint64_t)k < bp.min || (uint64_t)k > bp.max) {
+        if (!key_in_bounds(bp, k)) {
             bad = true;
             continue;
         }
@@ -118,7 +118,7 @@ struct BucketCountDigits {
     }
     template <typename KeyT>
     __device__ __forceinline__ bool in_range(KeyT k) const {
-        return (uint64_t)k >= bp.min && (uint64_t)k <= bp.max;
+        return key_in_bounds(bp, k);
     }
     template <typename KeyT>
     __device__ __forceinline__ KeyT order(KeyT k) const {

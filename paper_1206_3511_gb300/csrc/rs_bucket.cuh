@@ -46,8 +46,15 @@ struct BucketParams {
 __device__ __forceinline__ uint64_t bucket_of(const BucketParams& bp, uint32_t k) {
     const uint32_t t = k - (uint32_t)bp.min;
     if (bp.mul_ok) {
-        const uint64_t e = ((uint64_t)t * (uint32_t)(bp.mul >> 32) + __umulhi(t, (uint32_t)bp.mul)) >> 32;
-        return e + (uint64_t)((e + 1) * bp.range <= (uint64_t)t * bp.nb);
+        // nb < range <= 2^32, so the estimate e <= floor(t nb / range) < nb
+        // and e + 1 fit 32 bits, and both sides of the exact comparison are
+        // sums of 32 x 32-bit products (range split into its low word and
+        // bit 32): no 64 x 64-bit multiplication per key
+        const uint32_t e =
+            (uint32_t)(((uint64_t)t * (uint32_t)(bp.mul >> 32) + __umulhi(t, (uint32_t)bp.mul)) >> 32);
+        const uint64_t lhs =
+            (uint64_t)(e + 1u) * (uint32_t)bp.range + ((bp.range >> 32) ? ((uint64_t)(e + 1u) << 32) : 0ull);
+        return (uint64_t)(e + (uint32_t)(lhs <= (uint64_t)t * (uint32_t)bp.nb));
     }
     const uint64_t x = (uint64_t)t * bp.nb;
     uint64_t q = __umul64hi(x, bp.recip);
@@ -80,6 +87,15 @@ __device__ __forceinline__ uint64_t bucket_of(const BucketParams& bp, uint64_t k
             r -= bp.range;
         }
     return q;
+}
+
+// min <= k <= max; for 32-bit keys max - min < 2^32, so one 32-bit
+// subtraction and comparison decide it.
+__device__ __forceinline__ bool key_in_bounds(const BucketParams& bp, uint32_t k) {
+    return k - (uint32_t)bp.min <= (uint32_t)(bp.max - bp.min);
+}
+__device__ __forceinline__ bool key_in_bounds(const BucketParams& bp, uint64_t k) {
+    return k >= bp.min && k <= bp.max;
 }
 
 __device__ __forceinline__ BucketParams load_bucket_params(const BucketParams* p) {
@@ -174,7 +190,7 @@ struct BucketDigits {
     }
     template <typename KeyT>
     __device__ __forceinline__ bool in_range(KeyT k) const {
-        return !check_range || ((uint64_t)k >= bp.min && (uint64_t)k <= bp.max);
+        return !check_range || key_in_bounds(bp, k);
     }
 };
 
@@ -197,7 +213,7 @@ struct SegBucketFn {
     }
     template <typename KeyT>
     __device__ __forceinline__ bool in_range(KeyT k) const {
-        return !check_range || ((uint64_t)k >= bp.min && (uint64_t)k <= bp.max);
+        return !check_range || key_in_bounds(bp, k);
     }
     __device__ __forceinline__ uint64_t first_bucket(const SegDesc& s) const { return s.aux; }
     __device__ __forceinline__ uint64_t bucket_span(const SegDesc& s) const { return s.chunk0; }
