@@ -166,6 +166,7 @@ struct BucketDigit {
 // check_range, keys outside the segment's [min, max] are reported (declared
 // bounds of the segmented bucket sort).
 struct BucketDigits {
+    static constexpr bool kBytesCapable = false;
     const BucketParams* src;
     int shift;
     uint32_t mask;
@@ -192,6 +193,7 @@ struct BucketDigits {
     __device__ __forceinline__ bool in_range(KeyT k) const {
         return !check_range || key_in_bounds(bp, k);
     }
+    __device__ __forceinline__ bool byte_digits() const { return false; }
 };
 
 // Bucket view for the shared-memory sort of one partition: the partition's

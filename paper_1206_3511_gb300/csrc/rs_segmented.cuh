@@ -130,6 +130,24 @@ __global__ void __launch_bounds__(512) k_seg_counts(const KeyT* __restrict__ key
         // that enough loads are in flight to cover the memory latency
         constexpr uint32_t kU = 8;
         uint32_t i = lo + tid;
+        // 8-bit digits from bit 0, one per key byte (every segmented radix
+        // sort over whole bytes): digit q is byte q of the key, read with
+        // compile-time shifts
+        const bool bytes = Digits::kBytesCapable && dg.byte_digits() && passes <= (int)sizeof(KeyT);
+        if (bytes) {
+            for (; i + (kU - 1) * blockDim.x < hi; i += kU * blockDim.x) {
+                KeyT x[kU];
+#pragma unroll
+                for (uint32_t u = 0; u < kU; ++u) x[u] = (KeyT)(__ldcs(kp + i + u * blockDim.x) - klo);
+#pragma unroll
+                for (uint32_t u = 0; u < kU; ++u) {
+                    bad |= check && (x[u] >> (check ? d.bits : 0)) != 0;
+#pragma unroll
+                    for (int q = 0; q < (int)sizeof(KeyT); ++q)
+                        if (q < passes) atomicAdd(&s_cnt[q * 256 + (uint32_t)((x[u] >> (8 * q)) & 0xffu)], 1u);
+                }
+            }
+        }
         for (; i + (kU - 1) * blockDim.x < hi; i += kU * blockDim.x) {
             KeyT x[kU];
 #pragma unroll
@@ -237,14 +255,16 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep_seg(SegPassParams<Digi
 // Algorithm 1, made for all keys at once); a segment with a bucket above
 // kBucketSortMax keys, or spanning more than 256 buckets, is sorted by its
 // key bits instead, which gives the same order because bucket ids grow with
-// the key.  So is a segment whose keys span at most kLeafKeyBits bits: its
-// whole run of buckets is then sorted by at most three 8-bit passes on the
-// key bits, which on GB300 costs less than the counting pass by bucket and
-// the rank sort of every bucket (0.68 against 1.12 ms per launch for the
-// leaves of 100M uniform 32-bit keys, whose runs span about 18 bits; for
-// 64-bit keys, whose runs span about 49 bits, the bucket pass wins, 1.62
-// against 1.86 ms).  The result is the same: sorting a run of whole buckets
-// by key sorts every bucket and keeps them in bucket order.
+// the key.  So is every segment of 32-bit keys, and a segment of 64-bit
+// keys that span at most kLeafKeyBits bits: the whole run of buckets is then
+// sorted by at most four (32-bit) or three 8-bit passes on the key bits,
+// which on GB300 costs less than the counting pass by bucket and the rank
+// sort of every bucket (0.68 against 1.12 ms per launch for the leaves of
+// 100M uniform 32-bit keys, whose runs span about 18 bits; for 64-bit keys,
+// whose runs span about 49 bits, the bucket pass wins, 1.62 against 1.86
+// ms).  The result is the same: sorting a run of whole buckets by key sorts
+// every bucket and keeps them in bucket order.  For 32-bit keys the bucket
+// path is compiled out, which also frees the registers it would hold.
 constexpr uint32_t kBucketSortMax = 48;
 constexpr uint32_t kLeafKeyBits = 24;
 
@@ -390,7 +410,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
         bool by_keys = !already_sorted;
         if (already_sorted) {
             // output straight from the loaded keys
-        } else if (bfn.active() && seg.bits > kLeafKeyBits) {
+        } else if (sizeof(KeyT) > 4 && bfn.active() && seg.bits > kLeafKeyBits) {
             const uint64_t b_lo = bfn.first_bucket(seg), span = bfn.bucket_span(seg);
             if (threadIdx.x == 0) *s_flag = 0u;
             __syncthreads();
