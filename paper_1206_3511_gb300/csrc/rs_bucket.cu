@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(256) k_bucket_counts(const KeyT* __restrict__ 
 // Range check of the declared bounds in the level-1 counting kernel.
 struct BucketCountDigits {
     static constexpr bool kBytesCapable = false;
+    static constexpr bool kOneDigit = true;
     const BucketParams* src;
     int shift;
     uint32_t mask;

@@ -78,6 +78,7 @@ __device__ __forceinline__ T warp_max(T x) {
 // and the key-range check (every key must be below 2^key_bits).
 struct RadixDigits {
     static constexpr bool kBytesCapable = true;
+    static constexpr bool kOneDigit = false;
     int shift0;
     int digit_bits;
     uint32_t mask;
@@ -107,6 +108,7 @@ struct RadixDigits {
 // images are valid, so there is no range check.
 struct OrderedRadixDigits {
     static constexpr bool kBytesCapable = true;
+    static constexpr bool kOneDigit = false;
     RadixDigits base;
     KeyXform xf;
     __device__ __forceinline__ void init() {}
@@ -148,7 +150,9 @@ template <typename KeyT, typename Digits, bool BYTES>
 __device__ __forceinline__ void count_key(uint32_t* s_cnt, KeyT k, const Digits& dg, int P, uint32_t bins,
                                           bool& bad) {
     bad |= !dg.in_range(k);
-    if (BYTES) {
+    if constexpr (Digits::kOneDigit) {  // one digit per key (the bucket sort's partition digit)
+        atomicAdd(&s_cnt[dg(k, 0)], 1u);
+    } else if (BYTES) {
         const KeyT o = dg.order(k);
 #pragma unroll
         for (int q = 0; q < (int)sizeof(KeyT); ++q)
