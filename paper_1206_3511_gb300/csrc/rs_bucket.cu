@@ -150,7 +150,8 @@ struct PlanLevel {
     int level;
     uint32_t row_stride;
     uint32_t cap;     // largest partition sorted in shared memory
-    uint32_t tile_keys;
+    uint32_t tile_keys;      // tile of the next level's partition pass
+    uint32_t ovf_tile_keys;  // tile of the overflow radix passes
     // parents: either the whole array (parents == null) or a device list
     const SegDesc* parents;
     const uint32_t* num_parents;
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(256) k_bucket_plan(PlanLevel pl) {
             bigc.key_lo = to_next ? 0 : bp.min + s_below[d];  // the next level digits the key's bucket id
             bigc.bits = to_next ? 0u : min(bit_length(wm1), (uint32_t)pl.key_width);
             is_big = 1;
-            big_tiles = ceil_div_u32(bigc.n, pl.tile_keys);
+            big_tiles = ceil_div_u32(bigc.n, to_next ? pl.tile_keys : pl.ovf_tile_keys);
             big_chunks = ceil_div_u32(bigc.n, kSegChunk);
         }
         const uint32_t at_leaf = block_exclusive_sum<kBlock>(is_leaf, s_scan);
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(256) k_copy_segments(const KeyT* __restrict__ 
 
 template <typename KeyT, bool VALS>
 cudaError_t launch_plain_bucket_pass(const PassParams<BucketDigit>& p, cudaStream_t s) {
-    using S = SegShape<KeyT, VALS>;
+    using S = BucketShape<KeyT, VALS>;
     using Shape = OnesweepShape<KeyT, VALS, S::kBlock, S::kItems>;
     auto kern = k_onesweep<KeyT, VALS, S::kBlock, S::kItems, S::kMinB, BucketDigit>;
     static std::once_flag once;
@@ -454,7 +455,7 @@ BucketPlanInfo plan_info(int key_bytes, bool vals, size_t n, size_t nb, bool bou
         I.ovf_bits = (bits + P - 1) / P;
         if (I.ovf_bits < 1) I.ovf_bits = 1;
     }
-    const uint32_t tk = seg_tile_keys(key_bytes, vals);
+    const uint32_t tk = std::min(seg_tile_keys(key_bytes, vals), bucket_tile_keys(key_bytes, vals));
     const size_t parents2 = (size_t)1 << I.d1;
     I.max_leaf2 = I.level2 ? std::min<size_t>(parents2 << I.d2, n) : 1;
     I.max_ovf = std::min<size_t>(n / kLocalCap + 1, I.level2 ? (parents2 << I.d2) : parents2);
@@ -645,7 +646,7 @@ static rs_status bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const uint32
                            reinterpret_cast<uint32_t*>(base + L.off_status1)};
     KeyT* tmp_k = reinterpret_cast<KeyT*>(base + L.off_tmp_keys);
     uint32_t* tmp_v = VALS ? reinterpret_cast<uint32_t*>(base + L.off_tmp_vals) : nullptr;
-    const uint32_t tk = SegShape<KeyT, VALS>::kTile;
+    const uint32_t tk = BucketShape<KeyT, VALS>::kTile;
 
     // header, plan counters and level-1 counts start at zero
     RS_CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(WsHeader), stream));
@@ -707,6 +708,7 @@ static rs_status bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const uint32
     pl.bp = bp;
     pl.cap = kLocalCap;
     pl.tile_keys = tk;
+    pl.ovf_tile_keys = SegShape<KeyT, VALS>::kTile;  // the overflow passes run the segmented radix shape
     pl.key_width = 8 * (int)sizeof(KeyT);
     pl.copy = copyl;
     pl.num_copy = &h_leaf1->num_next;
@@ -769,7 +771,7 @@ static rs_status bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const uint32
         sp.seg_base = rows;
         sp.pass = 0;
         sp.passes = 1;
-        if (launch_seg_pass<KeyT, VALS, BucketDigit>(sp, I.max_tiles, stream) != cudaSuccess) return RS_ERR_CUDA;
+        if (launch_bucket_seg_pass<KeyT, VALS, BucketDigit>(sp, I.max_tiles, stream) != cudaSuccess) return RS_ERR_CUDA;
         pl.shift = I.shift2;
         pl.digit_bits = I.d2;
         pl.parents = next;
@@ -930,7 +932,7 @@ SegBucketLayout seg_bucket_layout(int key_bytes, bool vals, size_t n_total, size
                                   bool bounds_known, uint64_t min_key, uint64_t max_key) {
     SegBucketLayout L{};
     const size_t big = n_total / (kLocalCap + 1) + 1;
-    const uint32_t tk = seg_tile_keys(key_bytes, vals);
+    const uint32_t tk = std::min(seg_tile_keys(key_bytes, vals), bucket_tile_keys(key_bytes, vals));
     L.max_large = std::min<size_t>(std::max<size_t>(nseg, 1), big);
     L.max_runs1 = std::min<size_t>(256 * L.max_large, n_total + 1);
     L.max_next = big;
@@ -1009,7 +1011,7 @@ static rs_status seg_bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const ui
                            reinterpret_cast<uint32_t*>(base + L.off_status1)};
     KeyT* tmp_k = reinterpret_cast<KeyT*>(base + L.off_tmp_keys);
     uint32_t* tmp_v = VALS ? reinterpret_cast<uint32_t*>(base + L.off_tmp_vals) : nullptr;
-    const uint32_t tk = SegShape<KeyT, VALS>::kTile;
+    const uint32_t tk = BucketShape<KeyT, VALS>::kTile;
     const int sms = device_sm_count();
     const unsigned seg_grid = (unsigned)((nseg + 255) / 256);
     const int check = bounds_known ? 1 : 0;
@@ -1080,12 +1082,13 @@ static rs_status seg_bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const ui
     sp.base.tile_ctr = &hdr->tile_ctr[0];
     sp.segs = large;
     sp.hdr = h_seg;
-    if (launch_seg_pass<KeyT, VALS, BucketDigit>(sp, L.max_tiles, stream) != cudaSuccess) return RS_ERR_CUDA;
+    if (launch_bucket_seg_pass<KeyT, VALS, BucketDigit>(sp, L.max_tiles, stream) != cudaSuccess) return RS_ERR_CUDA;
     PlanLevel pl{};
     pl.table = table;
     pl.row_stride = 256;
     pl.cap = kLocalCap;
     pl.tile_keys = tk;
+    pl.ovf_tile_keys = SegShape<KeyT, VALS>::kTile;  // the overflow passes run the segmented radix shape
     pl.key_width = 8 * (int)sizeof(KeyT);
     pl.copy = copyl;
     pl.num_copy = &h_leaf1->num_next;
@@ -1133,7 +1136,7 @@ static rs_status seg_bucket_sort_t(const KeyT* keys_in, KeyT* keys_out, const ui
     sp.base.tile_ctr = &hdr->tile_ctr[1];
     sp.segs = next;
     sp.hdr = h_next;
-    if (launch_seg_pass<KeyT, VALS, BucketDigit>(sp, L.max_tiles, stream) != cudaSuccess) return RS_ERR_CUDA;
+    if (launch_bucket_seg_pass<KeyT, VALS, BucketDigit>(sp, L.max_tiles, stream) != cudaSuccess) return RS_ERR_CUDA;
     {
         pl.level = 2;
         pl.parents = next;

@@ -59,6 +59,9 @@ const Variant kVariants[] = {
     make_variant<uint32_t, false, 384, 16, 3>(),
     make_variant<uint32_t, false, 256, 20, 4>(),
     make_variant<uint32_t, false, 256, 24, 4>(),
+    make_variant<uint32_t, false, 256, 26, 4>(),
+    make_variant<uint32_t, false, 256, 28, 3>(),
+    make_variant<uint32_t, false, 256, 32, 3>(),
     make_variant<uint32_t, false, 256, 18, 4>(),
     make_variant<uint32_t, false, 256, 15, 4>(),
     make_variant<uint32_t, false, 512, 15, 2>(),

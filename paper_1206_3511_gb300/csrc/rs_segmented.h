@@ -18,6 +18,12 @@ constexpr int kLocalBlock = 256;
 constexpr int kLocalItems = 16;
 constexpr uint32_t kLocalCap = kLocalBlock * kLocalItems;
 
+#ifndef RS_BUCKET_BLOCK  // u32 keys-only bucket partition passes: 384 x 12, 3 blocks/SM
+#define RS_BUCKET_BLOCK 384
+#define RS_BUCKET_ITEMS 12
+#define RS_BUCKET_MINB 3
+#endif
+
 // Kernel shapes of the segmented and bucket scatter passes.
 template <typename KeyT, bool VALS>
 struct SegShape;
@@ -37,6 +43,26 @@ template <>
 struct SegShape<uint64_t, true> {
     static constexpr int kBlock = 256, kItems = 10, kMinB = 3, kTile = kBlock * kItems;
 };
+
+// Kernel shapes of the bucket sort's partition passes.  Their digit carries
+// the bucket parameters (and computes the bucket id of every key twice),
+// which takes registers the radix passes spend on keys: the u32 keys-only
+// radix shape (256 x 22) spills 80 bytes with it, so the bucket passes take
+// a shape that holds it without spilling.
+template <typename KeyT, bool VALS>
+struct BucketShape : SegShape<KeyT, VALS> {};
+template <>
+struct BucketShape<uint32_t, false> {
+    static constexpr int kBlock = RS_BUCKET_BLOCK, kItems = RS_BUCKET_ITEMS, kMinB = RS_BUCKET_MINB,
+                         kTile = kBlock * kItems;
+};
+
+// Keys per tile of the bucket passes, and the smallest tile of the bucket
+// and segmented radix passes (workspace sizing of the bucket sorts).
+inline uint32_t bucket_tile_keys(int key_bytes, bool vals) {
+    if (key_bytes == 4) return vals ? BucketShape<uint32_t, true>::kTile : BucketShape<uint32_t, false>::kTile;
+    return vals ? BucketShape<uint64_t, true>::kTile : BucketShape<uint64_t, false>::kTile;
+}
 
 // One segmented scatter pass with an explicit kernel shape.
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS, int MINB, typename DigitOp>
@@ -58,10 +84,16 @@ cudaError_t launch_seg_pass_shape(const SegPassParams<DigitOp>& sp, size_t grid,
     return cudaGetLastError();
 }
 
-// One segmented scatter pass with the default shape of its key type.
+// One segmented scatter pass with the default shape of its key type (the
+// bucket shape for bucket-id digits).
 template <typename KeyT, bool VALS, typename DigitOp>
 cudaError_t launch_seg_pass(const SegPassParams<DigitOp>& sp, size_t grid, cudaStream_t s) {
     using S = SegShape<KeyT, VALS>;
+    return launch_seg_pass_shape<KeyT, VALS, S::kBlock, S::kItems, S::kMinB, DigitOp>(sp, grid, s);
+}
+template <typename KeyT, bool VALS, typename DigitOp>
+cudaError_t launch_bucket_seg_pass(const SegPassParams<DigitOp>& sp, size_t grid, cudaStream_t s) {
+    using S = BucketShape<KeyT, VALS>;
     return launch_seg_pass_shape<KeyT, VALS, S::kBlock, S::kItems, S::kMinB, DigitOp>(sp, grid, s);
 }
 
