@@ -392,10 +392,10 @@ cudaError_t launch_plain_bucket_pass(const PassParams<BucketDigit>& p, cudaStrea
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
         attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)max_fitting_pass_smem<Shape>());
+                                        (int)pass_smem_bytes<Shape, BucketDigit>(8));
     });
     if (attr_err != cudaSuccess) return attr_err;
-    const size_t smem = Shape::smem_bytes(p.digit_bits);
+    const size_t smem = pass_smem_bytes<Shape, BucketDigit>(p.digit_bits);
     const size_t grid = std::min<size_t>(p.num_tiles, (size_t)resident_grid(kern, S::kBlock, smem));
     KernelScope scope("bucket_pass", s);
     kern<<<(unsigned)(grid ? grid : 1), S::kBlock, smem, s>>>(p);

@@ -134,6 +134,7 @@ __host__ __device__ __forceinline__ void bucket_level_digit(uint32_t bbits, int 
 // (table[SegDesc::grp]) and the digit is that of partition level `level` for
 // the segment's bucket-id width; for_segment selects them per tile.
 struct BucketDigit {
+    static constexpr bool kStageDigit = true;  // a bucket id costs more than a staged byte: stage it
     const BucketParams* src;
     int shift;
     uint32_t mask;
@@ -167,6 +168,7 @@ struct BucketDigit {
 // bounds of the segmented bucket sort).
 struct BucketDigits {
     static constexpr bool kBytesCapable = false;
+    static constexpr bool kOneDigit = true;
     const BucketParams* src;
     int shift;
     uint32_t mask;

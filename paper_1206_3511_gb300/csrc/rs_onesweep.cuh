@@ -27,6 +27,7 @@ namespace rs {
 
 // Digit of a key for plain LSD radix sort: (key >> shift) & mask.
 struct RadixDigit {
+    static constexpr bool kStageDigit = false;  // the digit is two operations: recompute it when scattering
     int shift;
     uint32_t mask;
     __device__ __forceinline__ void init() {}
@@ -428,7 +429,16 @@ struct PassSmem {
     uint32_t* local;          // [bins] start of each digit inside the staged tile
     uint32_t* delta;          // [bins] segment position minus staged position
     uint32_t* scan;           // [warps + 1] block-scan scratch
+    uint8_t* digs;            // [tile] digit of each staged key (digit functions with kStageDigit)
 };
+
+// Shared memory of a pass: the shape's, plus one byte per key of the tile
+// for digit functions that stage their digit (kStageDigit: a bucket id costs
+// more than a byte stored and loaded again).
+template <typename Shape, typename DigitOp>
+size_t pass_smem_bytes(int digit_bits) {
+    return Shape::smem_bytes(digit_bits) + (DigitOp::kStageDigit ? (size_t)Shape::kTile : 0);
+}
 
 template <typename KeyT, bool VALS, int BLOCK>
 __device__ __forceinline__ PassSmem<KeyT> carve_pass_smem(unsigned char* smem, uint32_t bins, int tile_keys) {
@@ -440,6 +450,7 @@ __device__ __forceinline__ PassSmem<KeyT> carve_pass_smem(unsigned char* smem, u
     sm.local = sm.vals + (VALS ? tile_keys : 0);
     sm.delta = sm.local + bins;
     sm.scan = sm.delta + bins;
+    sm.digs = reinterpret_cast<uint8_t*>(sm.scan + BLOCK / 32 + 4);
     return sm;
 }
 
@@ -469,7 +480,8 @@ __device__ __forceinline__ void scatter_staged(const PassParams<DigitOp>& p, con
         const uint32_t idx = j * BLOCK + threadIdx.x;
         if (FULL || idx < c.tile_n) {
             const KeyT key = sm.keys[idx];
-            const uint32_t pos = sm.delta[op((KeyT)(key - c.key_lo))] + idx;
+            const uint32_t d = DigitOp::kStageDigit ? (uint32_t)sm.digs[idx] : op((KeyT)(key - c.key_lo));
+            const uint32_t pos = sm.delta[d] + idx;
             if (pos < c.seg_n) {
                 c.kout[pos] = XF ? p.xf.from_ordered(key) : key;
                 if (VALS) c.vout[pos] = sm.vals[idx];
@@ -595,6 +607,7 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
             if (pos < (uint32_t)kTile) {
                 sm.keys[pos] = k[i];
                 if (VALS) sm.vals[pos] = v[i];
+                if (DigitOp::kStageDigit) sm.digs[pos] = (uint8_t)(dr[i] >> 16);
             }
         }
     }

@@ -156,14 +156,20 @@ __global__ void __launch_bounds__(512) k_seg_counts(const KeyT* __restrict__ key
             for (uint32_t u = 0; u < kU; ++u) {
                 bad |= check && (x[u] >> (check ? d.bits : 0)) != 0;
                 bad |= !dg.in_range(x[u]);
-                for (int q = 0; q < passes; ++q) atomicAdd(&s_cnt[q * bins + dg(x[u], q)], 1u);
+                if constexpr (Digits::kOneDigit)
+                    atomicAdd(&s_cnt[dg(x[u], 0)], 1u);
+                else
+                    for (int q = 0; q < passes; ++q) atomicAdd(&s_cnt[q * bins + dg(x[u], q)], 1u);
             }
         }
         for (; i < hi; i += blockDim.x) {
             const KeyT x = (KeyT)(__ldcs(kp + i) - klo);
             bad |= check && (x >> (check ? d.bits : 0)) != 0;
             bad |= !dg.in_range(x);
-            for (int q = 0; q < passes; ++q) atomicAdd(&s_cnt[q * bins + dg(x, q)], 1u);
+            if constexpr (Digits::kOneDigit)
+                atomicAdd(&s_cnt[dg(x, 0)], 1u);
+            else
+                for (int q = 0; q < passes; ++q) atomicAdd(&s_cnt[q * bins + dg(x, q)], 1u);
         }
         if (bad && range_hdr) set_device_error(range_hdr, RS_ERR_KEY_RANGE, li);
         __syncthreads();

@@ -71,13 +71,13 @@ cudaError_t launch_seg_pass_shape(const SegPassParams<DigitOp>& sp, size_t grid,
     auto kern = k_onesweep_seg<KeyT, VALS, BLOCK, ITEMS, MINB, DigitOp>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
+    const size_t most = DigitOp::kStageDigit ? pass_smem_bytes<Shape, DigitOp>(8) : max_fitting_pass_smem<Shape>();
     std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)max_fitting_pass_smem<Shape>());
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     });
     if (attr_err != cudaSuccess) return attr_err;
-    const size_t smem = Shape::smem_bytes(sp.base.digit_bits);
-    if (smem > max_fitting_pass_smem<Shape>()) return cudaErrorInvalidValue;
+    const size_t smem = pass_smem_bytes<Shape, DigitOp>(sp.base.digit_bits);
+    if (smem > most) return cudaErrorInvalidValue;
     grid = std::min<size_t>(grid, (size_t)resident_grid(kern, BLOCK, smem));
     KernelScope scope("onesweep_seg_pass", s);
     kern<<<(unsigned)(grid ? grid : 1), BLOCK, smem, s>>>(sp);
