@@ -62,6 +62,10 @@ const Variant kVariants[] = {
     make_variant<uint32_t, false, 256, 26, 4>(),
     make_variant<uint32_t, false, 256, 28, 3>(),
     make_variant<uint32_t, false, 256, 32, 3>(),
+    make_variant<uint32_t, false, 256, 36, 3>(),
+    make_variant<uint32_t, false, 256, 40, 2>(),
+    make_variant<uint32_t, false, 384, 24, 2>(),
+    make_variant<uint32_t, false, 512, 20, 2>(),
     make_variant<uint32_t, false, 256, 18, 4>(),
     make_variant<uint32_t, false, 256, 15, 4>(),
     make_variant<uint32_t, false, 512, 15, 2>(),

@@ -56,6 +56,10 @@ constexpr SegVariant seg_variant() {
 const SegVariant kSegVariants[] = {
     seg_variant<uint32_t, false, 256, 22, 4>(), seg_variant<uint32_t, false, 384, 16, 3>(),
     seg_variant<uint32_t, false, 256, 20, 4>(), seg_variant<uint32_t, false, 256, 24, 4>(),
+    seg_variant<uint32_t, false, 256, 26, 4>(), seg_variant<uint32_t, false, 256, 28, 3>(),
+    seg_variant<uint32_t, false, 256, 32, 3>(), seg_variant<uint32_t, false, 256, 36, 3>(),
+    seg_variant<uint32_t, false, 256, 40, 2>(), seg_variant<uint32_t, false, 384, 24, 2>(),
+    seg_variant<uint32_t, false, 512, 20, 2>(),
     seg_variant<uint32_t, false, 256, 18, 4>(),
     seg_variant<uint32_t, false, 256, 15, 4>(), seg_variant<uint32_t, false, 512, 15, 2>(),
     seg_variant<uint32_t, true, 256, 12, 4>(),  seg_variant<uint32_t, true, 256, 15, 3>(),
