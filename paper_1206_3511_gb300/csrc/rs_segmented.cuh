@@ -274,34 +274,39 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep_seg(SegPassParams<Digi
 constexpr uint32_t kBucketSortMax = 48;
 constexpr uint32_t kLeafKeyBits = 24;
 
+// Rank tables of the shared-memory sort: one per half-warp, room for 9-bit
+// digits (kLocalMaxBins + kSubPad 32-bit words each, as in the scatter pass).
+constexpr uint32_t kLocalMaxBins = 512;
+constexpr uint32_t kLocalTabStride = kLocalMaxBins + kSubPad;
+
 template <typename KeyT, bool VALS, int BLOCK>
 struct LocalSmem {
     static constexpr int kWarps = BLOCK / 32;
     static size_t bytes(int cap) {
-        size_t b = (size_t)(BLOCK / 16) * (256 + kSubPad) * 4;  // rank tables (one per half-warp)
+        size_t b = (size_t)(BLOCK / 16) * (kLocalMaxBins + kSubPad) * 4;  // rank tables (one per half-warp)
         b += 2 * (size_t)cap * sizeof(KeyT);          // key buffers
         if (VALS) b += 2 * (size_t)cap * 4;           // value buffers
-        b += 256 * 4 * 2 + (kWarps + 1 + 3) * 4 + 16; // starts, counts, scan scratch, flags
+        b += kLocalMaxBins * 4 * 2 + (kWarps + 1 + 3) * 4 + 16;  // starts, counts, scan scratch, flags
         b += (size_t)cap;                             // bucket of each staged key (bucket mode)
         return b;
     }
 };
 
-// Rank tables of the shared-memory sort: one per half-warp, 256 + kSubPad
-// 32-bit words each (as in the scatter pass).
-constexpr uint32_t kLocalTabStride = 256 + kSubPad;
 
 // One stable pass of the shared-memory sort: keys (and values) move from
-// (ka, va) to (kb, vb) ordered by digit dfun(key) < 256.  Each half-warp owns
-// a contiguous run of keys and ranks them with subwarp_rank.
+// (ka, va) to (kb, vb) ordered by digit dfun(key) < bins (at most 512).  Each
+// half-warp owns a contiguous run of keys and ranks them with subwarp_rank;
+// table work covers only the `bins` words a pass uses.
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename DFun>
 __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, KeyT* kb, uint32_t* vb, uint32_t m,
-                                           uint32_t* s_tab, uint32_t* s_start, uint32_t* s_cnt, uint32_t* s_scan,
-                                           DFun dfun, uint8_t* s_dig = nullptr) {
+                                           int dbits, uint32_t* s_tab, uint32_t* s_start, uint32_t* s_cnt,
+                                           uint32_t* s_scan, DFun dfun, uint8_t* s_dig = nullptr) {
     constexpr int kSubs = BLOCK / 16;
+    const uint32_t bins = 1u << dbits;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int half = lane >> 4, hl = lane & 15;
-    for (uint32_t i = tid; i < (uint32_t)kSubs * kLocalTabStride; i += BLOCK) s_tab[i] = 0u;
+    for (uint32_t i = tid; i < (uint32_t)kSubs * bins; i += BLOCK)
+        s_tab[(i >> dbits) * kLocalTabStride + (i & (bins - 1u))] = 0u;
     __syncthreads();
     const uint32_t tab = smem_addr(s_tab + (size_t)(2 * warp + half) * kLocalTabStride);
     const uint32_t hbit = 1u << hl, hlt = hbit - 1u, hgt = 0xffffu & ~(hlt | hbit);
@@ -320,7 +325,7 @@ __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, K
         }
     }
     __syncthreads();
-    for (uint32_t d = tid; d < 256; d += BLOCK) {
+    for (uint32_t d = tid; d < bins; d += BLOCK) {
         uint32_t sum = 0;
 #pragma unroll
         for (int s = 0; s < kSubs; ++s) sum += s_tab[(size_t)s * kLocalTabStride + d] >> 16;
@@ -328,8 +333,8 @@ __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, K
         s_start[d] = sum;
     }
     __syncthreads();
-    block_exclusive_scan_smem<BLOCK>(s_start, 256, s_scan);
-    for (uint32_t d = tid; d < 256; d += BLOCK) {
+    block_exclusive_scan_smem<BLOCK>(s_start, (int)bins, s_scan);
+    for (uint32_t d = tid; d < bins; d += BLOCK) {
         uint32_t run = s_start[d];
 #pragma unroll
         for (int s = 0; s < kSubs; ++s) {
@@ -381,8 +386,8 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
     vbuf[0] = reinterpret_cast<uint32_t*>(kbuf[1] + kCap);
     vbuf[1] = vbuf[0] + (VALS ? kCap : 0);
     uint32_t* s_start = vbuf[1] + (VALS ? kCap : 0);
-    uint32_t* s_cnt = s_start + 256;
-    uint32_t* s_scan = s_cnt + 256;
+    uint32_t* s_cnt = s_start + kLocalMaxBins;
+    uint32_t* s_scan = s_cnt + kLocalMaxBins;
     uint32_t* s_flag = s_scan + kWarps + 1;
     uint8_t* s_dig = reinterpret_cast<uint8_t*>(s_flag + 4);
 
@@ -421,8 +426,9 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
             if (threadIdx.x == 0) *s_flag = 0u;
             __syncthreads();
             if (span <= 256) {
-                local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[0], vbuf[0], kbuf[1], vbuf[1], m, s_tab, s_start, s_cnt, s_scan,
-                                                     [&](KeyT k) { return (uint32_t)(bfn.bucket(k) - b_lo); }, s_dig);
+                local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[0], vbuf[0], kbuf[1], vbuf[1], m, 8, s_tab, s_start, s_cnt,
+                                                     s_scan, [&](KeyT k) { return (uint32_t)(bfn.bucket(k) - b_lo); },
+                                                     s_dig);
                 cur = 1;
                 for (uint32_t d = threadIdx.x; d < 256; d += BLOCK)
                     if (s_cnt[d] > kBucketSortMax) *s_flag = 1u;
@@ -462,10 +468,17 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
             __syncthreads();
         }
         if (by_keys) {
-            for (uint32_t shift = 0; shift < seg.bits; shift += 8) {
-                local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1], m, s_tab, s_start,
-                                                     s_cnt, s_scan,
-                                                     [&](KeyT k) { return (uint32_t)((KeyT)(k - klo) >> shift) & 255u; });
+            // the fewest passes of at most 9 bits that cover the segment's
+            // key bits, the bits shared evenly (18 bits: two 9-bit passes
+            // instead of three 8-bit ones)
+            const uint32_t nb = seg.bits;
+            const uint32_t P = nb ? (nb + 8) / 9 : 0;
+            const int dw = P ? (int)((nb + P - 1) / P) : 0;
+            for (uint32_t q = 0, shift = 0; q < P; ++q, shift += (uint32_t)dw) {
+                const uint32_t dmask = (1u << dw) - 1u;
+                local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1], m, dw, s_tab,
+                                                     s_start, s_cnt, s_scan,
+                                                     [&](KeyT k) { return (uint32_t)((KeyT)(k - klo) >> shift) & dmask; });
                 cur ^= 1;
             }
         }
