@@ -50,19 +50,21 @@ constexpr Variant make_variant() {
 
 // Compiled kernel shapes.  The first entry of each (key width, values) group
 // is the default (the fastest measured on GB300 at 100M keys with the
-// half-warp rank tables: u32 keys only 256 x 22, 1.84 ms per sort against
-// 1.93 for 256 x 20 and 1.96 for 384 x 16; u32 with values 256 x 15, 2.78 ms
-// against 3.05 for 256 x 12); only the defaults are also compiled for typed
-// keys.
+// half-warp rank tables: u32 keys only 256 x 36 at 3 blocks/SM, 1.64 ms per
+// sort against 1.66 for 256 x 32, 1.71 for 256 x 26, 1.77 for 256 x 24, 1.84
+// for 256 x 22 and 1.95 for 384 x 16: larger tiles spread the per-tile work
+// and shorten the look-back chain, even with 140 bytes spilled; u32 with
+// values 256 x 15, 2.78 ms against 3.05 for 256 x 12); only the defaults are
+// also compiled for typed keys.
 const Variant kVariants[] = {
-    make_variant<uint32_t, false, 256, 22, 4, true>(),
+    make_variant<uint32_t, false, 256, 36, 3, true>(),
+    make_variant<uint32_t, false, 256, 22, 4>(),
     make_variant<uint32_t, false, 384, 16, 3>(),
     make_variant<uint32_t, false, 256, 20, 4>(),
     make_variant<uint32_t, false, 256, 24, 4>(),
     make_variant<uint32_t, false, 256, 26, 4>(),
     make_variant<uint32_t, false, 256, 28, 3>(),
     make_variant<uint32_t, false, 256, 32, 3>(),
-    make_variant<uint32_t, false, 256, 36, 3>(),
     make_variant<uint32_t, false, 256, 40, 2>(),
     make_variant<uint32_t, false, 384, 24, 2>(),
     make_variant<uint32_t, false, 512, 20, 2>(),
