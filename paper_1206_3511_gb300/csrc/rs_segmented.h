@@ -18,9 +18,9 @@ constexpr int kLocalBlock = 256;
 constexpr int kLocalItems = 16;
 constexpr uint32_t kLocalCap = kLocalBlock * kLocalItems;
 
-#ifndef RS_BUCKET_BLOCK  // u32 keys-only bucket partition passes: 384 x 12, 3 blocks/SM
-#define RS_BUCKET_BLOCK 384
-#define RS_BUCKET_ITEMS 12
+#ifndef RS_BUCKET_BLOCK  // u32 keys-only bucket partition passes: 256 x 28, 3 blocks/SM
+#define RS_BUCKET_BLOCK 256
+#define RS_BUCKET_ITEMS 28
 #define RS_BUCKET_MINB 3
 #endif
 
@@ -46,9 +46,10 @@ struct SegShape<uint64_t, true> {
 
 // Kernel shapes of the bucket sort's partition passes.  Their digit carries
 // the bucket parameters (and computes the bucket id of every key twice),
-// which takes registers the radix passes spend on keys: the u32 keys-only
-// radix shape (256 x 22) spills 80 bytes with it, so the bucket passes take
-// a shape that holds it without spilling.
+// which takes registers the radix passes spend on keys, so they have their
+// own shape.  Measured at 100M uniform u32 keys (whole bucket sort): 256 x 28
+// 2.74 ms, 256 x 32 2.75, 384 x 18 2.81, 384 x 12 2.93 (the only one of them
+// without a spill); larger tiles win as in the radix passes.
 template <typename KeyT, bool VALS>
 struct BucketShape : SegShape<KeyT, VALS> {};
 template <>
