@@ -49,13 +49,16 @@ constexpr Variant make_variant() {
 }
 
 // Compiled kernel shapes.  The first entry of each (key width, values) group
-// is the default (the fastest measured on GB300 at 100M keys with the
-// half-warp rank tables: u32 keys only 256 x 36 at 3 blocks/SM, 1.64 ms per
-// sort against 1.66 for 256 x 32, 1.71 for 256 x 26, 1.77 for 256 x 24, 1.84
-// for 256 x 22 and 1.95 for 384 x 16: larger tiles spread the per-tile work
-// and shorten the look-back chain, even with 140 bytes spilled; u32 with
-// values 256 x 15, 2.78 ms against 3.05 for 256 x 12); only the defaults are
-// also compiled for typed keys.
+// is the default, the fastest measured on GB300 at 100M keys with the
+// half-warp rank tables and packed ranks:
+//   u32 keys only   256 x 36 (3 blocks/SM)  1.57 ms per sort; 256 x 32 1.63,
+//                   256 x 26 1.66, 256 x 40 1.72, 256 x 24 1.74, 256 x 22 1.80,
+//                   384 x 16 1.91 (larger tiles spread the per-tile work and
+//                   shorten the look-back chain, even with 84 bytes spilled)
+//   u32 + values    256 x 20 (3 blocks/SM)  2.40 ms; 256 x 18 2.52, 256 x 15 2.78
+//   u64 keys only   384 x 16 (2 blocks/SM)  4.89 ms; 384 x 12 5.05, 256 x 16 5.05
+//   u64 + values    384 x 12 (2 blocks/SM)  6.60 ms; 256 x 12 6.97, 384 x 10 7.21
+// Only the defaults are also compiled for typed keys.
 const Variant kVariants[] = {
     make_variant<uint32_t, false, 256, 36, 3, true>(),
     make_variant<uint32_t, false, 256, 22, 4>(),
@@ -71,18 +74,25 @@ const Variant kVariants[] = {
     make_variant<uint32_t, false, 256, 18, 4>(),
     make_variant<uint32_t, false, 256, 15, 4>(),
     make_variant<uint32_t, false, 512, 15, 2>(),
-    make_variant<uint32_t, true, 256, 15, 3, true>(),
+    make_variant<uint32_t, true, 256, 20, 3, true>(),
+    make_variant<uint32_t, true, 256, 15, 3>(),
     make_variant<uint32_t, true, 256, 12, 4>(),
-    // u64 defaults: 384 x 12 keys only (5.59 ms at 100M 64-bit keys against
-    // 5.77 for 256 x 12), 384 x 10 with values (7.35 ms against 8.02)
-    make_variant<uint64_t, false, 384, 12, 3, true>(),
+    make_variant<uint32_t, true, 256, 18, 3>(),
+    make_variant<uint32_t, true, 256, 24, 2>(),
+    make_variant<uint64_t, false, 384, 16, 2, true>(),
+    make_variant<uint64_t, false, 384, 12, 3>(),
     make_variant<uint64_t, false, 256, 12, 4>(),
     make_variant<uint64_t, false, 256, 9, 4>(),
     make_variant<uint64_t, false, 384, 10, 3>(),
-    make_variant<uint64_t, true, 384, 10, 2, true>(),
+    make_variant<uint64_t, false, 256, 16, 3>(),
+    make_variant<uint64_t, false, 256, 20, 2>(),
+    make_variant<uint64_t, true, 384, 12, 2, true>(),
+    make_variant<uint64_t, true, 384, 10, 2>(),
     make_variant<uint64_t, true, 256, 10, 3>(),
     make_variant<uint64_t, true, 256, 8, 4>(),
     make_variant<uint64_t, true, 384, 8, 3>(),
+    make_variant<uint64_t, true, 256, 12, 3>(),
+    make_variant<uint64_t, true, 256, 14, 2>(),
 };
 // digit widths offered to an autotuner for every kernel shape
 constexpr int kTuneDigitBits[] = {8, 4, 5, 6, 7, 9, 10, 11};

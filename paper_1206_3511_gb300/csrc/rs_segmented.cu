@@ -63,10 +63,16 @@ const SegVariant kSegVariants[] = {
     seg_variant<uint32_t, false, 256, 18, 4>(),
     seg_variant<uint32_t, false, 256, 15, 4>(), seg_variant<uint32_t, false, 512, 15, 2>(),
     seg_variant<uint32_t, true, 256, 12, 4>(),  seg_variant<uint32_t, true, 256, 15, 3>(),
+    seg_variant<uint32_t, true, 256, 18, 3>(),  seg_variant<uint32_t, true, 256, 20, 3>(),
+    seg_variant<uint32_t, true, 256, 24, 2>(),
     seg_variant<uint64_t, false, 256, 12, 4>(), seg_variant<uint64_t, false, 256, 9, 4>(),
     seg_variant<uint64_t, false, 384, 12, 3>(), seg_variant<uint64_t, false, 384, 10, 3>(),
+    seg_variant<uint64_t, false, 256, 16, 3>(), seg_variant<uint64_t, false, 256, 20, 2>(),
+    seg_variant<uint64_t, false, 384, 16, 2>(),
     seg_variant<uint64_t, true, 256, 10, 3>(),  seg_variant<uint64_t, true, 256, 8, 4>(),
     seg_variant<uint64_t, true, 384, 10, 2>(),  seg_variant<uint64_t, true, 384, 8, 3>(),
+    seg_variant<uint64_t, true, 256, 12, 3>(),  seg_variant<uint64_t, true, 256, 14, 2>(),
+    seg_variant<uint64_t, true, 384, 12, 2>(),
 };
 
 const SegVariant* seg_variant_at(int key_bytes, bool vals, int i) {

@@ -62,7 +62,7 @@ def test_host_side_queries_need_no_gpu(lib):
     # small u32 keys-only sorts take the larger-tile shape; other key types do not
     assert _lib.rs_default_config(4, 0, 10**6).as_tuple() == (8, 512, 15)
     assert _lib.rs_default_config(4, 0, (1 << 22) + 1).as_tuple() == (8, 256, 36)
-    assert _lib.rs_default_config(4, 1, 10**6).as_tuple() == (8, 256, 15)
+    assert _lib.rs_default_config(4, 1, 10**6).as_tuple() == (8, 256, 20)
     assert _lib.rs_config_count(4, 0) >= 8
     seen = {_lib.rs_config_get(4, 0, i).as_tuple() for i in range(_lib.rs_config_count(4, 0))}
     assert len(seen) == _lib.rs_config_count(4, 0)
