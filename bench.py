@@ -1438,11 +1438,11 @@ def run_served(args):
     big = int(sizes.max())
     # resident inputs: one array per (kind, distribution); request i reads a prefix
     src_k, src_v = {}, None
-    for d in sorted(set(dists.tolist())):
+    for d in sorted(set(dists.tolist())):  # built on the device (same bits as the numpy forms)
         if np.any((dists == d) & (kinds == 0)):
-            src_k[(0, d)] = torch.from_numpy(synth.keys_u32(big, d, seed=rank).view(np.int32)).to(dev)
+            src_k[(0, d)] = synth.keys_u32_torch(big, d, seed=rank, device=dev)
         if np.any((dists == d) & (kinds == 1)):
-            src_k[(1, d)] = torch.from_numpy(synth.keys_u64_shaped(big, d, seed=rank).view(np.int64)).to(dev)
+            src_k[(1, d)] = synth.keys_u64_shaped_torch(big, d, seed=rank, device=dev)
     if np.any(kinds == 1):
         src_v = torch.arange(big, dtype=torch.int32, device=dev)
     # outputs: a circular arena; request i's keys (and values) go at the head,
