@@ -144,29 +144,15 @@ struct CountParams {
 
 constexpr int kCountBlock = 512;
 constexpr int kCountVecIters = 8;  // 16-byte loads per thread per chunk
-// Column copies of each counter in the byte-digit kernel: counter (q, d)
-// has NCOL copies, one word each, and lane l adds to copy l mod NCOL.  Lanes
-// with distinct copies fall in distinct banks, so only lanes NCOL apart can
-// meet: with 16 copies (at most four digits) a conflict has at most two ways
-// and with 8 copies (up to eight digits) four, against about 3.5 on average
-// for 32 lanes on one copy.  Either way the copies take 64 KB, so two blocks
-// of 512 threads still fit per SM.
-constexpr int kCountColsBytes = 64 * 1024;
-__host__ __device__ constexpr int count_cols(int passes) { return passes <= 4 ? 16 : (passes <= 8 ? 8 : 0); }
 
 // BYTES: digit q is byte q of dg.order(k) (8-bit digits from bit 0, the
 // usual case): the key is mapped once and every digit is a fixed byte.
-template <typename KeyT, typename Digits, bool BYTES, int NCOL = 0>
+template <typename KeyT, typename Digits, bool BYTES>
 __device__ __forceinline__ void count_key(uint32_t* s_cnt, KeyT k, const Digits& dg, int P, uint32_t bins,
-                                          bool& bad, uint32_t col = 0) {
+                                          bool& bad) {
     bad |= !dg.in_range(k);
     if constexpr (Digits::kOneDigit) {  // one digit per key (the bucket sort's partition digit)
         atomicAdd(&s_cnt[dg(k, 0)], 1u);
-    } else if (NCOL > 0) {
-        const KeyT o = dg.order(k);
-#pragma unroll
-        for (int q = 0; q < (int)sizeof(KeyT); ++q)
-            if (q < P) atomicAdd(&s_cnt[((q * 256 + (uint32_t)((o >> (8 * q)) & 0xffu)) * NCOL) + col], 1u);
     } else if (BYTES) {
         const KeyT o = dg.order(k);
 #pragma unroll
@@ -177,20 +163,16 @@ __device__ __forceinline__ void count_key(uint32_t* s_cnt, KeyT k, const Digits&
     }
 }
 
-// NCOL > 0: the byte-digit kernel with NCOL column copies of every counter
-// (NCOL = count_cols(passes)).
-template <typename KeyT, typename Digits, bool BYTES = false, int NCOL = 0>
+template <typename KeyT, typename Digits, bool BYTES = false>
 __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Digits dg) {
-    extern __shared__ uint32_t s_cnt[];  // [P][bins] (x NCOL copies), then kCountBlock/32+1 scan words
+    extern __shared__ uint32_t s_cnt[];  // [P][bins], then kCountBlock/32+1 scan words
     __shared__ uint32_t s_last;
     const uint32_t bins = p.bins;
     const int ncnt = p.passes * (int)bins;
-    const int nwords = NCOL > 0 ? ncnt * NCOL : ncnt;
-    uint32_t* s_scan = s_cnt + nwords;
+    uint32_t* s_scan = s_cnt + ncnt;
     const int tid = threadIdx.x;
-    const uint32_t col = NCOL > 0 ? ((uint32_t)tid & (NCOL - 1)) : 0u;
     dg.init();
-    for (int i = tid; i < nwords; i += kCountBlock) s_cnt[i] = 0;
+    for (int i = tid; i < ncnt; i += kCountBlock) s_cnt[i] = 0;
     for (size_t i = (size_t)blockIdx.x * kCountBlock + tid; i < p.zero_words; i += (size_t)gridDim.x * kCountBlock)
         p.zero_ptr[i] = 0;
     __syncthreads();
@@ -214,11 +196,11 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Dig
     // (a thread stops checking at its first inversion: on unordered keys
     // that is its first few keys)
     for (size_t i = gtid; i < head; i += gthreads) {
-        count_key<KeyT, Digits, BYTES, NCOL>(s_cnt, keys[i], dg, p.passes, bins, bad, col);
+        count_key<KeyT, Digits, BYTES>(s_cnt, keys[i], dg, p.passes, bins, bad);
         if (check && !inv && i + 1 < p.n) inv = dg.order(keys[i + 1]) < dg.order(keys[i]);
     }
     for (size_t i = tail0 + gtid; i < p.n; i += gthreads) {
-        count_key<KeyT, Digits, BYTES, NCOL>(s_cnt, keys[i], dg, p.passes, bins, bad, col);
+        count_key<KeyT, Digits, BYTES>(s_cnt, keys[i], dg, p.passes, bins, bad);
         if (check && !inv && i + 1 < p.n) inv = dg.order(keys[i + 1]) < dg.order(keys[i]);
     }
     const uint4* vec = reinterpret_cast<const uint4*>(keys + head);
@@ -236,7 +218,7 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Dig
             if (idx < nvec) {
                 const KeyT* kk = reinterpret_cast<const KeyT*>(&v[j]);
 #pragma unroll
-                for (int e = 0; e < kPerVec; ++e) count_key<KeyT, Digits, BYTES, NCOL>(s_cnt, kk[e], dg, p.passes, bins, bad, col);
+                for (int e = 0; e < kPerVec; ++e) count_key<KeyT, Digits, BYTES>(s_cnt, kk[e], dg, p.passes, bins, bad);
                 if (check && !inv) {
 #pragma unroll
                     for (int e = 0; e + 1 < kPerVec; ++e) inv |= dg.order(kk[e + 1]) < dg.order(kk[e]);
@@ -248,18 +230,8 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Dig
     }
     if (bad) set_device_error(p.hdr, RS_ERR_KEY_RANGE, blockIdx.x);
     if (__syncthreads_or(inv) && tid == 0) atomicOr(p.unsorted, 1u);
-    if (NCOL > 0) {
-        __syncthreads();
-        for (int i = tid; i < ncnt; i += kCountBlock) {
-            uint32_t sum = 0;
-#pragma unroll
-            for (int c = 0; c < NCOL; ++c) sum += s_cnt[i * NCOL + ((c + i) & (NCOL - 1))];
-            if (sum) atomicAdd(&p.counts[i], sum);
-        }
-    } else {
-        for (int i = tid; i < ncnt; i += kCountBlock)
-            if (s_cnt[i]) atomicAdd(&p.counts[i], s_cnt[i]);
-    }
+    for (int i = tid; i < ncnt; i += kCountBlock)
+        if (s_cnt[i]) atomicAdd(&p.counts[i], s_cnt[i]);
 
     if (!p.scan) return;
     // the last block to finish turns the counts into exclusive prefixes
@@ -289,14 +261,13 @@ __global__ void __launch_bounds__(kCountBlock) k_digit_counts(CountParams p, Dig
     }
 }
 
-inline size_t count_smem_bytes(int passes, int digit_bits, int ncol = 0) {
-    return ((size_t)passes * ((size_t)1 << digit_bits) * (ncol > 0 ? ncol : 1) + kCountBlock / 32 + 1) *
-           sizeof(uint32_t);
+inline size_t count_smem_bytes(int passes, int digit_bits) {
+    return ((size_t)passes * ((size_t)1 << digit_bits) + kCountBlock / 32 + 1) * sizeof(uint32_t);
 }
 
 // Largest digit-count shared memory over every digit width and 64-bit keys.
 inline size_t max_count_smem_bytes() {
-    size_t best = kCountColsBytes + (kCountBlock / 32 + 1) * sizeof(uint32_t);
+    size_t best = 0;
     for (int D = kMinDigitBits; D <= kMaxDigitBits; ++D) {
         size_t b = count_smem_bytes((64 + D - 1) / D, D);
         if (b > best) best = b;

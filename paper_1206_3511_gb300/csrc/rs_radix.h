@@ -74,9 +74,9 @@ rs_status enqueue_order_check(int key_bytes, const void* keys, size_t n, const K
 size_t count_grid(size_t n);
 
 // Launch the digit-count kernel with a digit functor.
-template <typename KeyT, typename Digits, bool BYTES, int NCOL = 0>
+template <typename KeyT, typename Digits, bool BYTES>
 cudaError_t launch_counts_as(const CountParams& p, const Digits& dg, size_t grid, cudaStream_t s) {
-    auto kern = k_digit_counts<KeyT, Digits, BYTES, NCOL>;
+    auto kern = k_digit_counts<KeyT, Digits, BYTES>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -84,23 +84,16 @@ cudaError_t launch_counts_as(const CountParams& p, const Digits& dg, size_t grid
                                         (int)max_count_smem_bytes());
     });
     if (attr_err != cudaSuccess) return attr_err;
-    const size_t smem = ((size_t)p.passes * p.bins * (NCOL > 0 ? NCOL : 1) + kCountBlock / 32 + 1) * 4;
     KernelScope scope("digit_counts", s);
-    kern<<<(unsigned)grid, kCountBlock, smem, s>>>(p, dg);
+    kern<<<(unsigned)grid, kCountBlock, (p.passes * p.bins + kCountBlock / 32 + 1) * 4, s>>>(p, dg);
     return cudaGetLastError();
 }
 
-// 8-bit digits from bit 0 take the kernel that reads them as bytes, with
-// column copies of the counters (16 for up to four digits, 8 for up to
-// eight).
+// 8-bit digits from bit 0 take the kernel that reads them as bytes.
 template <typename KeyT, typename Digits>
 cudaError_t launch_counts(const CountParams& p, const Digits& dg, size_t grid, cudaStream_t s) {
     if constexpr (Digits::kBytesCapable) {
-        if (dg.byte_digits()) {
-            if (count_cols(p.passes) == 16) return launch_counts_as<KeyT, Digits, true, 16>(p, dg, grid, s);
-            if (count_cols(p.passes) == 8) return launch_counts_as<KeyT, Digits, true, 8>(p, dg, grid, s);
-            return launch_counts_as<KeyT, Digits, true>(p, dg, grid, s);
-        }
+        if (dg.byte_digits()) return launch_counts_as<KeyT, Digits, true>(p, dg, grid, s);
     }
     return launch_counts_as<KeyT, Digits, false>(p, dg, grid, s);
 }
