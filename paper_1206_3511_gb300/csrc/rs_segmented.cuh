@@ -402,12 +402,30 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
         const KeyT* kin = static_cast<const KeyT*>(lp.keys_in) + seg.start;
         bool bad = false;
         const bool xf = lp.xf.active();
-        for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
-            const KeyT k = xf ? lp.xf.to_ordered(kin[i]) : kin[i];
-            kbuf[0][i] = k;
-            if (VALS) vbuf[0][i] = lp.vals_in[seg.start + i];
-            bad |= seg.bits < 8 * sizeof(KeyT) && ((KeyT)(k - klo) >> seg.bits) != 0;
-            bad |= !bfn.in_range(k);
+        {
+            // every load of the thread is issued before the first store, so
+            // that a segment costs one memory latency, not ITEMS of them
+            KeyT kr[ITEMS];
+            uint32_t vr[VALS ? ITEMS : 1];
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t idx = threadIdx.x + (uint32_t)i * BLOCK;
+                if (idx < m) {
+                    kr[i] = kin[idx];
+                    if (VALS) vr[i] = lp.vals_in[seg.start + idx];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t idx = threadIdx.x + (uint32_t)i * BLOCK;
+                if (idx < m) {
+                    const KeyT k = xf ? lp.xf.to_ordered(kr[i]) : kr[i];
+                    kbuf[0][idx] = k;
+                    if (VALS) vbuf[0][idx] = vr[i];
+                    bad |= seg.bits < 8 * sizeof(KeyT) && ((KeyT)(k - klo) >> seg.bits) != 0;
+                    bad |= !bfn.in_range(k);
+                }
+            }
         }
         if (bad && lp.hdr) set_device_error(lp.hdr, RS_ERR_KEY_RANGE, si);
         // keys already in nondecreasing order (a sorted run) are their own
