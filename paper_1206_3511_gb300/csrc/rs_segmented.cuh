@@ -294,41 +294,51 @@ struct LocalSmem {
 
 
 // One stable pass of the shared-memory sort: keys (and values) move from
-// (ka, va) to (kb, vb) ordered by digit dfun(key) < bins (at most 512).  Each
-// half-warp owns a contiguous run of keys and ranks them with subwarp_rank;
-// table work covers only the `bins` words a pass uses.
+// (ka, va) to (kb, vb) ordered by digit dfun(key) < bins (at most 512).
+// Each half-warp in use owns a contiguous run of 16 * ITEMS keys and ranks
+// them with subwarp_rank; only the warps whose runs reach into the segment
+// take part (a short segment leaves the other warps idle rather than
+// spreading a few keys over every thread, whose empty items would still
+// issue their instructions), and table work covers only the tables and
+// the `bins` words in use.
 template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename DFun>
 __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, KeyT* kb, uint32_t* vb, uint32_t m,
                                            int dbits, uint32_t* s_tab, uint32_t* s_start, uint32_t* s_cnt,
                                            uint32_t* s_scan, DFun dfun, uint8_t* s_dig = nullptr) {
-    constexpr int kSubs = BLOCK / 16;
+    constexpr uint32_t kRun = 16u * ITEMS;  // keys per half-warp
     const uint32_t bins = 1u << dbits;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int half = lane >> 4, hl = lane & 15;
-    for (uint32_t i = tid; i < (uint32_t)kSubs * bins; i += BLOCK)
+    const uint32_t nsub = 2u * ((m + 2u * kRun - 1u) / (2u * kRun));  // half-warps in use, whole warps
+    for (uint32_t i = tid; i < nsub * bins; i += BLOCK)
         s_tab[(i >> dbits) * kLocalTabStride + (i & (bins - 1u))] = 0u;
     __syncthreads();
-    const uint32_t tab = smem_addr(s_tab + (size_t)(2 * warp + half) * kLocalTabStride);
+    const uint32_t sub = 2u * (uint32_t)warp + (uint32_t)half;
+    const bool active = 2u * (uint32_t)warp < nsub;  // the same for the whole warp
+    const uint32_t tab = smem_addr(s_tab + (size_t)sub * kLocalTabStride);
     const uint32_t hbit = 1u << hl, hlt = hbit - 1u, hgt = 0xffffu & ~(hlt | hbit);
-    // each half-warp owns a contiguous run of `used` items of 16 keys, just
-    // enough to cover the m keys of the segment
-    const uint32_t used = (m + BLOCK - 1) / BLOCK;
-    const uint32_t hofs = (uint32_t)(2 * warp + half) * (used * 16) + hl;
+    const uint32_t hofs = sub * kRun + (uint32_t)hl;
+    // 32-bit keys stay in registers from ranking to scattering; 64-bit keys
+    // are read again (holding them would spill)
+    constexpr bool kKeep = sizeof(KeyT) == 4;
     uint32_t dr[ITEMS];
+    KeyT kr[kKeep ? ITEMS : 1];
+    if (active) {
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        if ((uint32_t)i < used) {
-            const uint32_t idx = hofs + i * 16;
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t idx = hofs + (uint32_t)i * 16u;
             const bool ok = idx < m;
-            const uint32_t d = ok ? dfun(ka[idx]) : 0u;
+            const KeyT k = ok ? ka[idx] : (KeyT)0;
+            if (kKeep) kr[kKeep ? i : 0] = k;
+            const uint32_t d = ok ? dfun(k) : 0u;
             dr[i] = (d << 16) | subwarp_rank<false>(tab, d, ok, hbit, hlt, hgt);
         }
     }
     __syncthreads();
     for (uint32_t d = tid; d < bins; d += BLOCK) {
         uint32_t sum = 0;
-#pragma unroll
-        for (int s = 0; s < kSubs; ++s) sum += s_tab[(size_t)s * kLocalTabStride + d] >> 16;
+#pragma unroll 4
+        for (uint32_t s = 0; s < nsub; ++s) sum += s_tab[(size_t)s * kLocalTabStride + d] >> 16;
         s_cnt[d] = sum;
         s_start[d] = sum;
     }
@@ -336,8 +346,8 @@ __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, K
     block_exclusive_scan_smem<BLOCK>(s_start, (int)bins, s_scan);
     for (uint32_t d = tid; d < bins; d += BLOCK) {
         uint32_t run = s_start[d];
-#pragma unroll
-        for (int s = 0; s < kSubs; ++s) {
+#pragma unroll 4
+        for (uint32_t s = 0; s < nsub; ++s) {
             uint32_t* e = s_tab + (size_t)s * kLocalTabStride + d;
             const uint32_t cnt = *e >> 16;
             *e = run;
@@ -345,15 +355,17 @@ __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, K
         }
     }
     __syncthreads();
+    if (active) {
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const uint32_t idx = hofs + i * 16;
-        if ((uint32_t)i < used && idx < m) {
-            const uint32_t pos = ld_shared_u32(tab + 4u * (dr[i] >> 16)) + (dr[i] & 0xffffu);
-            if (pos < m) {
-                kb[pos] = ka[idx];
-                if (VALS) vb[pos] = va[idx];
-                if (s_dig) s_dig[pos] = (uint8_t)(dr[i] >> 16);
+        for (int i = 0; i < ITEMS; ++i) {
+            const uint32_t idx = hofs + (uint32_t)i * 16u;
+            if (idx < m) {
+                const uint32_t pos = ld_shared_u32(tab + 4u * (dr[i] >> 16)) + (dr[i] & 0xffffu);
+                if (pos < m) {
+                    kb[pos] = kKeep ? kr[kKeep ? i : 0] : ka[idx];
+                    if (VALS) vb[pos] = va[idx];
+                    if (s_dig) s_dig[pos] = (uint8_t)(dr[i] >> 16);
+                }
             }
         }
     }
@@ -402,30 +414,12 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
         const KeyT* kin = static_cast<const KeyT*>(lp.keys_in) + seg.start;
         bool bad = false;
         const bool xf = lp.xf.active();
-        {
-            // every load of the thread is issued before the first store, so
-            // that a segment costs one memory latency, not ITEMS of them
-            KeyT kr[ITEMS];
-            uint32_t vr[VALS ? ITEMS : 1];
-#pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                const uint32_t idx = threadIdx.x + (uint32_t)i * BLOCK;
-                if (idx < m) {
-                    kr[i] = kin[idx];
-                    if (VALS) vr[i] = lp.vals_in[seg.start + idx];
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < ITEMS; ++i) {
-                const uint32_t idx = threadIdx.x + (uint32_t)i * BLOCK;
-                if (idx < m) {
-                    const KeyT k = xf ? lp.xf.to_ordered(kr[i]) : kr[i];
-                    kbuf[0][idx] = k;
-                    if (VALS) vbuf[0][idx] = vr[i];
-                    bad |= seg.bits < 8 * sizeof(KeyT) && ((KeyT)(k - klo) >> seg.bits) != 0;
-                    bad |= !bfn.in_range(k);
-                }
-            }
+        for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
+            const KeyT k = xf ? lp.xf.to_ordered(kin[i]) : kin[i];
+            kbuf[0][i] = k;
+            if (VALS) vbuf[0][i] = lp.vals_in[seg.start + i];
+            bad |= seg.bits < 8 * sizeof(KeyT) && ((KeyT)(k - klo) >> seg.bits) != 0;
+            bad |= !bfn.in_range(k);
         }
         if (bad && lp.hdr) set_device_error(lp.hdr, RS_ERR_KEY_RANGE, si);
         // keys already in nondecreasing order (a sorted run) are their own
