@@ -372,6 +372,25 @@ __device__ __forceinline__ void local_pass(const KeyT* ka, const uint32_t* va, K
     __syncthreads();
 }
 
+// Items per lane of the shared-memory sort's passes over segments of at
+// most BLOCK * RS_LOCAL_FIT_ITEMS keys (longer segments take ITEMS): a
+// short segment is then spread over more warps, whose rank chains run side
+// by side instead of one after another.  One such variant besides ITEMS
+// keeps every instantiation free of spills.
+#ifndef RS_LOCAL_FIT_ITEMS
+#define RS_LOCAL_FIT_ITEMS 4
+#endif
+
+template <typename KeyT, bool VALS, int BLOCK, int ITEMS, typename DFun>
+__device__ __forceinline__ void local_pass_fit(const KeyT* ka, const uint32_t* va, KeyT* kb, uint32_t* vb, uint32_t m,
+                                               int dbits, uint32_t* s_tab, uint32_t* s_start, uint32_t* s_cnt,
+                                               uint32_t* s_scan, DFun dfun, uint8_t* s_dig = nullptr) {
+    if (ITEMS > RS_LOCAL_FIT_ITEMS && m <= (uint32_t)BLOCK * RS_LOCAL_FIT_ITEMS)
+        local_pass<KeyT, VALS, BLOCK, RS_LOCAL_FIT_ITEMS>(ka, va, kb, vb, m, dbits, s_tab, s_start, s_cnt, s_scan, dfun, s_dig);
+    else
+        local_pass<KeyT, VALS, BLOCK, ITEMS>(ka, va, kb, vb, m, dbits, s_tab, s_start, s_cnt, s_scan, dfun, s_dig);
+}
+
 struct LocalParams {
     const void* keys_in;
     void* keys_out;
@@ -438,9 +457,9 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
             if (threadIdx.x == 0) *s_flag = 0u;
             __syncthreads();
             if (span <= 256) {
-                local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[0], vbuf[0], kbuf[1], vbuf[1], m, 8, s_tab, s_start, s_cnt,
-                                                     s_scan, [&](KeyT k) { return (uint32_t)(bfn.bucket(k) - b_lo); },
-                                                     s_dig);
+                local_pass_fit<KeyT, VALS, BLOCK, ITEMS>(
+                    kbuf[0], vbuf[0], kbuf[1], vbuf[1], m, 8, s_tab, s_start, s_cnt, s_scan,
+                    [&](KeyT k) { return (uint32_t)(bfn.bucket(k) - b_lo); }, s_dig);
                 cur = 1;
                 for (uint32_t d = threadIdx.x; d < 256; d += BLOCK)
                     if (s_cnt[d] > kBucketSortMax) *s_flag = 1u;
@@ -488,9 +507,9 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
             const int dw = P ? (int)((nb + P - 1) / P) : 0;
             for (uint32_t q = 0, shift = 0; q < P; ++q, shift += (uint32_t)dw) {
                 const uint32_t dmask = (1u << dw) - 1u;
-                local_pass<KeyT, VALS, BLOCK, ITEMS>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1], m, dw, s_tab,
-                                                     s_start, s_cnt, s_scan,
-                                                     [&](KeyT k) { return (uint32_t)((KeyT)(k - klo) >> shift) & dmask; });
+                local_pass_fit<KeyT, VALS, BLOCK, ITEMS>(
+                    kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1], m, dw, s_tab, s_start, s_cnt, s_scan,
+                    [&](KeyT k) { return (uint32_t)((KeyT)(k - klo) >> shift) & dmask; });
                 cur ^= 1;
             }
         }
