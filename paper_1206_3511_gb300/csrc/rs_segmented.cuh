@@ -433,10 +433,20 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
         const KeyT* kin = static_cast<const KeyT*>(lp.keys_in) + seg.start;
         bool bad = false;
         const bool xf = lp.xf.active();
+        // the segment comes in by asynchronous copies, all of a thread's in
+        // flight at once (one memory latency per segment, no registers)
         for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
-            const KeyT k = xf ? lp.xf.to_ordered(kin[i]) : kin[i];
-            kbuf[0][i] = k;
-            if (VALS) vbuf[0][i] = lp.vals_in[seg.start + i];
+            cp_async_word<sizeof(KeyT)>(&kbuf[0][i], kin + i);
+            if (VALS) cp_async_word<4>(&vbuf[0][i], lp.vals_in + seg.start + i);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < m; i += BLOCK) {
+            KeyT k = kbuf[0][i];
+            if (xf) {
+                k = lp.xf.to_ordered(k);
+                kbuf[0][i] = k;
+            }
             bad |= seg.bits < 8 * sizeof(KeyT) && ((KeyT)(k - klo) >> seg.bits) != 0;
             bad |= !bfn.in_range(k);
         }
@@ -444,7 +454,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
         // keys already in nondecreasing order (a sorted run) are their own
         // stable sort: nothing to rank or move.  On unsorted keys nearly every
         // thread stops at its first pair.
-        __syncthreads();
+        if (xf) __syncthreads();
         bool in_order = true;
         for (uint32_t i = threadIdx.x; i + 1 < m && in_order; i += BLOCK) in_order = !(kbuf[0][i + 1] < kbuf[0][i]);
         const bool already_sorted = __syncthreads_and(in_order) != 0;
