@@ -57,17 +57,6 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Asynchronous copy of one 4- or 8-byte word from global to shared memory
-// (no register holds it, so a thread can have all its copies in flight);
-// cp_async_wait_all waits for all of the thread's copies.
-template <int BYTES>
-__device__ __forceinline__ void cp_async_word(void* smem, const void* gmem) {
-    static_assert(BYTES == 4 || BYTES == 8, "cp.async of 4 or 8 bytes");
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(smem)), "l"(gmem), "n"(BYTES)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 __device__ __forceinline__ void red_or_shared_if(uint32_t addr, uint32_t v, bool pred) {
     asm volatile(
         "{ .reg .pred p; setp.ne.u32 p, %2, 0; @p red.shared.or.b32 [%0], %1; }" ::"r"(addr), "r"(v),

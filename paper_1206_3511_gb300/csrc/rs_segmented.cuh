@@ -274,6 +274,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep_seg(SegPassParams<Digi
 constexpr uint32_t kBucketSortMax = 48;
 constexpr uint32_t kLeafKeyBits = 24;
 
+// Asynchronous copy of one 4- or 8-byte word from global to shared memory
+// (no register holds it, so a thread can have all its copies in flight);
+// cp_async_wait_all waits for all of the thread's copies.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_word(void* smem, const void* gmem) {
+    static_assert(BYTES == 4 || BYTES == 8, "cp.async of 4 or 8 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(smem)), "l"(gmem), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Rank tables of the shared-memory sort: one per half-warp, room for 9-bit
 // digits (kLocalMaxBins + kSubPad 32-bit words each, as in the scatter pass).
 constexpr uint32_t kLocalMaxBins = 512;
