@@ -493,21 +493,43 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
                     // order, which the counting pass kept) -- the comparisons
                     // of insertion sort (Algorithm 1), made for all keys at
                     // once instead of one bucket per thread
+                    // When the run's key bits leave room for 12 more, each key
+                    // is first rewritten in place as ((key - lo) << 12) | its
+                    // position, which orders keys the stable way in one
+                    // comparison: then a key's rank is the number of its
+                    // bucket's words below its own (ties cannot occur), and
+                    // the key comes back as (word >> 12) + lo.
+                    const bool packed = seg.bits + 12u <= 8u * sizeof(KeyT);
+                    if (packed) {
+                        for (uint32_t j = threadIdx.x; j < m; j += BLOCK)
+                            kbuf[1][j] = (KeyT)(((KeyT)(kbuf[1][j] - klo) << 12) | (KeyT)j);
+                        __syncthreads();
+                    }
                     for (uint32_t j = threadIdx.x; j < m; j += BLOCK) {
                         const KeyT key = kbuf[1][j];
                         const uint32_t d = s_dig[j];
                         const uint32_t lo = s_start[d], hi = lo + s_cnt[d];
                         uint32_t r = 0, q = lo;
-                        for (; q + 4 <= hi; q += 4) {  // four independent reads per step
-                            const KeyT o0 = kbuf[1][q], o1 = kbuf[1][q + 1], o2 = kbuf[1][q + 2], o3 = kbuf[1][q + 3];
-                            r += ((o0 < key) | ((o0 == key) & (q < j))) + ((o1 < key) | ((o1 == key) & (q + 1 < j))) +
-                                 ((o2 < key) | ((o2 == key) & (q + 2 < j))) + ((o3 < key) | ((o3 == key) & (q + 3 < j)));
+                        if (packed) {
+                            for (; q + 4 <= hi; q += 4)  // four independent reads per step
+                                r += (kbuf[1][q] < key) + (kbuf[1][q + 1] < key) + (kbuf[1][q + 2] < key) +
+                                     (kbuf[1][q + 3] < key);
+                            for (; q < hi; ++q) r += kbuf[1][q] < key;
+                        } else {
+                            for (; q + 4 <= hi; q += 4) {
+                                const KeyT o0 = kbuf[1][q], o1 = kbuf[1][q + 1], o2 = kbuf[1][q + 2],
+                                           o3 = kbuf[1][q + 3];
+                                r += ((o0 < key) | ((o0 == key) & (q < j))) +
+                                     ((o1 < key) | ((o1 == key) & (q + 1 < j))) +
+                                     ((o2 < key) | ((o2 == key) & (q + 2 < j))) +
+                                     ((o3 < key) | ((o3 == key) & (q + 3 < j)));
+                            }
+                            for (; q < hi; ++q) {
+                                const KeyT other = kbuf[1][q];
+                                r += (other < key) | ((other == key) & (q < j));
+                            }
                         }
-                        for (; q < hi; ++q) {
-                            const KeyT other = kbuf[1][q];
-                            r += (other < key) | ((other == key) & (q < j));
-                        }
-                        kbuf[0][lo + r] = key;
+                        kbuf[0][lo + r] = packed ? (KeyT)((key >> 12) + klo) : key;
                         if (VALS) vbuf[0][lo + r] = vbuf[1][j];
                     }
                     cur = 0;

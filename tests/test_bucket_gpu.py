@@ -107,6 +107,23 @@ def test_u64(rs, oracle, key_bits):
     _check(rs, oracle, small, synth.index_values(small.size), 0, 2**key_bits - 1, 0, what="u64 vs bucket oracle")
 
 
+@pytest.mark.parametrize("key_bits", [40, 50])
+def test_u64_equal_keys_within_buckets(rs, oracle, key_bits):
+    """64-bit keys drawn from n/2.5 distinct values, so buckets of ~16 keys
+    hold equal keys: the rank sort of every bucket must keep them in input
+    order (their values show it).  40- and 50-bit keys make runs of buckets
+    narrow enough for the rank sort's one-comparison form (key bits + 12 of
+    position within 64)."""
+    n = 300_000
+    distinct = synth.keys_u64(120_000, key_bits, seed=key_bits + 7)
+    keys = distinct[synth.uniform_below(n, distinct.size, key_bits, 54)]
+    _check(rs, oracle, keys, synth.index_values(n), 0, 2**key_bits - 1, 0, what=f"u64 dup {key_bits}",
+           use_bucket_oracle=False)
+    small = keys[:60_000].copy()
+    _check(rs, oracle, small, synth.index_values(small.size), 0, 2**key_bits - 1, 0,
+           what=f"u64 dup {key_bits} vs bucket oracle")
+
+
 def test_in_place(rs, oracle):
     n = 250_000
     keys = synth.u32(n, 54, 0)
