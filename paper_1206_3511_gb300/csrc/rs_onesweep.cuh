@@ -674,6 +674,25 @@ __device__ __forceinline__ void identity_pass(const PassParams<DigitOp>& p, uint
     }
 }
 
+// Ask the keys (and values) of tile `t` into L2 (one prefetch per 128-byte
+// line, spread over the block's threads); nothing when t is past the end.
+template <typename KeyT, bool VALS, int BLOCK, int TILE, typename DigitOp>
+__device__ __forceinline__ void prefetch_tile_l2(const PassParams<DigitOp>& p, uint32_t t) {
+    if (t >= p.num_tiles) return;
+    const size_t first = (size_t)t * TILE;
+    const size_t count = min((size_t)TILE, (size_t)p.n - first);
+    const char* kb = reinterpret_cast<const char*>(static_cast<const KeyT*>(p.keys_in) + first);
+    const uint32_t klines = (uint32_t)((count * sizeof(KeyT) + 127) / 128);
+    for (uint32_t i = threadIdx.x; i < klines; i += BLOCK)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(kb + (size_t)i * 128));
+    if (VALS) {
+        const char* vb = reinterpret_cast<const char*>(p.vals_in + first);
+        const uint32_t vlines = (uint32_t)((count * 4 + 127) / 128);
+        for (uint32_t i = threadIdx.x; i < vlines; i += BLOCK)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(vb + (size_t)i * 128));
+    }
+}
+
 // Persistent: every block claims tiles from the pass's counter until none is
 // left.  A block holds one tile at a time and only waits on tiles claimed
 // earlier, whose blocks are running, so the waits always end.
@@ -709,6 +728,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p)
         if (tile >= p.num_tiles) return;  // uniform across the block
         if (p.status_next)
             for (uint32_t d = tid; d < bins; d += BLOCK) p.status_next[(size_t)tile * bins + d] = 0u;
+        // Tiles are claimed in order, so the tile one grid ahead is about
+        // the one this block takes next: its keys (and values) are asked
+        // into L2 now, one 128-byte line per thread, and its loads then
+        // wait on L2 rather than on DRAM.  Measured at 100M keys: u64 keys
+        // with values 0.787 -> 0.764 ms per pass, 40-bit u64 keys 0.293 ->
+        // 0.286; u32 keys alone 0.353 -> 0.356, so not for 4-byte items.
+        constexpr bool kPrefetch = sizeof(KeyT) + (VALS ? 4 : 0) >= 8;
+        if (kPrefetch) prefetch_tile_l2<KeyT, VALS, BLOCK, kTile>(p, tile + gridDim.x);
         TileCtx<KeyT> c;
         const uint32_t base = tile * (uint32_t)kTile;
         c.kin = static_cast<const KeyT*>(p.keys_in) + base;
