@@ -674,19 +674,16 @@ __device__ __forceinline__ void identity_pass(const PassParams<DigitOp>& p, uint
     }
 }
 
-// Ask the keys (and values) of tile `t` into L2 (one prefetch per 128-byte
-// line, spread over the block's threads); nothing when t is past the end.
-template <typename KeyT, bool VALS, int BLOCK, int TILE, typename DigitOp>
-__device__ __forceinline__ void prefetch_tile_l2(const PassParams<DigitOp>& p, uint32_t t) {
-    if (t >= p.num_tiles) return;
-    const size_t first = (size_t)t * TILE;
-    const size_t count = min((size_t)TILE, (size_t)p.n - first);
-    const char* kb = reinterpret_cast<const char*>(static_cast<const KeyT*>(p.keys_in) + first);
+// Ask `count` keys (and values) into L2: one prefetch per 128-byte line,
+// spread over the block's threads.
+template <typename KeyT, bool VALS, int BLOCK>
+__device__ __forceinline__ void prefetch_l2(const KeyT* keys, const uint32_t* vals, size_t count) {
+    const char* kb = reinterpret_cast<const char*>(keys);
     const uint32_t klines = (uint32_t)((count * sizeof(KeyT) + 127) / 128);
     for (uint32_t i = threadIdx.x; i < klines; i += BLOCK)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(kb + (size_t)i * 128));
     if (VALS) {
-        const char* vb = reinterpret_cast<const char*>(p.vals_in + first);
+        const char* vb = reinterpret_cast<const char*>(vals);
         const uint32_t vlines = (uint32_t)((count * 4 + 127) / 128);
         for (uint32_t i = threadIdx.x; i < vlines; i += BLOCK)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(vb + (size_t)i * 128));
@@ -733,9 +730,16 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep(PassParams<DigitOp> p)
         // into L2 now, one 128-byte line per thread, and its loads then
         // wait on L2 rather than on DRAM.  Measured at 100M keys: u64 keys
         // with values 0.787 -> 0.764 ms per pass, 40-bit u64 keys 0.293 ->
-        // 0.286; u32 keys alone 0.353 -> 0.356, so not for 4-byte items.
-        constexpr bool kPrefetch = sizeof(KeyT) + (VALS ? 4 : 0) >= 8;
-        if (kPrefetch) prefetch_tile_l2<KeyT, VALS, BLOCK, kTile>(p, tile + gridDim.x);
+        // 0.286; u32 keys alone 0.353 -> 0.356, so not for 4-byte items,
+        // and no gain for the bucket sort's partition passes (bound by their
+        // digits), nor in the segmented pass.
+        constexpr bool kPrefetch = !DigitOp::kStageDigit && sizeof(KeyT) + (VALS ? 4 : 0) >= 8;
+        if (kPrefetch && tile + gridDim.x < p.num_tiles) {
+            const size_t first = (size_t)(tile + gridDim.x) * kTile;
+            prefetch_l2<KeyT, VALS, BLOCK>(static_cast<const KeyT*>(p.keys_in) + first,
+                                           VALS ? p.vals_in + first : nullptr,
+                                           min((size_t)kTile, (size_t)p.n - first));
+        }
         TileCtx<KeyT> c;
         const uint32_t base = tile * (uint32_t)kTile;
         c.kin = static_cast<const KeyT*>(p.keys_in) + base;
