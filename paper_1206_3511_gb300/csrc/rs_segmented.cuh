@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep_seg(SegPassParams<Digi
 
 // ---------------------------------------------------------------------------
 // Shared-memory sort of one small segment per block: load it, run stable LSD
-// passes of up to 8 bits over (key - key_lo) between two shared buffers
+// passes of up to 9 bits over (key - key_lo) between two shared buffers
 // (each pass ranks keys inside their warps exactly like the scatter pass),
 // write it back.  In bucket mode the first pass sorts by the key's bucket
 // relative to the segment's first bucket (the insert step of Algorithm 2)
@@ -263,14 +263,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_onesweep_seg(SegPassParams<Digi
 // key bits instead, which gives the same order because bucket ids grow with
 // the key.  So is every segment of 32-bit keys, and a segment of 64-bit
 // keys that span at most kLeafKeyBits bits: the whole run of buckets is then
-// sorted by at most four (32-bit) or three 8-bit passes on the key bits,
-// which on GB300 costs less than the counting pass by bucket and the rank
-// sort of every bucket (0.68 against 1.12 ms per launch for the leaves of
-// 100M uniform 32-bit keys, whose runs span about 18 bits; for 64-bit keys,
-// whose runs span about 49 bits, the bucket pass wins, 1.62 against 1.86
-// ms).  The result is the same: sorting a run of whole buckets by key sorts
-// every bucket and keeps them in bucket order.  For 32-bit keys the bucket
-// path is compiled out, which also frees the registers it would hold.
+// sorted by its key bits in passes of at most 9 bits, which on GB300 costs
+// less than the counting pass by bucket and the rank sort of every bucket
+// for runs of 32-bit keys (about 18 bits at 100M uniform keys and n/16
+// buckets); for 64-bit keys, whose runs span about 49 bits, the bucket way
+// wins.  The result is the same: sorting a run of whole buckets by key
+// sorts every bucket and keeps them in bucket order.  For 32-bit keys the
+// bucket path is compiled out, which also frees the registers it would
+// hold.
 constexpr uint32_t kBucketSortMax = 48;
 constexpr uint32_t kLeafKeyBits = 24;
 
