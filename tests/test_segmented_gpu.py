@@ -36,8 +36,12 @@ def _check(rs, oracle, keys, sizes, vals=None, key_bits=0, in_place=False, what=
         assert_same(gv, wv, what + " values")
 
 
+# tiny-sort and shared-memory-sort limits (256, 4096), the shared-memory
+# sort's switch between 4 and 16 keys per lane (1024), its whole-warp runs
+# (multiples of 128 and 512 keys), tile edges of the scatter passes
 EDGE_SIZES = [0, 1, 2, 3, 0, 255, 256, 4095, 4096, 4097, 4608, 4609, 6143, 6144, 6145, 9217, 12289, 70_001, 0, 1,
-              3072, 3073, 200_000]
+              3072, 3073, 200_000, 257, 383, 384, 385, 511, 512, 513, 1023, 1024, 1025, 1535, 1536, 1537, 2047,
+              2048, 2049, 3583, 3584, 3585]
 
 
 @pytest.mark.parametrize("kb,with_values", [(4, False), (4, True), (8, False), (8, True)])
