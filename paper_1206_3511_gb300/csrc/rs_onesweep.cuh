@@ -532,7 +532,7 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     // kept, two per register, and the digit is taken again from the key
     // when it is staged: 18 registers instead of 36 for 36 keys per thread.
     constexpr bool kPackRanks = !DigitOp::kStageDigit;
-    uint32_t dr[kPackRanks ? (ITEMS + 1) / 2 : ITEMS];
+    uint32_t dr[kPackRanks ? (ITEMS + 1) / 2 : ITEMS] = {};  // (every word is set before it is read)
     auto put = [&](int i, uint32_t d, uint32_t rank) {
         if (kPackRanks) {
             if (i & 1)
