@@ -131,8 +131,9 @@ struct KeyXform {
 
 // Exclusive prefix sum of one value per thread across the block.  s_warp needs
 // BLOCK/32 + 1 words; the block total lands in s_warp[BLOCK/32].  Contains
-// __syncthreads() and must be reached by every thread.
-template <int BLOCK>
+// __syncthreads() and must be reached by every thread.  Without TAIL_SYNC
+// the caller must pass another barrier before s_warp is written again.
+template <int BLOCK, bool TAIL_SYNC = true>
 __device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t x, uint32_t* s_warp) {
     constexpr int kWarps = BLOCK / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -157,7 +158,7 @@ __device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t x, uint32_t* s_
     }
     __syncthreads();
     uint32_t r = inc - x + s_warp[warp];
-    __syncthreads();
+    if (TAIL_SYNC) __syncthreads();  // s_warp may be written again at once
     return r;
 }
 

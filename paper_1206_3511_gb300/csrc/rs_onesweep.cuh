@@ -580,35 +580,60 @@ __device__ __forceinline__ void onesweep_tile(const PassParams<DigitOp>& p, cons
     __syncthreads();
 
     // per digit: tile count, publish it, then the look-back right away, so
-    // this tile's inclusive prefix is published as early as possible
+    // this tile's inclusive prefix is published as early as possible; then
+    // each digit's start inside the staged tile, and each half-warp's offset
+    // inside that digit (it replaces the rank-table entry)
     uint32_t* srow = p.status + (size_t)c.tile * bins;
-    for (uint32_t d = tid; d < bins; d += BLOCK) {
+    // One digit per thread: its count, look-back and place in the tile's
+    // scan stay in registers (two barriers instead of five).  Measured at
+    // 100M keys: bucket partition passes 0.535 -> 0.521 ms, u32 key-value
+    // sorts 2.398 -> 2.367 ms; but u32 keys alone 0.353 -> 0.358 ms per
+    // pass, which keep the path through shared memory.
+    constexpr bool kFused = DigitOp::kStageDigit || VALS;
+    if (kFused && bins == (uint32_t)BLOCK) {
+        const uint32_t d = (uint32_t)tid;
         uint32_t sum = 0;
 #pragma unroll
         for (int s = 0; s < kSubs; ++s) sum += sm.tab[(size_t)s * sm.tab_stride + d] >> 16;
-        sm.local[d] = sum;
         if (publish) st_relaxed(srow + d, (first ? kFlagPrefix : kFlagAggregate) | sum);
-    }
-    for (uint32_t d = tid; d < bins; d += BLOCK) {
         const uint32_t excl =
             first ? 0u : lookback_digit(p.status, c.tile, c.first_tile, bins, d, p.spin_limit, p.hdr);
-        if (!first && publish) st_relaxed(srow + d, kFlagPrefix | ((excl + sm.local[d]) & kCountMask));
-        sm.delta[d] = c.digit_base[d] + excl;
-    }
-    __syncthreads();
-
-    // each digit's start inside the staged tile, and each half-warp's offset
-    // inside that digit (it replaces the rank-table entry)
-    block_exclusive_scan_smem<BLOCK>(sm.local, (int)bins, sm.scan);
-    for (uint32_t d = tid; d < bins; d += BLOCK) {
-        uint32_t run = sm.local[d];
-        sm.delta[d] -= run;
+        if (!first && publish) st_relaxed(srow + d, kFlagPrefix | ((excl + sum) & kCountMask));
+        uint32_t run = block_exclusive_sum<BLOCK, false>(sum, sm.scan);
+        sm.delta[d] = c.digit_base[d] + excl - run;
 #pragma unroll
         for (int s = 0; s < kSubs; ++s) {
             uint32_t* e = sm.tab + (size_t)s * sm.tab_stride + d;
             const uint32_t cnt = *e >> 16;
             *e = run;
             run += cnt;
+        }
+    } else {
+        for (uint32_t d = tid; d < bins; d += BLOCK) {
+            uint32_t sum = 0;
+#pragma unroll
+            for (int s = 0; s < kSubs; ++s) sum += sm.tab[(size_t)s * sm.tab_stride + d] >> 16;
+            sm.local[d] = sum;
+            if (publish) st_relaxed(srow + d, (first ? kFlagPrefix : kFlagAggregate) | sum);
+        }
+        for (uint32_t d = tid; d < bins; d += BLOCK) {
+            const uint32_t excl =
+                first ? 0u : lookback_digit(p.status, c.tile, c.first_tile, bins, d, p.spin_limit, p.hdr);
+            if (!first && publish) st_relaxed(srow + d, kFlagPrefix | ((excl + sm.local[d]) & kCountMask));
+            sm.delta[d] = c.digit_base[d] + excl;
+        }
+        __syncthreads();
+        block_exclusive_scan_smem<BLOCK>(sm.local, (int)bins, sm.scan);
+        for (uint32_t d = tid; d < bins; d += BLOCK) {
+            uint32_t run = sm.local[d];
+            sm.delta[d] -= run;
+#pragma unroll
+            for (int s = 0; s < kSubs; ++s) {
+                uint32_t* e = sm.tab + (size_t)s * sm.tab_stride + d;
+                const uint32_t cnt = *e >> 16;
+                *e = run;
+                run += cnt;
+            }
         }
     }
     __syncthreads();
