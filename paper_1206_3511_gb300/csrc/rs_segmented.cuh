@@ -559,14 +559,17 @@ __global__ void __launch_bounds__(BLOCK, 3) k_local_sort(LocalParams lp, BucketF
         if (by_keys) {
             // the fewest passes of at most 9 bits that cover the segment's
             // key bits, the bits shared evenly (18 bits: two 9-bit passes
-            // instead of three 8-bit ones)
+            // instead of three 8-bit ones); the last pass takes only the
+            // bits left (17 bits: 9 + 8), so its tables are no wider than
+            // its digits
             const uint32_t nb = seg.bits;
             const uint32_t P = nb ? (nb + 8) / 9 : 0;
             const int dw = P ? (int)((nb + P - 1) / P) : 0;
             for (uint32_t q = 0, shift = 0; q < P; ++q, shift += (uint32_t)dw) {
-                const uint32_t dmask = (1u << dw) - 1u;
+                const int w = q + 1 == P ? (int)(nb - shift) : dw;
+                const uint32_t dmask = (1u << w) - 1u;
                 local_pass_fit<KeyT, VALS, BLOCK, ITEMS>(
-                    kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1], m, dw, s_tab, s_start, s_cnt, s_scan,
+                    kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1], m, w, s_tab, s_start, s_cnt, s_scan,
                     [&](KeyT k) { return (uint32_t)((KeyT)(k - klo) >> shift) & dmask; });
                 cur ^= 1;
             }
