@@ -361,7 +361,11 @@ static rs_status radix_sort_xf_body(int key_bytes, const void* keys_in, void* ke
         pp.keys_out = dst_k;
         pp.vals_in = src_v;
         pp.vals_out = dst_v;
-        pp.op = RadixDigit{p * D, L.bins - 1u};
+        // the last pass ranks only the key bits left (20-bit keys: 8 + 8 + 4),
+        // so its tables, scan and look-back cover 2^w digits, not 2^D
+        const int w = std::min(D, key_bits - p * D);
+        pp.digit_bits = w;
+        pp.op = RadixDigit{p * D, (1u << w) - 1u};
         pp.digit_base = scan + (size_t)p * L.bins;
         pp.status = status[p & 1];
         pp.status_next = (p + 1 < P) ? status[(p + 1) & 1] : nullptr;
