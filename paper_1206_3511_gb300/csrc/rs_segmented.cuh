@@ -709,7 +709,7 @@ __device__ __forceinline__ void bitonic_tiny(uint32_t m, const KeyT (&k)[kTinyCa
 // network in registers (bitonic_tiny).  Keys at or above 2^bits are reported
 // in hdr.
 template <typename KeyT, bool VALS>
-__global__ void __launch_bounds__(256) k_tiny_sort(const KeyT* __restrict__ keys_in, KeyT* keys_out,
+__global__ void __launch_bounds__(256, VALS ? 2 : 4) k_tiny_sort(const KeyT* __restrict__ keys_in, KeyT* keys_out,
                                                    const uint32_t* __restrict__ vals_in, uint32_t* vals_out,
                                                    const SegDesc* __restrict__ segs, const uint32_t* count,
                                                    WsHeader* hdr) {
@@ -718,20 +718,32 @@ __global__ void __launch_bounds__(256) k_tiny_sort(const KeyT* __restrict__ keys
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     KeyT* row = s_keys[warp];
     const uint32_t nseg = *count;
+    const uint32_t stride = gridDim.x * kWarps;
     bool bad = false;
-    for (uint32_t si = blockIdx.x * kWarps + warp; si < nseg; si += gridDim.x * kWarps) {
-        const SegDesc sd = segs[si];
+    // software pipeline: the next segment's descriptor and keys are loaded
+    // before the current one is sorted, so their latency overlaps the sort
+    SegDesc nsd{};
+    KeyT nk[kPerLane];
+    auto load = [&](uint32_t at) {
+        nsd = segs[at];
+#pragma unroll
+        for (int j = 0; j < kPerLane; ++j) {
+            const uint32_t i = (uint32_t)j * 32 + lane;
+            nk[j] = i < nsd.n ? keys_in[nsd.start + i] : (KeyT)0;
+        }
+    };
+    uint32_t si = blockIdx.x * kWarps + warp;
+    if (si < nseg) load(si);
+    for (; si < nseg; si += stride) {
+        const SegDesc sd = nsd;
         const uint32_t m = sd.n;
         KeyT k[kPerLane];
 #pragma unroll
         for (int j = 0; j < kPerLane; ++j) {
-            const uint32_t i = (uint32_t)j * 32 + lane;
-            k[j] = 0;
-            if (i < m) {
-                k[j] = keys_in[sd.start + i];
-                bad |= sd.bits < 8 * sizeof(KeyT) && (k[j] >> sd.bits) != 0;
-            }
+            k[j] = nk[j];
+            if ((uint32_t)j * 32 + lane < m) bad |= sd.bits < 8 * sizeof(KeyT) && (k[j] >> sd.bits) != 0;
         }
+        if (si + stride < nseg) load(si + stride);
         KeyT* kout = keys_out + sd.start;
         uint32_t* vout = VALS ? vals_out + sd.start : nullptr;
         const uint32_t* vin = VALS ? vals_in + sd.start : nullptr;
